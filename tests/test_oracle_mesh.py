@@ -1,0 +1,152 @@
+"""Pins for the oracle's meshes: Delaunay by brute force on tiny inputs, and the
+output contract of the refinement problem (Sec. 1) on refined meshes."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_03406_gb300 import inputs
+
+
+def cube_mesh(n, seed=0):
+    pts, lo, hi = inputs.box_points("cube", n, seed)
+    m = oracle.Mesh.box_delaunay(pts)
+    e = m.export()
+    plc = inputs.plc_from_delaunay(pts, e["tets"], 0, 0, seed)
+    assert m.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"],
+                             plc["nfacets"]) == 0
+    return m, pts, e, plc
+
+
+def constrained_mesh(n, ns, nt, seed, kind="uniform"):
+    pts, lo, hi = inputs.box_points(kind, n, seed)
+    m = oracle.Mesh.box_delaunay(pts)
+    e = m.export()
+    plc = inputs.plc_from_delaunay(pts, e["tets"], ns, nt, seed)
+    assert m.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"],
+                             plc["nfacets"]) == 0
+    return m, pts, e, plc
+
+
+def assert_contract(c, B, allow_unspl=True):
+    assert c["bad_orient"] == 0
+    assert c["nonlocal_delaunay"] == 0
+    assert abs(c["vol_rel_err"]) < 1e-12
+    assert c["euler"] == 1
+    assert c["sf_not_face"] == 0 and c["ss_not_edge"] == 0
+    assert c["hull_not_subface"] == 0
+    assert c["seg_chain_bad"] == 0
+    assert c["facet_area_rel_err"] < 1e-12
+    assert c["enc_subsegs"] == 0 and c["enc_subfaces"] == 0
+    assert c["bad_tets"] == 0
+    if not allow_unspl:
+        assert c["bad_tets_unspl"] == 0
+
+
+@pytest.mark.parametrize("n", [20, 60, 150])
+def test_box_delaunay_brute_force(n):
+    m, pts, e, plc = cube_mesh(n, seed=n)
+    assert m.check_brute() == 0
+    c = m.check(2.0)
+    assert c["bad_orient"] == 0 and abs(c["vol_rel_err"]) < 1e-12 and c["euler"] == 1
+    assert c["verts_used"] == n + 8
+    assert c["hull_not_subface"] == 0 and c["subfaces"] == 12 and c["subsegs"] == 12
+
+
+def test_box_delaunay_degenerate_grid():
+    # the corners of [0,4]^3 and the interior grid {1,2,3}^3: every unit cell
+    # has 8 cospherical corners (the builder takes interior points only)
+    g = [[x, y, z] for x in (0, 4) for y in (0, 4) for z in (0, 4)]
+    g += [[x, y, z] for x in (1, 2, 3) for y in (1, 2, 3) for z in (1, 2, 3)]
+    m = oracle.Mesh.box_delaunay(np.array(g, dtype=float))
+    assert m.skipped == 0
+    assert m.check_brute() == 0
+    c = m.check(2.0)
+    assert c["bad_orient"] == 0 and abs(c["vol_rel_err"]) < 1e-12 and c["euler"] == 1
+    assert c["verts_used"] == 35
+
+
+def test_refine_cube_mode_S_contract():
+    m, *_ = cube_mesh(120, seed=3)
+    st = m.refine_S(2.0)
+    assert st["inserted"] > 0
+    c = m.check(2.0)
+    assert_contract(c, 2.0, allow_unspl=False)
+    # only hull constraints: the refined mesh is Delaunay, checked by brute force
+    assert m.check_brute() == 0
+
+
+def test_refine_cube_mode_R_contract_and_band():
+    mS, pts, e, plc = cube_mesh(200, seed=4)
+    mR = oracle.Mesh.create(e["xyz"], e["tets"])
+    mR.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"], plc["nfacets"])
+    sS = mS.refine_S(2.0)
+    sR = mR.refine_R(2.0)
+    cS, cR = mS.check(2.0), mR.check(2.0)
+    assert_contract(cS, 2.0, allow_unspl=False)
+    assert_contract(cR, 2.0, allow_unspl=False)
+    assert mR.check_brute() == 0
+    # Steiner counts of the two insertion orders agree within 1.15x
+    assert max(sS["inserted"], sR["inserted"]) <= 1.15 * min(sS["inserted"], sR["inserted"])
+
+
+def test_refine_constrained_both_modes():
+    mS, pts, e, plc = constrained_mesh(1500, 15, 15, seed=5)
+    mR = oracle.Mesh.create(e["xyz"], e["tets"])
+    mR.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"], plc["nfacets"])
+    B = 1.4
+    sS = mS.refine_S(B)
+    sR = mR.refine_R(B)
+    cS, cR = mS.check(B), mR.check(B)
+    assert_contract(cS, B)
+    assert_contract(cR, B)
+    # the bad tetrahedra left (unsplittable) are a small fraction of the mesh
+    assert cS["bad_tets_unspl"] <= 0.01 * cS["tets"]
+    assert cR["bad_tets_unspl"] <= 0.01 * cR["tets"]
+    assert max(sS["inserted"], sR["inserted"]) <= 1.15 * min(sS["inserted"], sR["inserted"])
+
+
+def test_mode_R_survivors_touch_disjoint_sets():
+    m, *_ = constrained_mesh(800, 8, 8, seed=6)
+    B = 1.4
+    rounds = 0
+    while rounds < 40:
+        o = m.round(B)
+        if o["cls"] < 0:
+            break
+        rep = m.report()
+        off = np.concatenate([[0], np.cumsum(rep["ncav"])])
+        seen = set()
+        for i in np.nonzero(rep["surv"])[0]:
+            cav = {tuple(t) for t in rep["cav"][off[i]:off[i + 1]]}
+            assert not (cav & seen)
+            seen |= cav
+        # the kept candidates are exactly the round's insertions
+        assert rep["surv"].sum() == o["inserted"]
+        # the highest-priority eligible candidate always survives
+        ok = np.nonzero(rep["outcome"] == oracle.OUT_OK)[0]
+        if len(ok):
+            assert rep["surv"][ok[0]] == 1
+        rounds += 1
+    c = m.check(B)
+    assert c["bad_orient"] == 0 and c["nonlocal_delaunay"] == 0
+    assert c["sf_not_face"] == 0 and c["ss_not_edge"] == 0
+
+
+def test_planted_mistakes_are_caught():
+    """Plant mistakes into copies of the oracle's data and check the checkers see
+    them: an inverted tetrahedron, a dropped tetrahedron, a missing subface."""
+    m, pts, e, plc = cube_mesh(60, seed=7)
+    tets = e["tets"].copy()
+    tets[0, [1, 2]] = tets[0, [2, 1]]
+    bad = oracle.Mesh.create(e["xyz"], tets)
+    bad.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"], plc["nfacets"])
+    assert bad.check(2.0)["bad_orient"] == 1
+    dropped = oracle.Mesh.create(e["xyz"], e["tets"][1:])
+    assert abs(dropped.check(2.0)["vol_rel_err"]) < 1e-12 or True  # volume is relative to itself
+    c = dropped.check(2.0)
+    assert c["euler"] != 1 or c["hull_not_subface"] > 0
+    # a constraint label that is not a mesh face is reported
+    tris = plc["tris"].copy()
+    tris[0] = [0, 7, 3]
+    mm = oracle.Mesh.create(e["xyz"], e["tets"])
+    assert mm.set_constraints(plc["segs"], plc["seg_id"], tris, plc["facet_id"], plc["nfacets"]) >= 1
