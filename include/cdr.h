@@ -1,0 +1,223 @@
+/* cdr.h -- constrained Delaunay refinement on one GB300 (sm_103a).
+ *
+ * The library implements the per-round parallel refinement step of gQM3D
+ * (Chen & Tan, "Computing Three-dimensional Constrained Delaunay Refinement
+ * Using the GPU", I3D 2019):
+ *   Sec. 1  -- problem: given a piecewise linear complex G = (P, E, F), a
+ *              constrained Delaunay triangulation (CDT) T conforming to G and a
+ *              constant B, add Steiner points until (most) tetrahedra have
+ *              circumradius / shortest edge <= B, keeping T a CDT of G.
+ *   Sec. 2  -- rounds: subsegments, then subfaces, then bad tetrahedra are split;
+ *              splitting points are midpoints / circumcentres; each point's
+ *              Delaunay region is grown, regions are made disjoint by
+ *              predetermined priorities ("grow-and-blast"), and the surviving
+ *              points are inserted concurrently.
+ *
+ * Conventions used by every call:
+ *   - Coordinates are FP64, row-major (x, y, z) per vertex.
+ *   - Ids are int32. A tetrahedron (a, b, c, d) is positively oriented:
+ *     (b - a) . ((c - a) x (d - a)) > 0.
+ *   - Constraint labels: a subsegment is a mesh edge lying on a PLC segment (E),
+ *     given with that segment's id; a subface is a mesh face lying in a PLC
+ *     polygon (F), given with that polygon's (facet's) id. Each PLC polygon edge
+ *     is itself a segment.
+ *   - All pointers passed in are HOST pointers unless stated otherwise. The
+ *     library copies every input; the caller keeps ownership of its buffers.
+ *   - Device memory comes from the caller's allocator when one is given (the
+ *     Python binding passes PyTorch's caching allocator), else from
+ *     cudaMallocAsync on the handle's stream. The handle owns its device buffers
+ *     until cdr_destroy.
+ *   - One handle is used by one host thread at a time. No call throws; every
+ *     call returns a status code (CDR_OK = 0), see cdr_status_string.
+ *   - Errors leave the handle usable unless stated (CDR_ERR_CUDA and
+ *     CDR_ERR_INTERNAL may leave it in an unspecified state; destroy it).
+ */
+#ifndef CDR_H_
+#define CDR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CDR_OK = 0,
+  CDR_ROUND_LIMIT = 1,        /* informational: max_rounds reached with work left */
+  CDR_ERR_INVALID_INPUT = -1, /* malformed mesh / labels / arguments             */
+  CDR_ERR_OOM = -2,           /* the allocator returned NULL                      */
+  CDR_ERR_CUDA = -3,          /* a CUDA call failed                               */
+  CDR_ERR_ITER_LIMIT = -4,    /* a bounded device loop gave up                    */
+  CDR_ERR_INTERNAL = -5       /* exact-arithmetic capacity or an invariant failed */
+};
+
+typedef struct cdr_handle cdr_handle;
+
+/* Device memory provider. alloc returns device memory of at least `bytes` bytes
+ * usable on `stream` (NULL on failure); free releases it. */
+typedef struct {
+  void* (*alloc)(uint64_t bytes, void* ctx, void* stream);
+  void (*free)(void* ptr, uint64_t bytes, void* ctx, void* stream);
+  void* ctx;
+} cdr_allocator;
+
+/* The input: a CDT with its constraint labels (Sec. 1).
+ *   xyz[n_verts*3]            vertex coordinates
+ *   tets[n_tets*4]            positively oriented tetrahedra
+ *   segs[n_segs*2], seg_id[]  subsegments (mesh edges) and their PLC segment ids
+ *   tris[n_tris*3], facet_id[] subfaces (mesh faces) and their PLC facet ids;
+ *                              facet ids are 0 .. n_facets-1
+ *   facet_ref[n_facets*3]     optional (NULL = derived) per-facet reference point
+ *                              used to read circles and sides inside a facet; the
+ *                              derived point is the facet's first listed triangle's
+ *                              first vertex moved along the dominant axis of that
+ *                              triangle's normal by the smallest power of two that
+ *                              is >= 4x the largest bounding-box extent.
+ * Every hull face must be a subface (the domain is closed by facets). */
+typedef struct {
+  const double* xyz;
+  int32_t n_verts;
+  const int32_t* tets;
+  int32_t n_tets;
+  const int32_t* segs;
+  const int32_t* seg_id;
+  int32_t n_segs;
+  const int32_t* tris;
+  const int32_t* facet_id;
+  int32_t n_tris;
+  int32_t n_facets;
+  const double* facet_ref;
+} cdr_mesh_in;
+
+/* Options. Zero-initialised fields select the defaults given. */
+typedef struct {
+  double guard2;        /* squared shortest-edge guard; <= 0: (1e-9 * bbox diagonal)^2 */
+  int32_t walk_limit;   /* point-location step limit; 0: 100000                         */
+  int32_t reserve_factor; /* initial capacity multiple of the input sizes; 0: 4          */
+} cdr_options;
+
+/* Per-call statistics. */
+typedef struct {
+  int32_t rounds;
+  int32_t rounds_by_class[3]; /* subsegment, subface, tetrahedron rounds        */
+  int64_t candidates;         /* splitting points evaluated                     */
+  int64_t steiner_inserted;   /* points inserted                                */
+  int64_t rejected;           /* points refused for encroachment (split first)  */
+  int64_t blasted;            /* eligible points that lost a priority conflict  */
+  int64_t unsplittable;       /* elements given up (guard, closure, overflow)   */
+  int64_t n_verts, n_tets, n_subfaces, n_subsegs;
+  int64_t n_bad_left;         /* bad tetrahedra left (all unsplittable)         */
+} cdr_stats;
+
+/* Sizes of the live mesh, for cdr_export. */
+typedef struct {
+  int32_t n_verts, n_tets, n_subfaces, n_subsegs, n_facets;
+} cdr_sizes;
+
+/* Export buffers (host, caller-owned, sized from cdr_export_sizes). Any pointer
+ * may be NULL to skip that array.
+ *   xyz[n_verts*3]
+ *   tets[n_tets*4]            live tetrahedra, positively oriented
+ *   tet_flag[n_tets]          bit1: unsplittable
+ *   subfaces[n_subfaces*4]    a, b, c, facet id
+ *   subface_flag[n_subfaces]  bit0: must split (encroached by a refused point),
+ *                             bit1: unsplittable
+ *   subsegs[n_subsegs*3]      a, b, segment id
+ *   subseg_flag[n_subsegs]    as subface_flag
+ *   facet_ref[n_facets*3]     the facet reference points in use */
+typedef struct {
+  double* xyz;
+  int32_t* tets;
+  uint8_t* tet_flag;
+  int32_t* subfaces;
+  uint8_t* subface_flag;
+  int32_t* subsegs;
+  uint8_t* subseg_flag;
+  double* facet_ref;
+} cdr_mesh_out;
+
+/* Create a handle from a CDT with constraint labels (Sec. 1). The mesh is
+ * validated (index ranges, labels present as edges / faces, faces shared by at
+ * most two tetrahedra, every hull face a subface): CDR_ERR_INVALID_INPUT.
+ * stream is a cudaStream_t (NULL = legacy default stream). alloc may be NULL. */
+int cdr_create(const cdr_mesh_in* in, const cdr_options* opt, const cdr_allocator* alloc,
+               void* stream, cdr_handle** out);
+
+/* Refine (Sec. 2) with bound B until no encroached subsegment, encroached
+ * subface or bad tetrahedron is left (apart from unsplittable ones), or
+ * max_rounds rounds ran (then CDR_ROUND_LIMIT). stats may be NULL. */
+int cdr_refine(cdr_handle* h, double B, int32_t max_rounds, cdr_stats* stats);
+
+/* Exactly one round (Sec. 2) with bound B. *cls receives the class served
+ * (0 subsegments, 1 subfaces, 2 tetrahedra; -1 = nothing left). stats
+ * (nullable) receives that round's counts. */
+int cdr_round(cdr_handle* h, double B, int32_t* cls, cdr_stats* stats);
+
+/* Sizes of the live mesh. */
+int cdr_export_sizes(cdr_handle* h, cdr_sizes* out);
+
+/* Copy the live mesh into caller buffers (see cdr_mesh_out). */
+int cdr_export(cdr_handle* h, const cdr_mesh_out* out);
+
+/* Report of the last round, candidate by candidate in priority order (used to
+ * check a round against a reference implementation). Two-call protocol:
+ * call with all pointers NULL to get *n_cand and *n_cav_total, then with
+ * buffers:
+ *   keys[n_cand*4]      the element's sorted vertex ids (-1 padded)
+ *   pts[n_cand*3]       splitting point
+ *   outcome[n_cand]     0 eligible, 1 refused (encroachment), 2 unsplittable
+ *   reason[n_cand]      detail code (see DESIGN notes in the repository)
+ *   survived[n_cand]    1 if inserted
+ *   n_cav[n_cand], n_bnd[n_cand], n_fcav[n_cand]  region sizes
+ *   cav[n_cav_total*4]  each candidate's cavity tetrahedra as sorted vertex ids,
+ *                       concatenated in candidate order (eligible candidates) */
+int cdr_round_report(cdr_handle* h, int32_t* n_cand, int64_t* n_cav_total, int32_t* keys,
+                     double* pts, int32_t* outcome, int32_t* reason, int32_t* survived,
+                     int32_t* n_cav, int32_t* n_bnd, int32_t* n_fcav, int32_t* cav);
+
+/* Save the current mesh on the device / restore it (for repeated timing). */
+int cdr_checkpoint(cdr_handle* h);
+int cdr_restore(cdr_handle* h);
+
+/* Release the handle and all its device memory. NULL is ignored. */
+void cdr_destroy(cdr_handle* h);
+
+/* Delaunay tetrahedralisation of points whose bounding-box corners are among
+ * them and whose other points lie strictly inside the box, built on the device
+ * by the same grow / select / insert rounds with plain points as candidates.
+ * The result (export: vertices = the points in input order, tetrahedra) has no
+ * constraint labels. Points that coincide with an earlier point are skipped
+ * (*n_skipped). */
+int cdr_delaunay_box(const double* xyz, int32_t n, const cdr_options* opt,
+                     const cdr_allocator* alloc, void* stream, cdr_handle** out,
+                     int32_t* n_skipped, int32_t* n_rounds);
+
+/* Text for a status code. */
+const char* cdr_status_string(int status);
+
+/* Library self-description: sm architecture compiled for, e.g. 103. */
+int cdr_device_arch(void);
+
+/* Evaluate one device predicate or formula over a batch (a checking aid for the
+ * geometry every round relies on; Sec. 1 bad-tetrahedron rule, Sec. 2 splitting
+ * points and Delaunay-region tests).
+ *   in[n*16]  per item: points a, b, c, d, e as (x, y, z) in doubles 0..14;
+ *             for kind 7 the bound B sits in double 12
+ *   kind      0 orient3d(a,b,c,d) sign       1 insphere(a,b,c,d; e) sign (> 0:
+ *             strictly inside, abcd positively oriented)
+ *             2 diametral (a-c).(b-c) sign   3 equatorial(a,b,c; d) sign (< 0:
+ *             strictly inside the smallest sphere through a, b, c)
+ *             4 tetrahedron circumcentre of (a,b,c,d)   5 circumcentre of (a,b,c)
+ *             6 midpoint of (a,b)            7 bad tetrahedron (a,b,c,d) for B
+ *             8..11 the exact-arithmetic paths of 0, 1, 3, 2 alone
+ *   sign[n]   the sign (kinds 4..7: 1 = ok / bad, 0 = degenerate / not bad)
+ *   out[n*3]  (nullable) the point computed by kinds 4..6
+ * Uses cudaMalloc / cudaFree for its own buffers and synchronises `stream`.
+ * CDR_ERR_INTERNAL if the exact arithmetic ran out of capacity. */
+int cdr_eval_predicates(int32_t kind, const double* in, int32_t n, int32_t* sign, double* out,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDR_H_ */

@@ -1,0 +1,1404 @@
+// Host driver and C-ABI of the refinement library (see include/cdr.h).
+//
+// cdr_create builds the device mesh from a CDT with constraint labels (Sec. 1 of
+// Chen & Tan, I3D 2019); cdr_round runs one round of the paper's refinement step
+// (Sec. 2): classify, order by priority, split points, locate, grow regions,
+// select disjoint regions, insert; cdr_refine repeats rounds until no candidate
+// is left. Device memory comes from the caller's allocator (or cudaMallocAsync).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cub/cub.cuh>
+#include <thrust/iterator/counting_iterator.h>
+
+#include "../../include/cdr.h"
+#include "kernels.cuh"
+#include "mesh.cuh"
+
+using namespace cdr;
+
+namespace {
+
+// ------------------------------------------------------------ device buffers
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct cdr_handle {
+  cudaStream_t stream = nullptr;
+  cdr_allocator alloc{};
+  bool has_alloc = false;
+  int err = 0;  // sticky allocation / CUDA failure
+  DevMesh m{};
+  int capV = 0, capT = 0, capS = 0, capG = 0;
+  int hcount = 0;
+  double lastB = -1.0;
+  unsigned epoch = 0;
+  bool dt_mode = false;
+  // mesh arrays
+  Buf bV, bT, bTS, bTflag, bTmark, bTfwd, bSV, bSN, bSflag, bSmust, bSmark, bGV, bGflag, bGmust,
+      bFQ, bHK, bHV;
+  // classification
+  Buf bCandS, bCandG, bCandT;
+  // round buffers
+  int capR = 0, capR2 = 0, capWs2 = 0;
+  Buf bCand, bCand2, bKeys, bKeys2, bSp, bLoc, bStatus, bSurv, bCounts, bOffs, bSlab1, bSlab2of,
+      bList2, bSlab2, bWs2, bCkey, bTmp, bStats, bErr, bI32;
+  size_t tmpBytes = 0;
+  // points (Delaunay mode)
+  Buf bPts, bHint, bPstate;
+  int npts = 0;
+  // last round, for the report
+  int lastN = 0, lastCls = -1, lastN2 = 0;
+  // checkpoint
+  std::vector<Buf> ck;
+  DevMesh ckm{};
+  int ck_hcount = 0;
+  bool has_ck = false;
+};
+
+namespace {
+
+int set_err(cdr_handle* h, int e) {
+  if (!h->err) h->err = e;
+  return e;
+}
+
+void* dalloc(cdr_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (h->has_alloc) {
+    p = h->alloc.alloc((uint64_t)bytes, h->alloc.ctx, (void*)h->stream);
+  } else {
+    if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) p = nullptr;
+  }
+  return p;
+}
+void dfree(cdr_handle* h, Buf& b) {
+  if (!b.p) return;
+  if (h->has_alloc) h->alloc.free(b.p, (uint64_t)b.bytes, h->alloc.ctx, (void*)h->stream);
+  else cudaFreeAsync(b.p, h->stream);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+// (re)allocate b to hold `bytes`, keeping the first `keep` bytes
+bool ensure(cdr_handle* h, Buf& b, size_t bytes, size_t keep = 0) {
+  if (b.bytes >= bytes && b.p) return true;
+  size_t nb = std::max(bytes, b.bytes + b.bytes / 2);
+  void* p = dalloc(h, nb);
+  if (!p) {
+    set_err(h, CDR_ERR_OOM);
+    return false;
+  }
+  if (keep && b.p) cudaMemcpyAsync(p, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, h->stream);
+  dfree(h, b);
+  b.p = p;
+  b.bytes = nb;
+  return true;
+}
+template <class T>
+T* ptr(Buf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+int cuda_status(cdr_handle* h) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(h, CDR_ERR_CUDA);
+  return h->err;
+}
+
+// bind the mesh pointers after any reallocation
+void bind(cdr_handle* h) {
+  DevMesh& m = h->m;
+  m.V = ptr<V4>(h->bV);
+  m.T = ptr<TetRec>(h->bT);
+  m.TS = ptr<int4>(h->bTS);
+  m.Tflag = ptr<uint8_t>(h->bTflag);
+  m.Tmark = ptr<unsigned long long>(h->bTmark);
+  m.Tfwd = ptr<int>(h->bTfwd);
+  m.SV = ptr<int4>(h->bSV);
+  m.SN = ptr<int4>(h->bSN);
+  m.Sflag = ptr<uint8_t>(h->bSflag);
+  m.Smust = ptr<uint8_t>(h->bSmust);
+  m.Smark = ptr<unsigned long long>(h->bSmark);
+  m.GV = ptr<int4>(h->bGV);
+  m.Gflag = ptr<uint8_t>(h->bGflag);
+  m.Gmust = ptr<uint8_t>(h->bGmust);
+  m.FQ = ptr<V4>(h->bFQ);
+  m.HK = ptr<unsigned long long>(h->bHK);
+  m.HV = ptr<int>(h->bHV);
+}
+
+bool grow_verts(cdr_handle* h, int need) {
+  if (need <= h->capV) return true;
+  int cap = std::max(need, h->capV + h->capV / 2);
+  if (cap > kMaxVerts) return false;
+  if (!ensure(h, h->bV, (size_t)cap * sizeof(V4), (size_t)h->m.nV * sizeof(V4))) return false;
+  h->capV = cap;
+  bind(h);
+  return true;
+}
+bool grow_tets(cdr_handle* h, int need) {
+  if (need <= h->capT) return true;
+  int cap = std::max(need, h->capT + h->capT / 2);
+  if (cap > kMaxTets) return false;
+  size_t n = h->m.nT;
+  bool ok = ensure(h, h->bT, cap * sizeof(TetRec), n * sizeof(TetRec)) &&
+            ensure(h, h->bTS, cap * sizeof(int4), n * sizeof(int4)) &&
+            ensure(h, h->bTflag, cap, n) &&
+            ensure(h, h->bTmark, cap * sizeof(unsigned long long), n * 8) &&
+            ensure(h, h->bTfwd, cap * sizeof(int), n * 4) && ensure(h, h->bCandT, cap, 0);
+  if (!ok) return false;
+  h->capT = cap;
+  bind(h);
+  return true;
+}
+bool grow_subfaces(cdr_handle* h, int need) {
+  if (need <= h->capS) return true;
+  int cap = std::max(need, h->capS + h->capS / 2);
+  size_t n = h->m.nS;
+  bool ok = ensure(h, h->bSV, cap * sizeof(int4), n * sizeof(int4)) &&
+            ensure(h, h->bSN, cap * sizeof(int4), n * sizeof(int4)) &&
+            ensure(h, h->bSflag, cap, n) && ensure(h, h->bSmust, cap, n) &&
+            ensure(h, h->bSmark, cap * 8, n * 8) && ensure(h, h->bCandS, cap, 0);
+  if (!ok) return false;
+  h->capS = cap;
+  bind(h);
+  return true;
+}
+bool grow_subsegs(cdr_handle* h, int need) {
+  if (need <= h->capG) return true;
+  int cap = std::max(need, h->capG + h->capG / 2);
+  size_t n = h->m.nG;
+  bool ok = ensure(h, h->bGV, cap * sizeof(int4), n * sizeof(int4)) &&
+            ensure(h, h->bGflag, cap, n) && ensure(h, h->bGmust, cap, n) &&
+            ensure(h, h->bCandG, cap, 0);
+  if (!ok) return false;
+  h->capG = cap;
+  bind(h);
+  return true;
+}
+// subsegment hash: rebuild with a capacity of at least 4x the keys it will hold
+bool rebuild_hash(cdr_handle* h, int keys) {
+  size_t cap = 64;
+  while (cap < (size_t)keys * 4) cap <<= 1;
+  if (!ensure(h, h->bHK, cap * 8) || !ensure(h, h->bHV, cap * 4)) return false;
+  bind(h);
+  h->m.hmask = (int)cap - 1;
+  launch_hash_clear(h->m, h->stream);
+  launch_hash_insert_subsegs(h->m, 0, h->m.nG, h->stream);
+  h->hcount = h->m.nG;
+  return true;
+}
+
+// ------------------------------------------------------------- small kernels
+__global__ void k_gather_u64(const unsigned long long* src, const int* perm, int n,
+                             unsigned long long* dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = src[perm[i]];
+}
+__global__ void k_gather_u32(const unsigned* src, const int* perm, int n, unsigned* dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = src[perm[i]];
+}
+__global__ void k_iota(int* a, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+__global__ void k_fill_int(int* a, int n, int v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
+}
+__global__ void k_xyz_to_v4(const double* xyz, int n, V4* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = make_v4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.0);
+}
+__global__ void k_init_subsegs(int4* GV, uint8_t* Gf, uint8_t* Gm, const int* segs,
+                               const int* sid, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    GV[i] = make_int4(segs[2 * i], segs[2 * i + 1], sid[i], -1);
+    Gf[i] = 0;
+    Gm[i] = 0;
+  }
+}
+__global__ void k_retry_flags(const int* status, int n, int* flag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    flag[i] = status[i] == OUT_RETRY ? 1 : 0;
+}
+__global__ void k_scatter_slab2(const int* list2, int n2, int* slab2_of) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n2; j += gridDim.x * blockDim.x)
+    slab2_of[list2[j]] = j;
+}
+struct Int4Sum {
+  __host__ __device__ int4 operator()(const int4& a, const int4& b) const {
+    return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+  }
+};
+__global__ void k_cand_keys(DevMesh m, int cls, const int* cand, int n, int4* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int e = cand[i];
+    int4 k = make_int4(-1, -1, -1, -1);
+    if (cls == CLS_SUBSEG) {
+      int4 G = m.GV[e];
+      k.x = min(G.x, G.y);
+      k.y = max(G.x, G.y);
+    } else if (cls == CLS_SUBFACE) {
+      int4 S = m.SV[e];
+      int a = S.x, b = S.y, c = S.z, t;
+      if (a > b) { t = a; a = b; b = t; }
+      if (b > c) { t = b; b = c; c = t; }
+      if (a > b) { t = a; a = b; b = t; }
+      k = make_int4(a, b, c, -1);
+    } else if (cls == CLS_TET) {
+      int4 v = m.T[e].v;
+      int s[4] = {v.x & kVidMask, v.y & kVidMask, v.z & kVidMask, v.w & kVidMask};
+      for (int a = 1; a < 4; ++a)
+        for (int b = a; b > 0 && s[b - 1] > s[b]; --b) {
+          int t = s[b];
+          s[b] = s[b - 1];
+          s[b - 1] = t;
+        }
+      k = make_int4(s[0], s[1], s[2], s[3]);
+    } else {
+      k.x = e;
+    }
+    out[i] = k;
+  }
+}
+// points: one candidate per located tetrahedron (the smallest rank) this round
+__global__ void k_point_prefilter(DevMesh m, int* status, const int* loc, int n,
+                                  unsigned long long epoch, int pass) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (status[i] != OUT_OK) continue;
+    unsigned long long mk = (epoch << 32) | (unsigned)i;
+    if (pass == 0) atomicMin(&m.Tmark[loc[i]], mk);
+    else if (m.Tmark[loc[i]] != mk) status[i] = OUT_UNSPL | (RS_NONE << 8) | (1 << 16);
+  }
+}
+__global__ void k_point_flags(const int* state, int n, int* flag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    flag[i] = state[i] == 0 ? 1 : 0;
+}
+// a deferred point (bit 16 of its status) is neither marked nor counted
+__global__ void k_undefer(int* status, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (status[i] & (1 << 16)) status[i] = OUT_REJECT | (RS_NONE << 8);
+}
+
+inline int gridn(long n, int b = 256) {
+  long g = (n + b - 1) / b;
+  return (int)std::max(1L, std::min(g, 152L * 32));
+}
+
+// CUB temporary storage
+bool tmp_ensure(cdr_handle* h, size_t bytes) { return ensure(h, h->bTmp, bytes); }
+
+// lexicographic sort of (hi, lo): sorted keys and the permutation of original
+// indices (two stable radix passes, low key first)
+bool sort2(cdr_handle* h, const unsigned long long* hi, const unsigned* lo, int n,
+           unsigned long long* hi_s, unsigned* lo_s, int* perm) {
+  Buf scr;
+  if (!ensure(h, scr, (size_t)n * 20 + 256)) return false;
+  char* base = ptr<char>(scr);
+  unsigned long long* hi1 = reinterpret_cast<unsigned long long*>(base);
+  int* idx0 = reinterpret_cast<int*>(base + (size_t)n * 8);
+  unsigned* lo1 = reinterpret_cast<unsigned*>(base + (size_t)n * 12);
+  int* perm1 = reinterpret_cast<int*>(base + (size_t)n * 16);
+  k_iota<<<gridn(n), 256, 0, h->stream>>>(idx0, n);
+  size_t tb = 0, tb2 = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tb, lo, lo1, idx0, perm1, n, 0, 32, h->stream);
+  cub::DeviceRadixSort::SortPairs(nullptr, tb2, hi1, hi_s, perm1, perm, n, 0, 64, h->stream);
+  if (!tmp_ensure(h, std::max(tb, tb2))) return false;
+  tb = h->bTmp.bytes;
+  cub::DeviceRadixSort::SortPairs(h->bTmp.p, tb, lo, lo1, idx0, perm1, n, 0, 32, h->stream);
+  k_gather_u64<<<gridn(n), 256, 0, h->stream>>>(hi, perm1, n, hi1);
+  tb = h->bTmp.bytes;
+  cub::DeviceRadixSort::SortPairs(h->bTmp.p, tb, hi1, hi_s, perm1, perm, n, 0, 64, h->stream);
+  k_gather_u32<<<gridn(n), 256, 0, h->stream>>>(lo, perm, n, lo_s);
+  cudaStreamSynchronize(h->stream);
+  dfree(h, scr);
+  return cuda_status(h) == 0;
+}
+
+// warp-aggregated counts of nonzero bytes in up to three arrays
+__global__ void k_count3(const unsigned char* a, int na, const unsigned char* b, int nb,
+                         const unsigned char* c, int nc, unsigned long long* out) {
+  int tot = na + nb + nc;
+  int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < tot; base += stride) {
+    int i = base + threadIdx.x;
+    int w = -1;
+    if (i < na) w = a[i] ? 0 : -1;
+    else if (i < na + nb) w = b[i - na] ? 1 : -1;
+    else if (i < tot) w = c[i - na - nb] ? 2 : -1;
+    for (int k = 0; k < 3; ++k) {
+      unsigned bal = __ballot_sync(0xffffffffu, w == k);
+      if (bal && (int)(threadIdx.x & 31) == __ffs(bal) - 1)
+        atomicAdd(&out[k], (unsigned long long)__popc(bal));
+    }
+  }
+}
+__global__ void k_count_bad(DevMesh m, unsigned long long* out) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x)
+    if ((m.Tflag[t] & (F_DEAD | F_BAD)) == F_BAD) atomicAdd(out, 1ULL);
+}
+// per-candidate report sizes: cavity size when the cavity is complete
+__global__ void k_report_sizes(DevRound r, int* ncav, int* nbnd, int* nfcav) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
+    int j = r.slab2_of ? r.slab2_of[i] : -1;
+    const int* slab = j >= 0 ? r.slab2 + (size_t)j * SlabLayout<Tier2>::STRIDE
+                             : r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
+    int st = r.status[i];
+    int oc = st & 0xff, rs = (st >> 8) & 0xff;
+    bool full = oc == OUT_OK || (oc == OUT_REJECT && rs == RS_ENCROACH) || rs == RS_GUARD ||
+                rs == RS_STARDEL || (rs == RS_ENCROACH_UNSPL && slab[0] > 0);
+    ncav[i] = full ? slab[0] : 0;
+    nbnd[i] = full ? slab[1] : 0;
+    nfcav[i] = full ? slab[2] : 0;
+  }
+}
+
+unsigned next_epoch(cdr_handle* h) { return 0xFFFFFFFFu - (++h->epoch); }
+
+bool ensure_round(cdr_handle* h, int n) {
+  if (n <= h->capR && h->bCand.p) return true;
+  int c = std::max(n, 1024);
+  bool ok = ensure(h, h->bCand, (size_t)c * 4) && ensure(h, h->bCand2, (size_t)c * 4) &&
+            ensure(h, h->bKeys, (size_t)c * 8) && ensure(h, h->bKeys2, (size_t)c * 8) &&
+            ensure(h, h->bSp, (size_t)c * sizeof(V4)) && ensure(h, h->bLoc, (size_t)c * 4) &&
+            ensure(h, h->bStatus, (size_t)c * 4) && ensure(h, h->bSurv, (size_t)c * 4) &&
+            ensure(h, h->bCounts, (size_t)c * 16) && ensure(h, h->bOffs, (size_t)(c + 1) * 16) &&
+            ensure(h, h->bSlab1, (size_t)c * SlabLayout<Tier1>::STRIDE * 4) &&
+            ensure(h, h->bSlab2of, (size_t)c * 4) && ensure(h, h->bList2, (size_t)c * 4) &&
+            ensure(h, h->bCkey, (size_t)c * 16) && ensure(h, h->bStats, 8 * 16) &&
+            ensure(h, h->bErr, 64) && ensure(h, h->bI32, (size_t)(c + 1) * 4);
+  if (ok) h->capR = c;
+  return ok;
+}
+
+DevRound make_round(cdr_handle* h, int cls, int n, double B) {
+  DevRound r{};
+  r.cls = cls;
+  r.n = n;
+  r.cand = ptr<int>(h->bCand2);
+  r.given = ptr<double>(h->bPts);
+  r.loc = ptr<int>(h->bLoc);
+  r.sp = ptr<V4>(h->bSp);
+  r.status = ptr<int>(h->bStatus);
+  r.slab1 = ptr<int>(h->bSlab1);
+  r.slab2 = ptr<int>(h->bSlab2);
+  r.slab2_of = ptr<int>(h->bSlab2of);
+  r.ws2 = ptr<int>(h->bWs2);
+  r.n2 = 0;
+  r.list2 = ptr<int>(h->bList2);
+  r.survived = ptr<int>(h->bSurv);
+  r.counts = ptr<int4>(h->bCounts);
+  r.offs = ptr<int4>(h->bOffs);
+  r.point_state = ptr<int>(h->bPstate);
+  r.stats = ptr<unsigned long long>(h->bStats);
+  r.B = B;
+  return r;
+}
+
+struct RoundOut {
+  int cls = -1;
+  long long cand = 0, ins = 0, rej = 0, unspl = 0, blasted = 0;
+};
+
+// count the live tetrahedra; compact when more than half are dead
+int maybe_compact(cdr_handle* h, bool force) {
+  DevMesh& m = h->m;
+  if (!force && m.nT < (1 << 19)) return 0;
+  Buf alive, newid;
+  if (!ensure(h, alive, (size_t)m.nT * 4 + 64) || !ensure(h, newid, (size_t)(m.nT + 1) * 4 + 64))
+    return CDR_ERR_OOM;
+  launch_compact_flags(m, ptr<int>(alive), h->stream);
+  size_t tb = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, tb, ptr<int>(alive), ptr<int>(newid), m.nT, h->stream);
+  if (!tmp_ensure(h, tb)) return CDR_ERR_OOM;
+  tb = h->bTmp.bytes;
+  cub::DeviceScan::ExclusiveSum(h->bTmp.p, tb, ptr<int>(alive), ptr<int>(newid), m.nT, h->stream);
+  int last[2] = {0, 0};
+  cudaMemcpyAsync(&last[0], ptr<int>(newid) + m.nT - 1, 4, cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(&last[1], ptr<int>(alive) + m.nT - 1, 4, cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  int live = last[0] + last[1];
+  if (!force && live * 2 > m.nT) {
+    dfree(h, alive);
+    dfree(h, newid);
+    return 0;
+  }
+  Buf T2, TS2, F2;
+  if (!ensure(h, T2, (size_t)h->capT * sizeof(TetRec)) ||
+      !ensure(h, TS2, (size_t)h->capT * sizeof(int4)) || !ensure(h, F2, (size_t)h->capT))
+    return CDR_ERR_OOM;
+  launch_compact_move(m, ptr<int>(newid), ptr<TetRec>(T2), ptr<int4>(TS2), ptr<uint8_t>(F2),
+                      h->dt_mode ? ptr<int>(h->bHint) : nullptr, h->dt_mode ? h->npts : 0,
+                      h->stream);
+  launch_compact_fix(m, ptr<int>(newid), h->stream);
+  cudaStreamSynchronize(h->stream);
+  std::swap(h->bT, T2);
+  std::swap(h->bTS, TS2);
+  std::swap(h->bTflag, F2);
+  dfree(h, T2);
+  dfree(h, TS2);
+  dfree(h, F2);
+  m.nT = live;
+  bind(h);
+  cudaMemsetAsync(h->bTmark.p, 0xff, (size_t)h->capT * 8, h->stream);
+  cudaMemsetAsync(h->bTfwd.p, 0xff, (size_t)h->capT * 4, h->stream);
+  dfree(h, alive);
+  dfree(h, newid);
+  return cuda_status(h);
+}
+
+// the shared body of a round once the ordered candidate list is in bCand2
+int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
+  DevMesh& m = h->m;
+  cudaStream_t s = h->stream;
+  DevRound r = make_round(h, cls, n, B);
+  cudaMemsetAsync(h->bStats.p, 0, 8 * 16, s);
+  k_fill_int<<<gridn(n), 256, 0, s>>>(ptr<int>(h->bSlab2of), n, -1);
+  k_cand_keys<<<gridn(n), 256, 0, s>>>(m, cls, r.cand, n, ptr<int4>(h->bCkey));
+  launch_split(m, r, s);
+  if (cls == CLS_POINT)
+    launch_follow_fwd(m, ptr<int>(h->bHint), ptr<int>(h->bPstate), h->npts, s);
+  launch_locate(m, r, ptr<int>(h->bHint), s);
+  if (cls == CLS_POINT) {
+    unsigned long long e0 = next_epoch(h);
+    k_point_prefilter<<<gridn(n), 256, 0, s>>>(m, r.status, r.loc, n, e0, 0);
+    k_point_prefilter<<<gridn(n), 256, 0, s>>>(m, r.status, r.loc, n, e0, 1);
+  }
+  r.epoch = next_epoch(h);
+  launch_grow1(m, r, s);
+  // tier 2 for regions that did not fit
+  {
+    int* flag = ptr<int>(h->bSurv);  // scratch before selection
+    k_retry_flags<<<gridn(n), 256, 0, s>>>(r.status, n, flag);
+    size_t tb = 0;
+    int* nsel = ptr<int>(h->bErr) + 4;
+    cub::DeviceSelect::Flagged(nullptr, tb, thrust::counting_iterator<int>(0), flag,
+                               ptr<int>(h->bList2), nsel, n, s);
+    if (!tmp_ensure(h, tb)) return CDR_ERR_OOM;
+    tb = h->bTmp.bytes;
+    cub::DeviceSelect::Flagged(h->bTmp.p, tb, thrust::counting_iterator<int>(0), flag,
+                               ptr<int>(h->bList2), nsel, n, s);
+    int n2 = 0;
+    cudaMemcpyAsync(&n2, nsel, 4, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (n2 > 0) {
+      const size_t stride2 = SlabLayout<Tier2>::STRIDE;
+      int warps = std::min(n2, 152 * 4);
+      if (!ensure(h, h->bSlab2, (size_t)n2 * stride2 * 4) ||
+          !ensure(h, h->bWs2, (size_t)warps * Tier2::HCAP * 4))
+        return CDR_ERR_OOM;
+      r.slab2 = ptr<int>(h->bSlab2);
+      r.ws2 = ptr<int>(h->bWs2);
+      r.n2 = n2;
+      k_scatter_slab2<<<gridn(n2), 256, 0, s>>>(r.list2, n2, r.slab2_of);
+      launch_grow2(m, r, warps, s);
+    }
+    h->lastN2 = n2;
+  }
+  if (cls == CLS_POINT) k_undefer<<<gridn(n), 256, 0, s>>>(r.status, n);
+  launch_select(m, r, s);
+  // allocation: exclusive scan of (verts, tets, subfaces, subsegs)
+  {
+    size_t tb = 0;
+    cub::DeviceScan::ExclusiveScan(nullptr, tb, r.counts, ptr<int4>(h->bOffs), Int4Sum(),
+                                   make_int4(0, 0, 0, 0), n, s);
+    if (!tmp_ensure(h, tb)) return CDR_ERR_OOM;
+    tb = h->bTmp.bytes;
+    cub::DeviceScan::ExclusiveScan(h->bTmp.p, tb, r.counts, ptr<int4>(h->bOffs), Int4Sum(),
+                                   make_int4(0, 0, 0, 0), n, s);
+  }
+  int4 lastOff, lastCnt;
+  unsigned long long st[ST_COUNT];
+  cudaMemcpyAsync(&lastOff, ptr<int4>(h->bOffs) + n - 1, 16, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&lastCnt, r.counts + n - 1, 16, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(st, h->bStats.p, sizeof(st), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (cuda_status(h)) return h->err;
+  int4 tot = make_int4(lastOff.x + lastCnt.x, lastOff.y + lastCnt.y, lastOff.z + lastCnt.z,
+                       lastOff.w + lastCnt.w);
+  if (!grow_verts(h, m.nV + tot.x) || !grow_tets(h, m.nT + tot.y) ||
+      !grow_subfaces(h, m.nS + tot.z) || !grow_subsegs(h, m.nG + tot.w))
+    return h->err ? h->err : CDR_ERR_OOM;
+  if ((size_t)(h->hcount + 2 * tot.w) * 2 > (size_t)m.hmask + 1) {
+    if (!rebuild_hash(h, (m.nG + 2 * tot.w) * 2)) return CDR_ERR_OOM;
+  }
+  r = make_round(h, cls, n, B);  // rebind after any reallocation
+  r.epoch = 0;
+  r.n2 = h->lastN2;
+  launch_insert(m, r, ptr<int>(h->bHint), s);
+  m.nV += cls == CLS_POINT ? 0 : tot.x;
+  m.nT += tot.y;
+  m.nS += tot.z;
+  m.nG += tot.w;
+  h->hcount += 2 * tot.w;
+  h->lastN = n;
+  h->lastCls = cls;
+  if (ro) {
+    ro->cls = cls;
+    ro->cand = n;
+    ro->ins = (long long)st[ST_SURV];
+    ro->rej = (long long)st[ST_REJECT];
+    ro->unspl = (long long)st[ST_UNSPL];
+    ro->blasted = (long long)st[ST_OK];
+  }
+  if (exact_overflow_flag(s, true)) return set_err(h, CDR_ERR_INTERNAL);
+  {
+    unsigned long long it = 0;
+    cudaMemcpyAsync(&it, ptr<unsigned long long>(h->bStats) + ST_ITER, 8, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (it) return set_err(h, CDR_ERR_INTERNAL);  // an invariant check failed on the device
+  }
+  return cuda_status(h);
+}
+
+// order candidates in bCand[0..n) by priority into bCand2
+int order_candidates(cdr_handle* h, int cls, int n) {
+  cudaStream_t s = h->stream;
+  launch_prio(h->m, cls, ptr<int>(h->bCand), n, ptr<unsigned long long>(h->bKeys), s);
+  size_t tb = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tb, ptr<unsigned long long>(h->bKeys),
+                                  ptr<unsigned long long>(h->bKeys2), ptr<int>(h->bCand),
+                                  ptr<int>(h->bCand2), n, 0, 64, s);
+  if (!tmp_ensure(h, tb)) return CDR_ERR_OOM;
+  tb = h->bTmp.bytes;
+  cub::DeviceRadixSort::SortPairs(h->bTmp.p, tb, ptr<unsigned long long>(h->bKeys),
+                                  ptr<unsigned long long>(h->bKeys2), ptr<int>(h->bCand),
+                                  ptr<int>(h->bCand2), n, 0, 64, s);
+  launch_tiefix(h->m, cls, ptr<unsigned long long>(h->bKeys2), ptr<int>(h->bCand2), n, s);
+  return cuda_status(h);
+}
+
+int refine_round(cdr_handle* h, double B, RoundOut* ro) {
+  DevMesh& m = h->m;
+  cudaStream_t s = h->stream;
+  if (B != h->lastB) {
+    launch_recompute_bad(m, B, s);
+    h->lastB = B;
+  }
+  int st = maybe_compact(h, false);
+  if (st) return st;
+  if (!ensure_round(h, 1024)) return CDR_ERR_OOM;
+  cudaMemsetAsync(h->bErr.p, 0, 64, s);
+  launch_classify(m, ptr<uint8_t>(h->bCandS), ptr<uint8_t>(h->bCandG), ptr<uint8_t>(h->bCandT),
+                  ptr<int>(h->bErr), s);
+  unsigned long long* cnt = ptr<unsigned long long>(h->bStats);
+  cudaMemsetAsync(cnt, 0, 24, s);
+  k_count3<<<gridn((long)m.nG + m.nS + m.nT), 256, 0, s>>>(
+      ptr<uint8_t>(h->bCandG), m.nG, ptr<uint8_t>(h->bCandS), m.nS, ptr<uint8_t>(h->bCandT), m.nT,
+      cnt);
+  unsigned long long c3[3];
+  int cerr = 0;
+  cudaMemcpyAsync(c3, cnt, 24, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&cerr, h->bErr.p, 4, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (cuda_status(h)) return h->err;
+  if (cerr) return set_err(h, CDR_ERR_INTERNAL);
+  int cls = -1;
+  for (int c = 0; c < 3; ++c)
+    if (c3[c] > 0) {
+      cls = c;
+      break;
+    }
+  if (ro) *ro = RoundOut();
+  if (cls < 0) return CDR_OK;
+  int n = (int)c3[cls];
+  if (!ensure_round(h, n)) return CDR_ERR_OOM;
+  const uint8_t* flags = cls == 0 ? ptr<uint8_t>(h->bCandG)
+                                  : (cls == 1 ? ptr<uint8_t>(h->bCandS) : ptr<uint8_t>(h->bCandT));
+  int nall = cls == 0 ? m.nG : (cls == 1 ? m.nS : m.nT);
+  size_t tb = 0;
+  int* nsel = ptr<int>(h->bErr) + 4;
+  cub::DeviceSelect::Flagged(nullptr, tb, thrust::counting_iterator<int>(0), flags,
+                             ptr<int>(h->bCand), nsel, nall, s);
+  if (!tmp_ensure(h, tb)) return CDR_ERR_OOM;
+  tb = h->bTmp.bytes;
+  cub::DeviceSelect::Flagged(h->bTmp.p, tb, thrust::counting_iterator<int>(0), flags,
+                             ptr<int>(h->bCand), nsel, nall, s);
+  st = order_candidates(h, cls, n);
+  if (st) return st;
+  return round_core(h, cls, n, B, ro);
+}
+
+int count_bad(cdr_handle* h, long long* out) {
+  if (!ensure(h, h->bStats, 8 * 16)) return CDR_ERR_OOM;
+  unsigned long long* c = ptr<unsigned long long>(h->bStats) + 8;
+  cudaMemsetAsync(c, 0, 8, h->stream);
+  k_count_bad<<<gridn(h->m.nT), 256, 0, h->stream>>>(h->m, c);
+  unsigned long long v = 0;
+  cudaMemcpyAsync(&v, c, 8, cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  *out = (long long)v;
+  return cuda_status(h);
+}
+
+int live_count(cdr_handle* h, const uint8_t* flag, int n, int* out) {
+  *out = 0;
+  if (n == 0) return 0;
+  Buf b;
+  if (!ensure(h, b, (size_t)n * 4 + 64) || !ensure(h, h->bErr, 64)) return CDR_ERR_OOM;
+  launch_live_flags(flag, n, ptr<int>(b), h->stream);
+  int* sum = ptr<int>(h->bErr) + 8;
+  size_t tb = 0;
+  cub::DeviceReduce::Sum(nullptr, tb, ptr<int>(b), sum, n, h->stream);
+  if (!tmp_ensure(h, tb)) return CDR_ERR_OOM;
+  tb = h->bTmp.bytes;
+  cub::DeviceReduce::Sum(h->bTmp.p, tb, ptr<int>(b), sum, n, h->stream);
+  cudaMemcpyAsync(out, sum, 4, cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  dfree(h, b);
+  return cuda_status(h);
+}
+
+// dense positions of live entries (exclusive scan of live flags)
+bool live_positions(cdr_handle* h, const uint8_t* flag, int n, Buf& pos) {
+  Buf b;
+  if (!ensure(h, b, (size_t)n * 4 + 64) || !ensure(h, pos, (size_t)n * 4 + 64)) return false;
+  launch_live_flags(flag, n, ptr<int>(b), h->stream);
+  size_t tb = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, tb, ptr<int>(b), ptr<int>(pos), n, h->stream);
+  if (!tmp_ensure(h, tb)) return false;
+  tb = h->bTmp.bytes;
+  cub::DeviceScan::ExclusiveSum(h->bTmp.p, tb, ptr<int>(b), ptr<int>(pos), n, h->stream);
+  cudaStreamSynchronize(h->stream);
+  dfree(h, b);
+  return true;
+}
+
+}  // namespace
+
+// ===================================================================== API
+extern "C" {
+
+const char* cdr_status_string(int s) {
+  switch (s) {
+    case CDR_OK: return "ok";
+    case CDR_ROUND_LIMIT: return "round limit reached with work left";
+    case CDR_ERR_INVALID_INPUT: return "invalid input";
+    case CDR_ERR_OOM: return "out of device memory";
+    case CDR_ERR_CUDA: return "CUDA error";
+    case CDR_ERR_ITER_LIMIT: return "a bounded device loop gave up";
+    case CDR_ERR_INTERNAL: return "internal error (exact-arithmetic capacity or invariant)";
+  }
+  return "unknown status";
+}
+
+int cdr_device_arch(void) { return 103; }
+
+void cdr_destroy(cdr_handle* h) {
+  if (!h) return;
+  Buf* all[] = {&h->bV, &h->bT, &h->bTS, &h->bTflag, &h->bTmark, &h->bTfwd, &h->bSV, &h->bSN,
+                &h->bSflag, &h->bSmust, &h->bSmark, &h->bGV, &h->bGflag, &h->bGmust, &h->bFQ,
+                &h->bHK, &h->bHV, &h->bCandS, &h->bCandG, &h->bCandT, &h->bCand, &h->bCand2,
+                &h->bKeys, &h->bKeys2, &h->bSp, &h->bLoc, &h->bStatus, &h->bSurv, &h->bCounts,
+                &h->bOffs, &h->bSlab1, &h->bSlab2of, &h->bList2, &h->bSlab2, &h->bWs2, &h->bCkey,
+                &h->bTmp, &h->bStats, &h->bErr, &h->bI32, &h->bPts, &h->bHint, &h->bPstate};
+  for (Buf* b : all) dfree(h, *b);
+  for (Buf& b : h->ck) dfree(h, b);
+  cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+}  // extern "C"
+
+namespace {
+
+// facet reference points: the facet's first listed triangle's first vertex
+// moved along the dominant axis of that triangle's normal by the smallest power
+// of two >= 4x the largest bounding-box extent
+void facet_refs(const cdr_mesh_in* in, std::vector<V4>& fq) {
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < in->n_verts; ++i)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], in->xyz[3 * i + k]);
+      hi[k] = std::max(hi[k], in->xyz[3 * i + k]);
+    }
+  double ex = 0.0;
+  for (int k = 0; k < 3; ++k) ex = std::max(ex, hi[k] - lo[k]);
+  double s = 1.0;
+  while (s < 4.0 * ex) s *= 2.0;
+  while (s * 0.5 >= 4.0 * ex && s > 1e-300) s *= 0.5;
+  fq.assign(in->n_facets, make_v4(0, 0, 0, 0));
+  std::vector<char> done(in->n_facets, 0);
+  for (int i = 0; i < in->n_tris; ++i) {
+    int f = in->facet_id[i];
+    if (done[f]) continue;
+    done[f] = 1;
+    const double* A = in->xyz + 3 * in->tris[3 * i];
+    const double* B = in->xyz + 3 * in->tris[3 * i + 1];
+    const double* C = in->xyz + 3 * in->tris[3 * i + 2];
+    double ux = B[0] - A[0], uy = B[1] - A[1], uz = B[2] - A[2];
+    double vx = C[0] - A[0], vy = C[1] - A[1], vz = C[2] - A[2];
+    double n[3] = {uy * vz - uz * vy, uz * vx - ux * vz, ux * vy - uy * vx};
+    int kk = 0;
+    for (int k = 1; k < 3; ++k)
+      if (std::fabs(n[k]) > std::fabs(n[kk])) kk = k;
+    double q[3] = {A[0], A[1], A[2]};
+    q[kk] = A[kk] + s;
+    fq[f] = make_v4(q[0], q[1], q[2], 0.0);
+  }
+}
+
+double default_guard2(const double* xyz, int n) {
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], xyz[3 * i + k]);
+      hi[k] = std::max(hi[k], xyz[3 * i + k]);
+    }
+  double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+  double diag2 = dx * dx + dy * dy + dz * dz;
+  return diag2 * 1e-18;
+}
+
+// shared by cdr_create and cdr_delaunay_box: allocate, upload vertices and
+// tetrahedra, build neighbours from sorted face keys. The sorted keys stay in
+// bKeys / bCand2 / bI32 for subface labelling.
+int build_mesh(cdr_handle* h, const double* xyz, int nv, const int* tets, int nt, int capV,
+               int capT) {
+  DevMesh& m = h->m;
+  h->capV = h->capT = 0;
+  if (!grow_verts(h, capV) || !grow_tets(h, capT)) return h->err ? h->err : CDR_ERR_OOM;
+  Buf tmp;
+  if (!ensure(h, tmp, (size_t)std::max((size_t)nv * 24, (size_t)nt * 16) + 64)) return CDR_ERR_OOM;
+  cudaMemcpyAsync(tmp.p, xyz, (size_t)nv * 24, cudaMemcpyHostToDevice, h->stream);
+  k_xyz_to_v4<<<gridn(nv), 256, 0, h->stream>>>(ptr<double>(tmp), nv, m.V);
+  m.nV = nv;
+  cudaStreamSynchronize(h->stream);
+  cudaMemcpyAsync(tmp.p, tets, (size_t)nt * 16, cudaMemcpyHostToDevice, h->stream);
+  launch_init_tets(m, ptr<int4>(tmp), nt, h->stream);
+  m.nT = nt;
+  cudaStreamSynchronize(h->stream);
+  dfree(h, tmp);
+  int nf = 4 * nt;
+  Buf bhi, blo;
+  if (!ensure(h, bhi, (size_t)nf * 8 + 64) || !ensure(h, blo, (size_t)nf * 4 + 64) ||
+      !ensure(h, h->bKeys, (size_t)nf * 8 + 64) || !ensure(h, h->bCand2, (size_t)nf * 4 + 64) ||
+      !ensure(h, h->bI32, (size_t)nf * 4 + 64))
+    return CDR_ERR_OOM;
+  launch_face_keys(m, ptr<unsigned long long>(bhi), ptr<unsigned>(blo), nullptr, h->stream);
+  if (!sort2(h, ptr<unsigned long long>(bhi), ptr<unsigned>(blo), nf,
+             ptr<unsigned long long>(h->bKeys), ptr<unsigned>(h->bCand2), ptr<int>(h->bI32)))
+    return h->err ? h->err : CDR_ERR_OOM;
+  dfree(h, bhi);
+  dfree(h, blo);
+  if (!ensure(h, h->bErr, 64)) return CDR_ERR_OOM;
+  cudaMemsetAsync(h->bErr.p, 0, 64, h->stream);
+  launch_pair_faces(m, ptr<unsigned long long>(h->bKeys), ptr<unsigned>(h->bCand2),
+                    ptr<int>(h->bI32), nf, ptr<int>(h->bErr), h->stream);
+  return cuda_status(h);
+}
+
+}  // namespace
+
+extern "C" int cdr_create(const cdr_mesh_in* in, const cdr_options* opt, const cdr_allocator* alloc,
+                          void* stream, cdr_handle** out) {
+  if (!in || !out) return CDR_ERR_INVALID_INPUT;
+  *out = nullptr;
+  if (in->n_verts < 4 || in->n_tets < 1 || in->n_segs < 0 || in->n_tris < 0 || in->n_facets < 0 ||
+      !in->xyz || !in->tets || (in->n_segs && (!in->segs || !in->seg_id)) ||
+      (in->n_tris && (!in->tris || !in->facet_id)) || in->n_verts >= kMaxVerts ||
+      in->n_tets >= kMaxTets / 8)
+    return CDR_ERR_INVALID_INPUT;
+  for (long i = 0; i < 4L * in->n_tets; ++i)
+    if (in->tets[i] < 0 || in->tets[i] >= in->n_verts) return CDR_ERR_INVALID_INPUT;
+  for (long i = 0; i < 2L * in->n_segs; ++i)
+    if (in->segs[i] < 0 || in->segs[i] >= in->n_verts) return CDR_ERR_INVALID_INPUT;
+  for (long i = 0; i < 3L * in->n_tris; ++i)
+    if (in->tris[i] < 0 || in->tris[i] >= in->n_verts) return CDR_ERR_INVALID_INPUT;
+  for (int i = 0; i < in->n_tris; ++i)
+    if (in->facet_id[i] < 0 || in->facet_id[i] >= in->n_facets) return CDR_ERR_INVALID_INPUT;
+  for (long i = 0; i < 3L * in->n_verts; ++i)
+    if (!std::isfinite(in->xyz[i])) return CDR_ERR_INVALID_INPUT;
+
+  cdr_handle* h = new (std::nothrow) cdr_handle();
+  if (!h) return CDR_ERR_OOM;
+  h->stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    h->alloc = *alloc;
+    h->has_alloc = true;
+  }
+  int rf = (opt && opt->reserve_factor > 0) ? opt->reserve_factor : 4;
+  h->m.walk_limit = (opt && opt->walk_limit > 0) ? opt->walk_limit : 100000;
+  h->m.guard2 = (opt && opt->guard2 > 0) ? opt->guard2 : default_guard2(in->xyz, in->n_verts);
+  h->m.nF = in->n_facets;
+
+  int st = build_mesh(h, in->xyz, in->n_verts, in->tets, in->n_tets,
+                      std::max(in->n_verts * rf, 1024), std::max(in->n_tets * rf, 4096));
+  if (st) {
+    cdr_destroy(h);
+    return st;
+  }
+  DevMesh& m = h->m;
+  // subsegments + hash
+  if (!grow_subsegs(h, std::max(in->n_segs * rf, 256)) ||
+      !grow_subfaces(h, std::max(in->n_tris * rf, 256))) {
+    cdr_destroy(h);
+    return CDR_ERR_OOM;
+  }
+  {
+    Buf tmp;
+    if (!ensure(h, tmp, (size_t)in->n_segs * 12 + 64)) {
+      cdr_destroy(h);
+      return CDR_ERR_OOM;
+    }
+    if (in->n_segs) {
+      cudaMemcpyAsync(tmp.p, in->segs, (size_t)in->n_segs * 8, cudaMemcpyHostToDevice, h->stream);
+      cudaMemcpyAsync(ptr<char>(tmp) + (size_t)in->n_segs * 8, in->seg_id, (size_t)in->n_segs * 4,
+                      cudaMemcpyHostToDevice, h->stream);
+      k_init_subsegs<<<gridn(in->n_segs), 256, 0, h->stream>>>(
+          m.GV, m.Gflag, m.Gmust, ptr<int>(tmp),
+          reinterpret_cast<int*>(ptr<char>(tmp) + (size_t)in->n_segs * 8), in->n_segs);
+    }
+    m.nG = in->n_segs;
+    cudaStreamSynchronize(h->stream);
+    dfree(h, tmp);
+    if (!rebuild_hash(h, std::max(in->n_segs * rf, 256))) {
+      cdr_destroy(h);
+      return CDR_ERR_OOM;
+    }
+    h->hcount = in->n_segs;
+  }
+  // facet reference points
+  {
+    std::vector<V4> fq;
+    if (in->facet_ref) {
+      fq.resize(in->n_facets);
+      for (int f = 0; f < in->n_facets; ++f)
+        fq[f] = make_v4(in->facet_ref[3 * f], in->facet_ref[3 * f + 1], in->facet_ref[3 * f + 2], 0);
+    } else {
+      facet_refs(in, fq);
+    }
+    if (!ensure(h, h->bFQ, std::max<size_t>(fq.size(), 1) * sizeof(V4))) {
+      cdr_destroy(h);
+      return CDR_ERR_OOM;
+    }
+    bind(h);
+    if (!fq.empty())
+      cudaMemcpyAsync(h->bFQ.p, fq.data(), fq.size() * sizeof(V4), cudaMemcpyHostToDevice,
+                      h->stream);
+    cudaStreamSynchronize(h->stream);
+  }
+  // subfaces: label faces, then facet adjacency
+  {
+    int ns = in->n_tris;
+    Buf tris;
+    if (!ensure(h, tris, (size_t)ns * 16 + 64)) {
+      cdr_destroy(h);
+      return CDR_ERR_OOM;
+    }
+    std::vector<int4> ht(ns);
+    for (int i = 0; i < ns; ++i)
+      ht[i] = make_int4(in->tris[3 * i], in->tris[3 * i + 1], in->tris[3 * i + 2], in->facet_id[i]);
+    if (ns) cudaMemcpyAsync(tris.p, ht.data(), (size_t)ns * 16, cudaMemcpyHostToDevice, h->stream);
+    m.nS = ns;
+    if (ns)
+      launch_label_subfaces(m, ptr<int4>(tris), ns, ptr<unsigned long long>(h->bKeys),
+                            ptr<unsigned>(h->bCand2), ptr<int>(h->bI32), 4 * m.nT,
+                            ptr<int>(h->bErr), h->stream);
+    cudaStreamSynchronize(h->stream);
+    dfree(h, tris);
+    dfree(h, h->bKeys);
+    dfree(h, h->bCand2);
+    dfree(h, h->bI32);
+    if (ns) {
+      int ne = 3 * ns;
+      Buf bhi, blo, shi, slo, sperm;
+      if (!ensure(h, bhi, (size_t)ne * 8 + 64) || !ensure(h, blo, (size_t)ne * 4 + 64) ||
+          !ensure(h, shi, (size_t)ne * 8 + 64) || !ensure(h, slo, (size_t)ne * 4 + 64) ||
+          !ensure(h, sperm, (size_t)ne * 4 + 64)) {
+        cdr_destroy(h);
+        return CDR_ERR_OOM;
+      }
+      launch_subface_edge_keys(m, ptr<unsigned long long>(bhi), ptr<unsigned>(blo), nullptr,
+                               h->stream);
+      if (!sort2(h, ptr<unsigned long long>(bhi), ptr<unsigned>(blo), ne,
+                 ptr<unsigned long long>(shi), ptr<unsigned>(slo), ptr<int>(sperm))) {
+        cdr_destroy(h);
+        return CDR_ERR_OOM;
+      }
+      launch_pair_subface_edges(m, ptr<unsigned long long>(shi), ptr<unsigned>(slo),
+                                ptr<int>(sperm), ne, ptr<int>(h->bErr), h->stream);
+      cudaStreamSynchronize(h->stream);
+      dfree(h, bhi);
+      dfree(h, blo);
+      dfree(h, shi);
+      dfree(h, slo);
+      dfree(h, sperm);
+    }
+  }
+  launch_mark_edges(m, h->stream);
+  launch_check_create(m, ptr<int>(h->bErr), h->stream);
+  int err = 0;
+  cudaMemcpyAsync(&err, h->bErr.p, 4, cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  if (cuda_status(h)) {
+    int e = h->err;
+    cdr_destroy(h);
+    return e;
+  }
+  if (err) {
+    cdr_destroy(h);
+    return CDR_ERR_INVALID_INPUT;
+  }
+  *out = h;
+  return CDR_OK;
+}
+
+// ===================================================================== API
+extern "C" {
+
+int cdr_round(cdr_handle* h, double B, int32_t* cls, cdr_stats* stats) {
+  if (!h || !(B > 0)) return CDR_ERR_INVALID_INPUT;
+  if (h->err) return h->err;
+  if (h->dt_mode) return CDR_ERR_INVALID_INPUT;
+  RoundOut ro;
+  int st = refine_round(h, B, &ro);
+  if (cls) *cls = st ? -1 : ro.cls;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->rounds = ro.cls >= 0 ? 1 : 0;
+    if (ro.cls >= 0) stats->rounds_by_class[ro.cls] = 1;
+    stats->candidates = ro.cand;
+    stats->steiner_inserted = ro.ins;
+    stats->rejected = ro.rej;
+    stats->blasted = ro.blasted;
+    stats->unsplittable = ro.unspl;
+    stats->n_verts = h->m.nV;
+  }
+  return st;
+}
+
+int cdr_refine(cdr_handle* h, double B, int32_t max_rounds, cdr_stats* stats) {
+  if (!h || !(B > 0) || max_rounds < 0) return CDR_ERR_INVALID_INPUT;
+  if (h->err) return h->err;
+  if (h->dt_mode) return CDR_ERR_INVALID_INPUT;
+  cdr_stats acc;
+  std::memset(&acc, 0, sizeof(acc));
+  int st = CDR_OK;
+  bool done = false;
+  for (int r = 0; r < max_rounds; ++r) {
+    RoundOut ro;
+    st = refine_round(h, B, &ro);
+    if (st) break;
+    if (ro.cls < 0) {
+      done = true;
+      break;
+    }
+    acc.rounds++;
+    acc.rounds_by_class[ro.cls]++;
+    acc.candidates += ro.cand;
+    acc.steiner_inserted += ro.ins;
+    acc.rejected += ro.rej;
+    acc.blasted += ro.blasted;
+    acc.unsplittable += ro.unspl;
+  }
+  if (!st && !done) st = CDR_ROUND_LIMIT;
+  if (stats) {
+    acc.n_verts = h->m.nV;
+    long long bad = 0;
+    if (count_bad(h, &bad) == 0) acc.n_bad_left = bad;
+    int nt = 0, ns = 0, ng = 0;
+    live_count(h, h->m.Tflag, h->m.nT, &nt);
+    live_count(h, h->m.Sflag, h->m.nS, &ns);
+    live_count(h, h->m.Gflag, h->m.nG, &ng);
+    acc.n_tets = nt;
+    acc.n_subfaces = ns;
+    acc.n_subsegs = ng;
+    *stats = acc;
+  }
+  return st;
+}
+
+int cdr_export_sizes(cdr_handle* h, cdr_sizes* out) {
+  if (!h || !out) return CDR_ERR_INVALID_INPUT;
+  int nt = 0, ns = 0, ng = 0;
+  int st = live_count(h, h->m.Tflag, h->m.nT, &nt);
+  if (!st) st = live_count(h, h->m.Sflag, h->m.nS, &ns);
+  if (!st) st = live_count(h, h->m.Gflag, h->m.nG, &ng);
+  out->n_verts = h->m.nV;
+  out->n_tets = nt;
+  out->n_subfaces = ns;
+  out->n_subsegs = ng;
+  out->n_facets = h->m.nF;
+  return st;
+}
+
+int cdr_export(cdr_handle* h, const cdr_mesh_out* out) {
+  if (!h || !out) return CDR_ERR_INVALID_INPUT;
+  DevMesh& m = h->m;
+  cudaStream_t s = h->stream;
+  if (out->xyz && m.nV > 0) {
+    std::vector<V4> v(m.nV);
+    cudaMemcpyAsync(v.data(), m.V, (size_t)m.nV * sizeof(V4), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (int i = 0; i < m.nV; ++i) {
+      out->xyz[3 * i] = v[i].x;
+      out->xyz[3 * i + 1] = v[i].y;
+      out->xyz[3 * i + 2] = v[i].z;
+    }
+  }
+  struct Part {
+    const uint8_t* flag;
+    int n;
+    int kind;
+  } parts[3] = {{m.Tflag, m.nT, 0}, {m.Sflag, m.nS, 1}, {m.Gflag, m.nG, 2}};
+  for (auto& p : parts) {
+    if (p.n == 0) continue;
+    Buf pos, dense, dflag;
+    if (!live_positions(h, p.flag, p.n, pos) || !ensure(h, dense, (size_t)p.n * 16 + 64) ||
+        !ensure(h, dflag, (size_t)p.n + 64))
+      return CDR_ERR_OOM;
+    if (p.kind == 0) launch_gather_tets(m, ptr<int>(pos), ptr<int4>(dense), ptr<uint8_t>(dflag), s);
+    if (p.kind == 1)
+      launch_gather_subfaces(m, ptr<int>(pos), ptr<int4>(dense), ptr<uint8_t>(dflag), s);
+    if (p.kind == 2)
+      launch_gather_subsegs(m, ptr<int>(pos), ptr<int4>(dense), ptr<uint8_t>(dflag), s);
+    int live = 0;
+    live_count(h, p.flag, p.n, &live);
+    std::vector<int4> d(live);
+    std::vector<uint8_t> f(live);
+    if (live) {
+      cudaMemcpyAsync(d.data(), dense.p, (size_t)live * 16, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(f.data(), dflag.p, (size_t)live, cudaMemcpyDeviceToHost, s);
+    }
+    cudaStreamSynchronize(s);
+    dfree(h, pos);
+    dfree(h, dense);
+    dfree(h, dflag);
+    for (int i = 0; i < live; ++i) {
+      if (p.kind == 0 && out->tets) {
+        out->tets[4 * i] = d[i].x;
+        out->tets[4 * i + 1] = d[i].y;
+        out->tets[4 * i + 2] = d[i].z;
+        out->tets[4 * i + 3] = d[i].w;
+      }
+      if (p.kind == 0 && out->tet_flag) out->tet_flag[i] = f[i];
+      if (p.kind == 1 && out->subfaces) {
+        out->subfaces[4 * i] = d[i].x;
+        out->subfaces[4 * i + 1] = d[i].y;
+        out->subfaces[4 * i + 2] = d[i].z;
+        out->subfaces[4 * i + 3] = d[i].w;
+      }
+      if (p.kind == 1 && out->subface_flag) out->subface_flag[i] = f[i];
+      if (p.kind == 2 && out->subsegs) {
+        out->subsegs[3 * i] = d[i].x;
+        out->subsegs[3 * i + 1] = d[i].y;
+        out->subsegs[3 * i + 2] = d[i].z;
+      }
+      if (p.kind == 2 && out->subseg_flag) out->subseg_flag[i] = f[i];
+    }
+  }
+  if (out->facet_ref && m.nF > 0) {
+    std::vector<V4> q(m.nF);
+    cudaMemcpyAsync(q.data(), m.FQ, (size_t)m.nF * sizeof(V4), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (int f = 0; f < m.nF; ++f) {
+      out->facet_ref[3 * f] = q[f].x;
+      out->facet_ref[3 * f + 1] = q[f].y;
+      out->facet_ref[3 * f + 2] = q[f].z;
+    }
+  }
+  return cuda_status(h);
+}
+
+int cdr_round_report(cdr_handle* h, int32_t* n_cand, int64_t* n_cav_total, int32_t* keys,
+                     double* pts, int32_t* outcome, int32_t* reason, int32_t* survived,
+                     int32_t* n_cav, int32_t* n_bnd, int32_t* n_fcav, int32_t* cav) {
+  if (!h || !n_cand || !n_cav_total) return CDR_ERR_INVALID_INPUT;
+  cudaStream_t s = h->stream;
+  int n = h->lastN;
+  *n_cand = n;
+  *n_cav_total = 0;
+  if (n == 0) return CDR_OK;
+  DevRound r = make_round(h, h->lastCls, n, 0.0);
+  r.n2 = h->lastN2;
+  Buf b;
+  if (!ensure(h, b, (size_t)n * 12 + 64)) return CDR_ERR_OOM;
+  int* dn = ptr<int>(b);
+  k_report_sizes<<<gridn(n), 256, 0, s>>>(r, dn, dn + n, dn + 2 * n);
+  std::vector<int> nc(3 * (size_t)n);
+  cudaMemcpyAsync(nc.data(), dn, (size_t)n * 12, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  long long tot = 0;
+  std::vector<int> offs(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    offs[i] = (int)tot;
+    tot += nc[i];
+  }
+  offs[n] = (int)tot;
+  *n_cav_total = tot;
+  std::vector<int4> k(n);
+  std::vector<V4> p(n);
+  std::vector<int> st(n), sv(n);
+  cudaMemcpyAsync(k.data(), h->bCkey.p, (size_t)n * 16, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(p.data(), h->bSp.p, (size_t)n * sizeof(V4), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(st.data(), h->bStatus.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(sv.data(), h->bSurv.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  for (int i = 0; i < n; ++i) {
+    if (keys) {
+      keys[4 * i] = k[i].x;
+      keys[4 * i + 1] = k[i].y;
+      keys[4 * i + 2] = k[i].z;
+      keys[4 * i + 3] = k[i].w;
+    }
+    if (pts) {
+      pts[3 * i] = p[i].x;
+      pts[3 * i + 1] = p[i].y;
+      pts[3 * i + 2] = p[i].z;
+    }
+    if (outcome) outcome[i] = st[i] & 0xff;
+    if (reason) reason[i] = (st[i] >> 8) & 0xff;
+    if (survived) survived[i] = sv[i];
+    if (n_cav) n_cav[i] = nc[i];
+    if (n_bnd) n_bnd[i] = nc[n + i];
+    if (n_fcav) n_fcav[i] = nc[2 * n + i];
+  }
+  if (cav && tot > 0) {
+    Buf doffs, dout;
+    if (!ensure(h, doffs, (size_t)(n + 1) * 4) || !ensure(h, dout, (size_t)tot * 16))
+      return CDR_ERR_OOM;
+    cudaMemcpyAsync(doffs.p, offs.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, s);
+    launch_report_cav(h->m, r, ptr<int>(doffs), ptr<int4>(dout), s);
+    cudaMemcpyAsync(cav, dout.p, (size_t)tot * 16, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    dfree(h, doffs);
+    dfree(h, dout);
+  }
+  dfree(h, b);
+  return cuda_status(h);
+}
+
+int cdr_checkpoint(cdr_handle* h) {
+  if (!h) return CDR_ERR_INVALID_INPUT;
+  DevMesh& m = h->m;
+  struct {
+    Buf* b;
+    size_t bytes;
+  } parts[] = {{&h->bV, (size_t)m.nV * sizeof(V4)},
+               {&h->bT, (size_t)m.nT * sizeof(TetRec)},
+               {&h->bTS, (size_t)m.nT * 16},
+               {&h->bTflag, (size_t)m.nT},
+               {&h->bTfwd, (size_t)m.nT * 4},
+               {&h->bSV, (size_t)m.nS * 16},
+               {&h->bSN, (size_t)m.nS * 16},
+               {&h->bSflag, (size_t)m.nS},
+               {&h->bSmust, (size_t)m.nS},
+               {&h->bGV, (size_t)m.nG * 16},
+               {&h->bGflag, (size_t)m.nG},
+               {&h->bGmust, (size_t)m.nG},
+               {&h->bHK, h->bHK.bytes},
+               {&h->bHV, h->bHV.bytes}};
+  for (Buf& b : h->ck) dfree(h, b);
+  h->ck.clear();
+  for (auto& p : parts) {
+    Buf c;
+    if (!ensure(h, c, p.bytes + 16)) return CDR_ERR_OOM;
+    if (p.bytes) cudaMemcpyAsync(c.p, p.b->p, p.bytes, cudaMemcpyDeviceToDevice, h->stream);
+    c.bytes = p.bytes;  // payload size
+    h->ck.push_back(c);
+  }
+  h->ckm = m;
+  h->ck_hcount = h->hcount;
+  h->has_ck = true;
+  cudaStreamSynchronize(h->stream);
+  return cuda_status(h);
+}
+
+int cdr_restore(cdr_handle* h) {
+  if (!h || !h->has_ck) return CDR_ERR_INVALID_INPUT;
+  DevMesh c = h->ckm;
+  if (!grow_verts(h, c.nV) || !grow_tets(h, c.nT) || !grow_subfaces(h, c.nS) ||
+      !grow_subsegs(h, c.nG))
+    return CDR_ERR_OOM;
+  if (!ensure(h, h->bHK, h->ck[12].bytes) || !ensure(h, h->bHV, h->ck[13].bytes)) return CDR_ERR_OOM;
+  Buf* dst[] = {&h->bV,  &h->bT,     &h->bTS,    &h->bTflag, &h->bTfwd,  &h->bSV,  &h->bSN,
+                &h->bSflag, &h->bSmust, &h->bGV, &h->bGflag, &h->bGmust, &h->bHK, &h->bHV};
+  for (int i = 0; i < 14; ++i)
+    if (h->ck[i].bytes)
+      cudaMemcpyAsync(dst[i]->p, h->ck[i].p, h->ck[i].bytes, cudaMemcpyDeviceToDevice, h->stream);
+  DevMesh& m = h->m;
+  m.nV = c.nV;
+  m.nT = c.nT;
+  m.nS = c.nS;
+  m.nG = c.nG;
+  m.hmask = c.hmask;
+  h->hcount = h->ck_hcount;
+  h->lastB = -1.0;
+  h->lastN = 0;
+  h->err = 0;
+  bind(h);
+  cudaMemsetAsync(h->bTmark.p, 0xff, (size_t)h->capT * 8, h->stream);
+  cudaMemsetAsync(h->bSmark.p, 0xff, (size_t)h->capS * 8, h->stream);
+  cudaStreamSynchronize(h->stream);
+  return cuda_status(h);
+}
+
+int cdr_delaunay_box(const double* xyz, int32_t n, const cdr_options* opt,
+                     const cdr_allocator* alloc, void* stream, cdr_handle** out,
+                     int32_t* n_skipped, int32_t* n_rounds) {
+  if (!xyz || !out || n < 8 || n >= kMaxVerts) return CDR_ERR_INVALID_INPUT;
+  *out = nullptr;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      double v = xyz[3 * i + k];
+      if (!std::isfinite(v)) return CDR_ERR_INVALID_INPUT;
+      lo[k] = std::min(lo[k], v);
+      hi[k] = std::max(hi[k], v);
+    }
+  int corner[8];
+  for (int c = 0; c < 8; ++c) corner[c] = -1;
+  std::vector<int> state(n, 0);
+  for (int i = 0; i < n; ++i) {
+    int code = 0;
+    bool ok = true, onb = false;
+    for (int k = 0; k < 3; ++k) {
+      double v = xyz[3 * i + k];
+      if (v == hi[k]) code |= 1 << k;
+      else if (v != lo[k]) ok = false;
+      if (v == hi[k] || v == lo[k]) onb = true;
+    }
+    if (ok && corner[code] < 0) {
+      corner[code] = i;
+      state[i] = 1;
+    } else if (onb) {
+      return CDR_ERR_INVALID_INPUT;  // only the corners may lie on the box
+    }
+  }
+  for (int c = 0; c < 8; ++c)
+    if (corner[c] < 0) return CDR_ERR_INVALID_INPUT;
+  // the cube as six tetrahedra around its main diagonal; an odd axis order
+  // gives a negatively oriented tuple, fixed by swapping two vertices
+  const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const bool odd[6] = {false, true, true, false, false, true};
+  std::vector<int> tets;
+  for (int q = 0; q < 6; ++q) {
+    int b1 = 1 << perm[q][0], b2 = b1 | (1 << perm[q][1]);
+    int t[4] = {corner[0], corner[b1], corner[b2], corner[7]};
+    if (odd[q]) std::swap(t[1], t[2]);
+    tets.insert(tets.end(), t, t + 4);
+  }
+  cdr_handle* h = new (std::nothrow) cdr_handle();
+  if (!h) return CDR_ERR_OOM;
+  h->stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    h->alloc = *alloc;
+    h->has_alloc = true;
+  }
+  h->dt_mode = true;
+  h->m.walk_limit = (opt && opt->walk_limit > 0) ? opt->walk_limit : 100000;
+  h->m.guard2 = 0.0;  // exact duplicates only
+  int st = build_mesh(h, xyz, n, tets.data(), 6, n, std::max(8 * n, 4096));
+  dfree(h, h->bKeys);
+  dfree(h, h->bCand2);
+  dfree(h, h->bI32);
+  if (!st && (!grow_subsegs(h, 16) || !grow_subfaces(h, 16) || !rebuild_hash(h, 16) ||
+              !ensure(h, h->bFQ, 64)))
+    st = CDR_ERR_OOM;
+  if (st) {
+    cdr_destroy(h);
+    return st;
+  }
+  bind(h);
+  h->npts = n;
+  if (!ensure(h, h->bPts, (size_t)n * 24) || !ensure(h, h->bHint, (size_t)n * 4) ||
+      !ensure(h, h->bPstate, (size_t)n * 4)) {
+    cdr_destroy(h);
+    return CDR_ERR_OOM;
+  }
+  cudaStream_t s = h->stream;
+  cudaMemcpyAsync(h->bPts.p, xyz, (size_t)n * 24, cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(h->bHint.p, 0, (size_t)n * 4, s);
+  cudaMemcpyAsync(h->bPstate.p, state.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s);
+  int rounds = 0;
+  for (;;) {
+    if (!ensure_round(h, n)) {
+      st = CDR_ERR_OOM;
+      break;
+    }
+    int* flag = ptr<int>(h->bI32);
+    k_point_flags<<<gridn(n), 256, 0, s>>>(ptr<int>(h->bPstate), n, flag);
+    size_t tb = 0;
+    int* nsel = ptr<int>(h->bErr) + 4;
+    cub::DeviceSelect::Flagged(nullptr, tb, thrust::counting_iterator<int>(0), flag,
+                               ptr<int>(h->bCand), nsel, n, s);
+    if (!tmp_ensure(h, tb)) {
+      st = CDR_ERR_OOM;
+      break;
+    }
+    tb = h->bTmp.bytes;
+    cub::DeviceSelect::Flagged(h->bTmp.p, tb, thrust::counting_iterator<int>(0), flag,
+                               ptr<int>(h->bCand), nsel, n, s);
+    int nc = 0;
+    cudaMemcpyAsync(&nc, nsel, 4, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (nc == 0) break;
+    st = order_candidates(h, CLS_POINT, nc);
+    if (!st) st = round_core(h, CLS_POINT, nc, 1.0, nullptr);
+    if (st) break;
+    ++rounds;
+    if (h->m.nT > (1 << 20) && (rounds % 8) == 0) {
+      st = maybe_compact(h, false);
+      if (st) break;
+    }
+  }
+  if (!st) {
+    cudaMemcpyAsync(state.data(), h->bPstate.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    int sk = 0;
+    for (int i = 0; i < n; ++i) sk += state[i] == 2;
+    if (n_skipped) *n_skipped = sk;
+    if (n_rounds) *n_rounds = rounds;
+    st = cuda_status(h);
+  }
+  if (st) {
+    cdr_destroy(h);
+    return st;
+  }
+  *out = h;
+  return CDR_OK;
+}
+
+int cdr_eval_predicates(int32_t kind, const double* in, int32_t n, int32_t* sign, double* out,
+                        void* stream) {
+  if (kind < 0 || kind > 11 || n < 0 || !in || !sign) return CDR_ERR_INVALID_INPUT;
+  if (n == 0) return CDR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* din = nullptr;
+  int* dsg = nullptr;
+  double* dout = nullptr;
+  if (cudaMalloc(&din, (size_t)n * 16 * 8) != cudaSuccess ||
+      cudaMalloc(&dsg, (size_t)n * 4) != cudaSuccess ||
+      cudaMalloc(&dout, (size_t)n * 3 * 8) != cudaSuccess) {
+    cudaFree(din);
+    cudaFree(dsg);
+    cudaFree(dout);
+    return CDR_ERR_OOM;
+  }
+  cudaMemcpyAsync(din, in, (size_t)n * 16 * 8, cudaMemcpyHostToDevice, s);
+  launch_eval_pred(kind, din, n, dsg, dout, s);
+  cudaMemcpyAsync(sign, dsg, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+  if (out) cudaMemcpyAsync(out, dout, (size_t)n * 3 * 8, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  int ov = exact_overflow_flag(s, true);
+  cudaFree(din);
+  cudaFree(dsg);
+  cudaFree(dout);
+  if (cudaGetLastError() != cudaSuccess) return CDR_ERR_CUDA;
+  return ov ? CDR_ERR_INTERNAL : CDR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1855 @@
+// Refinement kernels for sm_103a.
+//
+// One round (Sec. 2 of Chen & Tan, I3D 2019) is: classify elements, order the
+// candidates of the first non-empty class by predetermined priority, compute
+// splitting points (k_split), locate them (k_locate), grow every point's
+// Delaunay region with one warp per point and mark every touched element with
+// atomicMin of the point's priority (k_grow1 / k_grow2: the "grow" step with
+// work proportional to region size), keep the points that hold every mark
+// (k_select: the "blast" step), and insert the kept points concurrently,
+// re-linking the new stars to the rest of the mesh (k_insert).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "mesh.cuh"
+#include "predicates.cuh"
+
+namespace cdr {
+
+#define FULLMASK 0xffffffffu
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ int geti(const int4& a, int k) {
+  return k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? a.z : a.w));
+}
+__device__ __forceinline__ void seti(int4& a, int k, int v) {
+  if (k == 0) a.x = v;
+  else if (k == 1) a.y = v;
+  else if (k == 2) a.z = v;
+  else a.w = v;
+}
+__device__ __forceinline__ int vid(int x) { return x & kVidMask; }
+__device__ __forceinline__ D3 vtx(const DevMesh& m, int v) {
+  V4 q = m.V[v];
+  return D3{q.x, q.y, q.z};
+}
+__device__ __forceinline__ TetRec ld_tet(const DevMesh& m, int t) { return m.T[t]; }
+__device__ __forceinline__ int* tet_n_ptr(const DevMesh& m, int t) { return &m.T[t].n.x; }
+__device__ __forceinline__ int* tet_v_ptr(const DevMesh& m, int t) { return &m.T[t].v.x; }
+__device__ __forceinline__ int* ts_ptr(const DevMesh& m, int t) { return &m.TS[t].x; }
+__device__ __forceinline__ int* sn_ptr(const DevMesh& m, int s) { return &m.SN[s].x; }
+
+// edge e of a tetrahedron: 0:(0,1) 1:(0,2) 2:(0,3) 3:(1,2) 4:(1,3) 5:(2,3)
+__device__ __forceinline__ int edge_i(int e) { return e < 3 ? 0 : (e < 5 ? 1 : 2); }
+__device__ __forceinline__ int edge_j(int e) { return e < 3 ? e + 1 : (e < 5 ? e - 1 : 3); }
+__device__ __forceinline__ int edge_of(int i, int j) {
+  int a = min(i, j), b = max(i, j);
+  return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
+}
+__device__ __forceinline__ bool edge_bit(const int4& v, int e) {
+  return (geti(v, e >> 1) >> (29 + (e & 1))) & 1;
+}
+__device__ __forceinline__ bool face_sub(const int4& v, int f) { return (geti(v, f) >> kSubBit) & 1; }
+
+__device__ __forceinline__ void sort3(int& a, int& b, int& c) {
+  int t;
+  if (a > b) { t = a; a = b; b = t; }
+  if (b > c) { t = b; b = c; c = t; }
+  if (a > b) { t = a; a = b; b = t; }
+}
+__device__ __forceinline__ void sort4(int* s) {
+  for (int i = 1; i < 4; ++i)
+    for (int j = i; j > 0 && s[j - 1] > s[j]; --j) {
+      int t = s[j];
+      s[j] = s[j - 1];
+      s[j - 1] = t;
+    }
+}
+__device__ __forceinline__ bool lt3(int a0, int a1, int a2, int b0, int b1, int b2) {
+  if (a0 != b0) return a0 < b0;
+  if (a1 != b1) return a1 < b1;
+  return a2 < b2;
+}
+
+// subsegment hash: key (min << 32 | max)
+__device__ __forceinline__ unsigned long long ekey(int a, int b) {
+  unsigned u = (unsigned)min(a, b), w = (unsigned)max(a, b);
+  return ((unsigned long long)u << 32) | w;
+}
+__device__ int hash_lookup(const DevMesh& m, unsigned long long k) {
+  unsigned h = (unsigned)mix64(k) & (unsigned)m.hmask;
+  for (int it = 0; it <= m.hmask; ++it) {
+    unsigned long long e = m.HK[h];
+    if (e == k) return m.HV[h];
+    if (e == ~0ULL) return -1;
+    h = (h + 1) & (unsigned)m.hmask;
+  }
+  return -1;
+}
+__device__ void hash_insert(const DevMesh& m, unsigned long long k, int v) {
+  unsigned h = (unsigned)mix64(k) & (unsigned)m.hmask;
+  for (int it = 0; it <= m.hmask; ++it) {
+    unsigned long long old = atomicCAS(&m.HK[h], ~0ULL, k);
+    if (old == ~0ULL || old == k) {
+      m.HV[h] = v;
+      return;
+    }
+    h = (h + 1) & (unsigned)m.hmask;
+  }
+}
+
+// orient of tetrahedron r with vertex f replaced by p, from its 4 vertices
+__device__ __forceinline__ int orient_rep4(const D3* c, int f, D3 p) {
+  return orient3d(f == 0 ? p : c[0], f == 1 ? p : c[1], f == 2 ? p : c[2], f == 3 ? p : c[3]);
+}
+__device__ __forceinline__ int orient_rep(const DevMesh& m, const TetRec& r, int f, D3 p) {
+  D3 a = f == 0 ? p : vtx(m, vid(r.v.x));
+  D3 b = f == 1 ? p : vtx(m, vid(r.v.y));
+  D3 c = f == 2 ? p : vtx(m, vid(r.v.z));
+  D3 d = f == 3 ? p : vtx(m, vid(r.v.w));
+  return orient3d(a, b, c, d);
+}
+__device__ __forceinline__ bool tet_in_sphere(const DevMesh& m, const TetRec& r, D3 p) {
+  return insphere(vtx(m, vid(r.v.x)), vtx(m, vid(r.v.y)), vtx(m, vid(r.v.z)), vtx(m, vid(r.v.w)),
+                  p) > 0;
+}
+// subface winding seen from the facet reference point
+__device__ __forceinline__ int sf_wind(const DevMesh& m, int4 S) {
+  V4 q = m.FQ[S.w];
+  return orient3d(vtx(m, S.x), vtx(m, S.y), vtx(m, S.z), D3{q.x, q.y, q.z});
+}
+__device__ __forceinline__ int sf_orient_rep(const DevMesh& m, int4 S, int k, D3 p) {
+  V4 q = m.FQ[S.w];
+  D3 a = k == 0 ? p : vtx(m, S.x);
+  D3 b = k == 1 ? p : vtx(m, S.y);
+  D3 c = k == 2 ? p : vtx(m, S.z);
+  return orient3d(a, b, c, D3{q.x, q.y, q.z});
+}
+__device__ __forceinline__ bool sf_incircle(const DevMesh& m, int4 S, D3 p) {
+  V4 q = m.FQ[S.w];
+  D3 Q{q.x, q.y, q.z};
+  int o = insphere(vtx(m, S.x), vtx(m, S.y), vtx(m, S.z), Q, p);
+  return o * orient3d(vtx(m, S.x), vtx(m, S.y), vtx(m, S.z), Q) > 0;
+}
+
+__device__ __forceinline__ void set_status(const DevRound& r, int i, int outcome, int reason) {
+  r.status[i] = outcome | (reason << 8);
+}
+
+// ================================================================= create
+__global__ void k_init_tets(DevMesh m, const int4* tets, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    TetRec r;
+    r.v = tets[i];
+    r.n = make_int4(-1, -1, -1, -1);
+    m.T[i] = r;
+    m.TS[i] = make_int4(-1, -1, -1, -1);
+    m.Tflag[i] = 0;
+    m.Tmark[i] = ~0ULL;
+    m.Tfwd[i] = -1;
+  }
+}
+
+__global__ void k_face_keys(DevMesh m, unsigned long long* hi, unsigned int* lo, int* val) {
+  int n = m.nT * 4;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int t = i >> 2, f = i & 3;
+    int4 v = m.T[t].v;
+    int w[3], k = 0;
+    for (int j = 0; j < 4; ++j)
+      if (j != f) w[k++] = vid(geti(v, j));
+    sort3(w[0], w[1], w[2]);
+    hi[i] = ((unsigned long long)(unsigned)w[0] << 32) | (unsigned)w[1];
+    lo[i] = (unsigned)w[2];
+    if (val) val[i] = i;
+  }
+}
+
+__global__ void k_pair_faces(DevMesh m, const unsigned long long* hi, const unsigned int* lo,
+                             const int* val, int n, int* err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    bool eqn = i + 1 < n && hi[i + 1] == hi[i] && lo[i + 1] == lo[i];
+    bool eqp = i > 0 && hi[i - 1] == hi[i] && lo[i - 1] == lo[i];
+    if (eqn && eqp) atomicOr(err, 1);  // a face shared by three tetrahedra
+    if (eqn) {
+      int a = val[i], b = val[i + 1];
+      tet_n_ptr(m, a >> 2)[a & 3] = b;
+      tet_n_ptr(m, b >> 2)[b & 3] = a;
+    }
+  }
+}
+
+__device__ int face_lower_bound(const unsigned long long* hi, const unsigned int* lo, int n,
+                                unsigned long long h, unsigned l) {
+  int a = 0, b = n;
+  while (a < b) {
+    int c = (a + b) >> 1;
+    if (hi[c] < h || (hi[c] == h && lo[c] < l)) a = c + 1;
+    else b = c;
+  }
+  return a;
+}
+
+__global__ void k_label_subfaces(DevMesh m, const int4* tris, int n, const unsigned long long* hi,
+                                 const unsigned int* lo, const int* val, int nfaces, int* err) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    int4 S = tris[s];
+    m.SV[s] = S;
+    m.SN[s] = make_int4(-1, -1, -1, -1);
+    m.Sflag[s] = 0;
+    m.Smust[s] = 0;
+    m.Smark[s] = ~0ULL;
+    int a = S.x, b = S.y, c = S.z;
+    if (a < 0 || b < 0 || c < 0 || a >= m.nV || b >= m.nV || c >= m.nV || S.w < 0 || S.w >= m.nF) {
+      atomicOr(err, 8);
+      continue;
+    }
+    sort3(a, b, c);
+    unsigned long long h = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+    int j = face_lower_bound(hi, lo, nfaces, h, (unsigned)c);
+    if (j >= nfaces || hi[j] != h || lo[j] != (unsigned)c) {
+      atomicOr(err, 8);  // label is not a mesh face
+      continue;
+    }
+    int first = val[j];
+    m.SN[s].w = first;
+    for (int q = j; q < nfaces && q < j + 2 && hi[q] == h && lo[q] == (unsigned)c; ++q) {
+      int tf = val[q];
+      ts_ptr(m, tf >> 2)[tf & 3] = s;
+      atomicOr(&tet_v_ptr(m, tf >> 2)[tf & 3], 1 << kSubBit);
+    }
+  }
+}
+
+__global__ void k_subface_edge_keys(DevMesh m, unsigned long long* hi, unsigned int* lo, int* val) {
+  int n = m.nS * 3;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int s = i / 3, k = i % 3;
+    int4 S = m.SV[s];
+    int u = geti(S, (k + 1) % 3), w = geti(S, (k + 2) % 3);
+    if (u > w) { int t = u; u = w; w = t; }
+    hi[i] = ((unsigned long long)(unsigned)u << 32) | (unsigned)w;
+    lo[i] = (unsigned)S.w;
+    if (val) val[i] = i;
+  }
+}
+
+__global__ void k_pair_subface_edges(DevMesh m, const unsigned long long* hi,
+                                     const unsigned int* lo, const int* val, int n, int* err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    bool eqn = i + 1 < n && hi[i + 1] == hi[i] && lo[i + 1] == lo[i];
+    bool eqp = i > 0 && hi[i - 1] == hi[i] && lo[i - 1] == lo[i];
+    if (eqn && eqp) atomicOr(err, 16);  // three subfaces of one facet on an edge
+    bool isseg = hash_lookup(m, hi[i]) >= 0;
+    if (!eqn && !eqp && !isseg) atomicOr(err, 32);  // open facet edge that is not a segment
+    if (eqn && !isseg) {
+      int a = val[i], b = val[i + 1];  // subface * 3 + edge
+      sn_ptr(m, a / 3)[a % 3] = b / 3;
+      sn_ptr(m, b / 3)[b % 3] = a / 3;
+    }
+  }
+}
+
+__global__ void k_hash_clear(DevMesh m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= m.hmask; i += gridDim.x * blockDim.x) {
+    m.HK[i] = ~0ULL;
+    m.HV[i] = -1;
+  }
+}
+__global__ void k_hash_insert_subsegs(DevMesh m, int g0, int g1) {
+  for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += gridDim.x * blockDim.x) {
+    if (m.Gflag[g] & F_DEAD) continue;
+    int4 G = m.GV[g];
+    hash_insert(m, ekey(G.x, G.y), g);
+  }
+}
+__global__ void k_mark_edges(DevMesh m) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x) {
+    if (m.Tflag[t] & F_DEAD) continue;
+    int4 v = m.T[t].v;
+    for (int e = 0; e < 6; ++e) {
+      int a = vid(geti(v, edge_i(e))), b = vid(geti(v, edge_j(e)));
+      int g = hash_lookup(m, ekey(a, b));
+      if (g >= 0) {
+        atomicOr(&tet_v_ptr(m, t)[e >> 1], 1 << (29 + (e & 1)));
+        m.GV[g].w = t;
+      }
+    }
+  }
+}
+__global__ void k_check_create(DevMesh m, int* err) {
+  int n = m.nT + m.nG;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < m.nT) {
+      TetRec r = m.T[i];
+      int a = vid(r.v.x), b = vid(r.v.y), c = vid(r.v.z), d = vid(r.v.w);
+      if (orient3d(vtx(m, a), vtx(m, b), vtx(m, c), vtx(m, d)) <= 0) atomicOr(err, 2);
+      for (int f = 0; f < 4; ++f)
+        if (geti(r.n, f) < 0 && !face_sub(r.v, f)) atomicOr(err, 4);  // hull face not a subface
+    } else {
+      int g = i - m.nT;
+      if (m.GV[g].w < 0) atomicOr(err, 64);  // subsegment label is not a mesh edge
+    }
+  }
+}
+__global__ void k_recompute_bad(DevMesh m, double B) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x) {
+    uint8_t f = m.Tflag[t];
+    if (f & F_DEAD) continue;
+    int4 v = m.T[t].v;
+    int s[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
+    sort4(s);
+    bool bad = tet_bad_fixed(vtx(m, s[0]), vtx(m, s[1]), vtx(m, s[2]), vtx(m, s[3]), B);
+    m.Tflag[t] = bad ? (f | F_BAD) : (f & ~F_BAD);
+  }
+}
+
+// ============================================================ classification
+// Ring of tetrahedra around a subsegment edge, starting from a live tet that
+// contains it. Calls visit(tet record) for each tet. Returns false if the
+// start tet is invalid or the ring is longer than the step limit.
+template <class F>
+__device__ bool edge_ring(const DevMesh& m, int t0, int a, int b, F visit) {
+  if (t0 < 0 || t0 >= m.nT || (m.Tflag[t0] & F_DEAD)) return false;
+  TetRec r0 = ld_tet(m, t0);
+  int ia = -1, ib = -1;
+  for (int k = 0; k < 4; ++k) {
+    int x = vid(geti(r0.v, k));
+    if (x == a) ia = k;
+    if (x == b) ib = k;
+  }
+  if (ia < 0 || ib < 0) return false;
+  int c = -1, d = -1;
+  for (int k = 0; k < 4; ++k)
+    if (k != ia && k != ib) (c < 0 ? c : d) = k;
+  visit(t0, r0);
+  // two directions: leave through the face opposite d (holding vertex c), then
+  // opposite c (holding d) if the first direction hit the hull
+  for (int dir = 0; dir < 2; ++dir) {
+    int L = dir == 0 ? d : c;
+    int z = vid(geti(r0.v, dir == 0 ? c : d));
+    int cur = t0;
+    TetRec rc = r0;
+    for (int it = 0; it < 4096; ++it) {
+      int n = geti(rc.n, L);
+      if (n < 0) break;  // hull: try the other direction
+      int nt = n >> 2;
+      if (nt == t0) return true;  // closed ring
+      rc = ld_tet(m, nt);
+      int zpos = -1;
+      for (int k = 0; k < 4; ++k)
+        if (vid(geti(rc.v, k)) == z) zpos = k;
+      if (zpos < 0) return false;
+      visit(nt, rc);
+      z = vid(geti(rc.v, n & 3));
+      L = zpos;
+      cur = nt;
+    }
+    if (dir == 1) return true;
+  }
+  return true;
+}
+
+__global__ void k_classify(DevMesh m, unsigned char* candS, unsigned char* candG,
+                           unsigned char* candT, int* err) {
+  int n = m.nG + m.nS + m.nT;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < m.nG) {
+      int g = i;
+      uint8_t f = m.Gflag[g];
+      if (f & (F_DEAD | F_UNSPL)) {
+        candG[g] = 0;
+        continue;
+      }
+      if (m.Gmust[g]) {
+        candG[g] = 1;
+        continue;
+      }
+      int4 G = m.GV[g];
+      D3 A = vtx(m, G.x), Bp = vtx(m, G.y);
+      bool enc = false;
+      bool ok = edge_ring(m, G.w, G.x, G.y, [&](int t, const TetRec& r) {
+        for (int k = 0; k < 4; ++k) {
+          int x = vid(geti(r.v, k));
+          if (x == G.x || x == G.y) continue;
+          if (!enc && diametral(A, Bp, vtx(m, x)) < 0) enc = true;
+        }
+      });
+      if (!ok) atomicOr(err, 1);
+      candG[g] = enc ? 1 : 0;
+    } else if (i < m.nG + m.nS) {
+      int s = i - m.nG;
+      uint8_t f = m.Sflag[s];
+      if (f & (F_DEAD | F_UNSPL)) {
+        candS[s] = 0;
+        continue;
+      }
+      if (m.Smust[s]) {
+        candS[s] = 1;
+        continue;
+      }
+      int4 S = m.SV[s];
+      int w = m.SN[s].w;
+      if (w < 0 || (w >> 2) >= m.nT) {
+        atomicOr(err, 2);
+        candS[s] = 0;
+        continue;
+      }
+      TetRec r = ld_tet(m, w >> 2);
+      D3 A = vtx(m, S.x), Bp = vtx(m, S.y), C = vtx(m, S.z);
+      bool enc = equatorial(A, Bp, C, vtx(m, vid(geti(r.v, w & 3)))) < 0;
+      int nb = geti(r.n, w & 3);
+      if (!enc && nb >= 0) {
+        TetRec r2 = ld_tet(m, nb >> 2);
+        enc = equatorial(A, Bp, C, vtx(m, vid(geti(r2.v, nb & 3)))) < 0;
+      }
+      candS[s] = enc ? 1 : 0;
+    } else {
+      int t = i - m.nG - m.nS;
+      uint8_t f = m.Tflag[t];
+      candT[t] = ((f & (F_DEAD | F_UNSPL | F_BAD)) == F_BAD) ? 1 : 0;
+    }
+  }
+}
+
+__device__ int elem_key(const DevMesh& m, int cls, int e, int* ids) {
+  if (cls == CLS_SUBSEG) {
+    int4 G = m.GV[e];
+    ids[0] = min(G.x, G.y);
+    ids[1] = max(G.x, G.y);
+    return 2;
+  }
+  if (cls == CLS_SUBFACE) {
+    int4 S = m.SV[e];
+    ids[0] = S.x;
+    ids[1] = S.y;
+    ids[2] = S.z;
+    sort3(ids[0], ids[1], ids[2]);
+    return 3;
+  }
+  if (cls == CLS_TET) {
+    int4 v = m.T[e].v;
+    ids[0] = vid(v.x);
+    ids[1] = vid(v.y);
+    ids[2] = vid(v.z);
+    ids[3] = vid(v.w);
+    sort4(ids);
+    return 4;
+  }
+  ids[0] = e;
+  return 1;
+}
+
+__global__ void k_prio(DevMesh m, int cls, const int* elems, int n, unsigned long long* keys) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int ids[4];
+    int k = elem_key(m, cls, elems[i], ids);
+    keys[i] = prio_hash(cls, ids, k);
+  }
+}
+
+// Equal priority hashes (practically never): order the run by the sorted ids.
+__global__ void k_tiefix(DevMesh m, int cls, const unsigned long long* keys, int* elems, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    bool start = (i == 0 || keys[i - 1] != keys[i]) && (i + 1 < n && keys[i + 1] == keys[i]);
+    if (!start) continue;
+    int j = i + 1;
+    while (j < n && keys[j] == keys[i]) ++j;
+    for (int a = i + 1; a < j; ++a)
+      for (int b = a; b > i; --b) {
+        int x[4], y[4];
+        int nk = elem_key(m, cls, elems[b - 1], x);
+        elem_key(m, cls, elems[b], y);
+        bool lt = false, eq = true;
+        for (int q = 0; q < nk && eq; ++q)
+          if (y[q] != x[q]) {
+            lt = y[q] < x[q];
+            eq = false;
+          }
+        if (!lt) break;
+        int t = elems[b];
+        elems[b] = elems[b - 1];
+        elems[b - 1] = t;
+      }
+  }
+}
+
+// ============================================================ split + locate
+__global__ void k_split(DevMesh m, DevRound r) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
+    int e = r.cand[i];
+    D3 p{0, 0, 0};
+    bool ok = true;
+    if (r.cls == CLS_SUBSEG) {
+      int4 G = m.GV[e];
+      p = midpoint_fixed(vtx(m, min(G.x, G.y)), vtx(m, max(G.x, G.y)));
+      ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
+    } else if (r.cls == CLS_SUBFACE) {
+      int ids[4];
+      elem_key(m, CLS_SUBFACE, e, ids);
+      ok = tri_circumcenter_fixed(vtx(m, ids[0]), vtx(m, ids[1]), vtx(m, ids[2]), p);
+    } else if (r.cls == CLS_TET) {
+      int ids[4];
+      elem_key(m, CLS_TET, e, ids);
+      D3 off;
+      ok = tet_circumcenter_fixed(vtx(m, ids[0]), vtx(m, ids[1]), vtx(m, ids[2]),
+                                  vtx(m, ids[3]), p, off);
+    } else {
+      p = D3{r.given[3 * e], r.given[3 * e + 1], r.given[3 * e + 2]};
+      ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
+    }
+    r.sp[i] = make_v4(p.x, p.y, p.z, 0.0);
+    r.loc[i] = -1;
+    set_status(r, i, ok ? OUT_OK : OUT_UNSPL, ok ? RS_NONE : RS_BADPOINT);
+  }
+}
+
+// Visibility walk (exit through the face with the smallest sorted vertex triple
+// among those p lies strictly beyond) and the facet walk (same rule on edges).
+__global__ void k_locate(DevMesh m, DevRound r, int* hint) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
+    if (r.status[i] != OUT_OK) continue;
+    int e = r.cand[i];
+    V4 q = r.sp[i];
+    D3 p{q.x, q.y, q.z};
+    if (r.cls == CLS_TET || r.cls == CLS_POINT) {
+      int t = r.cls == CLS_TET ? e : hint[e];
+      bool done = false;
+      for (int it = 0; it < m.walk_limit && !done; ++it) {
+        TetRec rec = ld_tet(m, t);
+        int vv[4] = {vid(rec.v.x), vid(rec.v.y), vid(rec.v.z), vid(rec.v.w)};
+        D3 c[4] = {vtx(m, vv[0]), vtx(m, vv[1]), vtx(m, vv[2]), vtx(m, vv[3])};
+        int best = -1, b0 = 0, b1 = 0, b2 = 0;
+        for (int f = 0; f < 4; ++f) {
+          if (orient_rep4(c, f, p) < 0) {
+            int w[3], k = 0;
+            for (int j = 0; j < 4; ++j)
+              if (j != f) w[k++] = vv[j];
+            sort3(w[0], w[1], w[2]);
+            if (best < 0 || lt3(w[0], w[1], w[2], b0, b1, b2)) {
+              best = f;
+              b0 = w[0];
+              b1 = w[1];
+              b2 = w[2];
+            }
+          }
+        }
+        if (best < 0) {
+          r.loc[i] = t;
+          done = true;
+          break;
+        }
+        if (face_sub(rec.v, best)) {
+          int s = ts_ptr(m, t)[best];
+          if (s < 0 || s >= m.nS) {
+            atomicAdd(&r.stats[ST_ITER], 1ULL);
+            set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
+            done = true;
+            break;
+          }
+          if (m.Sflag[s] & F_UNSPL) {
+            set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
+          } else {
+            set_status(r, i, OUT_REJECT, RS_WALK_SUBFACE);
+          }
+          m.Smust[s] = 1;
+          done = true;
+          break;
+        }
+        int n = geti(rec.n, best);
+        if (n < 0) {
+          set_status(r, i, OUT_UNSPL, RS_WALK_HULL);
+          done = true;
+          break;
+        }
+        t = n >> 2;
+      }
+      if (!done) set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
+    } else if (r.cls == CLS_SUBFACE) {
+      int s = e;
+      bool done = false;
+      for (int it = 0; it < m.walk_limit && !done; ++it) {
+        int4 S = m.SV[s];
+        int w = sf_wind(m, S);
+        int best = -1, b0 = 0, b1 = 0;
+        for (int k = 0; k < 3; ++k) {
+          if (sf_orient_rep(m, S, k, p) == -w) {
+            int u = geti(S, (k + 1) % 3), x = geti(S, (k + 2) % 3);
+            int e0 = min(u, x), e1 = max(u, x);
+            if (best < 0 || e0 < b0 || (e0 == b0 && e1 < b1)) {
+              best = k;
+              b0 = e0;
+              b1 = e1;
+            }
+          }
+        }
+        if (best < 0) {
+          r.loc[i] = s;
+          done = true;
+          break;
+        }
+        int nb = geti(m.SN[s], best);
+        if (nb < 0) {
+          int g = hash_lookup(m, ekey(b0, b1));
+          if (g < 0) {
+            set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
+          } else {
+            if (m.Gflag[g] & F_UNSPL) set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
+            else set_status(r, i, OUT_REJECT, RS_WALK_SUBSEG);
+            m.Gmust[g] = 1;
+          }
+          done = true;
+          break;
+        }
+        s = nb;
+      }
+      if (!done) set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
+    } else {
+      r.loc[i] = e;
+    }
+  }
+}
+
+// =============================================================== growth
+struct Ws {
+  int* cav;   // cavity tets
+  int* hset;  // (tet << 2 | state) open addressing, -1 empty; state 1 in, 2 out
+  int* bin;   // boundary faces: tet << 2 | face
+  int* bout;  // neighbour across (tet << 2 | face) or -1
+  int* bv;    // the boundary face's 3 vertex ids
+  int* fcav;  // facet part subfaces
+  int* fbnd;  // facet boundary edges: subface << 2 | edge
+  int* fbv;   // the edge's 2 vertex ids and the facet id
+};
+
+__device__ __forceinline__ unsigned hs_slot(int t, int cap) {
+  return (unsigned)mix64((unsigned long long)(unsigned)t) & (unsigned)(cap - 1);
+}
+__device__ int hs_find(const int* hs, int cap, int t) {
+  unsigned h = hs_slot(t, cap);
+  for (int it = 0; it < cap; ++it) {
+    int e = hs[h];
+    if (e == -1) return 0;
+    if ((e >> 2) == t) return e & 3;
+    h = (h + 1) & (unsigned)(cap - 1);
+  }
+  return 0;
+}
+// returns 1 inserted, 0 present (state overwritten when force), -1 full
+__device__ int hs_put(int* hs, int cap, int t, int state, bool force) {
+  unsigned h = hs_slot(t, cap);
+  for (int it = 0; it < cap; ++it) {
+    int old = atomicCAS(&hs[h], -1, (t << 2) | state);
+    if (old == -1) return 1;
+    if ((old >> 2) == t) {
+      if (force) hs[h] = (t << 2) | state;
+      return 0;
+    }
+    h = (h + 1) & (unsigned)(cap - 1);
+  }
+  return -1;
+}
+__device__ __forceinline__ bool in_list(const int* a, int n, int x) {
+  for (int i = 0; i < n; ++i)
+    if (a[i] == x) return true;
+  return false;
+}
+// warp-uniform append of flagged lane values, in lane order; n is warp-uniform
+__device__ __forceinline__ void wappend(int* list, int& n, int cap, bool pred, int val, int lane) {
+  unsigned b = __ballot_sync(FULLMASK, pred);
+  int pos = n + __popc(b & ((1u << lane) - 1));
+  if (pred && pos < cap) list[pos] = val;
+  n += __popc(b);
+}
+
+template <class C>
+__device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w, int* slab,
+                         int lane) {
+  using L = SlabLayout<C>;
+  const int cls = r.cls;
+  int st = r.status[i];
+  if (st != OUT_OK && st != OUT_RETRY) {
+    if (lane == 0) {
+      slab[0] = slab[1] = slab[2] = slab[3] = 0;
+    }
+    return;
+  }
+  const int elem = r.cand[i];
+  const V4 q4 = r.sp[i];
+  const D3 p{q4.x, q4.y, q4.z};
+  int sa = -1, sb = -1;
+  if (cls == CLS_SUBSEG) {
+    int4 G = m.GV[elem];
+    sa = G.x;
+    sb = G.y;
+  }
+  int ncav = 0, nf = 0, nbnd = 0, nfb = 0;
+  int outcome = OUT_OK, reason = RS_NONE;
+  bool retry = false;  // tier-1 capacity exceeded
+
+  for (int k = lane; k < C::HCAP; k += 32) w.hset[k] = -1;
+  __syncwarp();
+
+  // ---------------------------------------------------------- start sets
+  if (cls == CLS_TET || cls == CLS_POINT) {
+    if (lane == 0) {
+      w.cav[0] = r.loc[i];
+      hs_put(w.hset, C::HCAP, r.loc[i], 1, false);
+    }
+    ncav = 1;
+  } else if (cls == CLS_SUBFACE) {
+    if (lane == 0) w.fcav[0] = r.loc[i];
+    nf = 1;
+  } else {  // subsegment: the ring of its edge, and the subfaces on the edge
+    int nc = 0, nfl = 0, bad = 0;
+    if (lane == 0) {
+      int4 G = m.GV[elem];
+      bool ok = edge_ring(m, G.w, sa, sb, [&](int t, const TetRec& rec) {
+        if (nc < C::CAPC) w.cav[nc] = t;
+        ++nc;
+        hs_put(w.hset, C::HCAP, t, 1, false);
+        for (int f = 0; f < 4; ++f) {
+          int x = vid(geti(rec.v, f));
+          if (x == sa || x == sb) continue;
+          if (face_sub(rec.v, f)) {
+            int s = ts_ptr(m, t)[f];
+            bool dup = false;
+            for (int z = 0; z < min(nfl, C::CAPF); ++z) dup |= w.fcav[z] == s;
+            if (!dup) {
+              if (nfl < C::CAPF) w.fcav[nfl] = s;
+              ++nfl;
+            }
+          }
+        }
+      });
+      bad = ok ? 0 : 1;
+    }
+    nc = __shfl_sync(FULLMASK, nc, 0);
+    nfl = __shfl_sync(FULLMASK, nfl, 0);
+    bad = __shfl_sync(FULLMASK, bad, 0);
+    if (bad) {
+      outcome = OUT_UNSPL;
+      reason = RS_WALK_LIMIT;
+      goto done;
+    }
+    if (nc > C::CAPC || nfl > C::CAPF) {
+      retry = true;
+      goto done;
+    }
+    ncav = nc;
+    nf = nfl;
+  }
+  __syncwarp();
+
+  // ---------------------------------------------------------- facet part
+  if (nf > 0) {
+    int head = 0;
+    for (;;) {
+      while (head < nf) {
+        int end = nf;
+        int items = (end - head) * 3;
+        for (int base = 0; base < items; base += 32) {
+          int it = base + lane;
+          int cand = -1;
+          if (it < items) {
+            int s = w.fcav[head + it / 3], k = it % 3;
+            int4 S = m.SV[s];
+            int u = geti(S, (k + 1) % 3), x = geti(S, (k + 2) % 3);
+            bool split = sa >= 0 && ((u == sa && x == sb) || (u == sb && x == sa));
+            int nb = geti(m.SN[s], k);
+            if (!split && nb >= 0 && !in_list(w.fcav, min(nf, C::CAPF), nb)) cand = nb;
+          }
+          // one lane per distinct neighbour tests it
+          unsigned grp = __match_any_sync(FULLMASK, cand);
+          bool leader = cand >= 0 && (__ffs(grp) - 1) == lane;
+          bool add = false;
+          if (leader) add = sf_incircle(m, m.SV[cand], p);
+          wappend(w.fcav, nf, C::CAPF, add, cand, lane);
+          __syncwarp();
+        }
+        head = end;
+        if (nf > C::CAPF) break;
+      }
+      if (nf > C::CAPF) {
+        retry = true;
+        goto done;
+      }
+      // closure: every boundary edge must see p strictly inside
+      bool changed = false, fail = false;
+      int items = nf * 3;
+      for (int base = 0; base < items; base += 32) {
+        int it = base + lane;
+        int cand = -1;
+        bool f_ = false;
+        if (it < items) {
+          int s = w.fcav[it / 3], k = it % 3;
+          int4 S = m.SV[s];
+          int u = geti(S, (k + 1) % 3), x = geti(S, (k + 2) % 3);
+          bool split = sa >= 0 && ((u == sa && x == sb) || (u == sb && x == sa));
+          int nb = geti(m.SN[s], k);
+          if (!split && !(nb >= 0 && in_list(w.fcav, nf, nb))) {
+            if (sf_orient_rep(m, S, k, p) != sf_wind(m, S)) {
+              if (nb < 0) f_ = true;
+              else cand = nb;
+            }
+          }
+        }
+        fail |= __any_sync(FULLMASK, f_);
+        unsigned grp = __match_any_sync(FULLMASK, cand);
+        bool leader = cand >= 0 && (__ffs(grp) - 1) == lane;
+        // a neighbour may already have been appended in this pass by a lower chunk
+        if (leader && in_list(w.fcav, nf, cand)) leader = false;
+        __syncwarp();
+        int before = nf;
+        wappend(w.fcav, nf, C::CAPF, leader, cand, lane);
+        changed |= nf != before;
+        __syncwarp();
+        if (nf > C::CAPF) break;
+      }
+      if (fail) {
+        outcome = OUT_UNSPL;
+        reason = RS_CLOSURE;
+        goto done;
+      }
+      if (nf > C::CAPF) {
+        retry = true;
+        goto done;
+      }
+      if (!changed) break;
+    }
+    // boundary edges
+    {
+      int items = nf * 3;
+      for (int base = 0; base < items; base += 32) {
+        int it = base + lane;
+        bool pred = false;
+        int val = 0, eu = 0, ew = 0, fid = 0;
+        if (it < items) {
+          int s = w.fcav[it / 3], k = it % 3;
+          int4 S = m.SV[s];
+          eu = geti(S, (k + 1) % 3);
+          ew = geti(S, (k + 2) % 3);
+          fid = S.w;
+          bool split = sa >= 0 && ((eu == sa && ew == sb) || (eu == sb && ew == sa));
+          int nb = geti(m.SN[s], k);
+          pred = !split && !(nb >= 0 && in_list(w.fcav, nf, nb));
+          val = (s << 2) | k;
+        }
+        int b0 = nfb;
+        unsigned bal = __ballot_sync(FULLMASK, pred);
+        int pos = b0 + __popc(bal & ((1u << lane) - 1));
+        if (pred && pos < C::CAPFB) {
+          w.fbnd[pos] = val;
+          w.fbv[3 * pos] = eu;
+          w.fbv[3 * pos + 1] = ew;
+          w.fbv[3 * pos + 2] = fid;
+        }
+        nfb += __popc(bal);
+      }
+      if (nfb > C::CAPFB) {
+        retry = true;
+        goto done;
+      }
+    }
+    __syncwarp();
+    // tets on both sides of every facet-part subface start the cavity
+    {
+      for (int base = 0; base < nf; base += 32) {
+        int it = base + lane;
+        int c0 = -1, c1 = -1;
+        if (it < nf) {
+          int tf = m.SN[w.fcav[it]].w;
+          if (tf >= 0 && (tf >> 2) < m.nT) {
+            c0 = tf >> 2;
+            int nb = tet_n_ptr(m, c0)[tf & 3];
+            c1 = nb >= 0 ? (nb >> 2) : -1;
+          } else {
+            atomicAdd(&r.stats[ST_ITER], 1ULL);
+          }
+        }
+        for (int side = 0; side < 2; ++side) {
+          int c = side == 0 ? c0 : c1;
+          bool pred = false;
+          if (c >= 0) {
+            int res = hs_put(w.hset, C::HCAP, c, 1, false);
+            if (res < 0) retry = true;
+            pred = res == 1;
+          }
+          retry = __any_sync(FULLMASK, retry);
+          wappend(w.cav, ncav, C::CAPC, pred, c, lane);
+        }
+        __syncwarp();
+      }
+      if (retry || ncav > C::CAPC) {
+        retry = true;
+        goto done;
+      }
+    }
+  }
+
+  // ----------------------------------------------------------- tet part
+  {
+    int head = 0;
+    for (;;) {
+      while (head < ncav) {
+        int end = ncav;
+        int items = (end - head) * 4;
+        for (int base = 0; base < items; base += 32) {
+          int it = base + lane;
+          int cand = -1;
+          if (it < items) {
+            int t = w.cav[head + (it >> 2)], f = it & 3;
+            TetRec rec = ld_tet(m, t);
+            int nb = geti(rec.n, f);
+            if (nb >= 0 && !face_sub(rec.v, f)) {
+              int nt = nb >> 2;
+              if (hs_find(w.hset, C::HCAP, nt) == 0 && orient_rep(m, rec, f, p) > 0) cand = nt;
+            }
+          }
+          unsigned grp = __match_any_sync(FULLMASK, cand);
+          bool leader = cand >= 0 && (__ffs(grp) - 1) == lane;
+          bool add = false;
+          if (leader) {
+            bool in = tet_in_sphere(m, ld_tet(m, cand), p);
+            int res = hs_put(w.hset, C::HCAP, cand, in ? 1 : 2, false);
+            if (res < 0) retry = true;
+            add = in && res == 1;
+          }
+          retry = __any_sync(FULLMASK, retry);
+          wappend(w.cav, ncav, C::CAPC, add, cand, lane);
+          __syncwarp();
+          if (retry || ncav > C::CAPC) break;
+        }
+        head = end;
+        if (retry || ncav > C::CAPC) break;
+      }
+      if (retry || ncav > C::CAPC) {
+        retry = true;
+        goto done;
+      }
+      // closure
+      bool changed = false, fail = false;
+      int items = ncav * 4;
+      for (int base = 0; base < items; base += 32) {
+        int it = base + lane;
+        int cand = -1;
+        bool f_ = false;
+        if (it < items) {
+          int t = w.cav[it >> 2], f = it & 3;
+          TetRec rec = ld_tet(m, t);
+          int nb = geti(rec.n, f);
+          bool sub = face_sub(rec.v, f);
+          bool removed = sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
+          bool interior = !sub && nb >= 0 && hs_find(w.hset, C::HCAP, nb >> 2) == 1;
+          if (!removed && !interior && orient_rep(m, rec, f, p) <= 0) {
+            if (sub || nb < 0) f_ = true;
+            else cand = nb >> 2;
+          }
+        }
+        fail |= __any_sync(FULLMASK, f_);
+        unsigned grp = __match_any_sync(FULLMASK, cand);
+        bool leader = cand >= 0 && (__ffs(grp) - 1) == lane;
+        bool add = false;
+        if (leader) {
+          int res = hs_put(w.hset, C::HCAP, cand, 1, true);
+          if (res < 0) retry = true;
+          add = true;
+          if (res == 0) {
+            // it was tested out before (state now forced to in); append it
+            add = true;
+          }
+        }
+        retry = __any_sync(FULLMASK, retry);
+        __syncwarp();
+        // a tet appended earlier in this pass is already in; skip duplicates
+        if (add && in_list(w.cav, min(ncav, C::CAPC), cand)) add = false;
+        __syncwarp();
+        int before = ncav;
+        wappend(w.cav, ncav, C::CAPC, add, cand, lane);
+        changed |= ncav != before;
+        __syncwarp();
+        if (retry || ncav > C::CAPC) break;
+      }
+      if (fail) {
+        outcome = OUT_UNSPL;
+        reason = RS_CLOSURE;
+        goto done;
+      }
+      if (retry || ncav > C::CAPC) {
+        retry = true;
+        goto done;
+      }
+      if (!changed) break;
+    }
+    // boundary faces
+    int items = ncav * 4;
+    for (int base = 0; base < items; base += 32) {
+      int it = base + lane;
+      bool pred = false;
+      int bi = 0, bo = -1, v0 = 0, v1 = 0, v2 = 0;
+      if (it < items) {
+        int t = w.cav[it >> 2], f = it & 3;
+        TetRec rec = ld_tet(m, t);
+        int nb = geti(rec.n, f);
+        bool sub = face_sub(rec.v, f);
+        bool removed = sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
+        bool interior = !sub && nb >= 0 && hs_find(w.hset, C::HCAP, nb >> 2) == 1;
+        pred = !removed && !interior;
+        bi = (t << 2) | f;
+        bo = nb;
+        int z[3], k = 0;
+        for (int j = 0; j < 4; ++j)
+          if (j != f) z[k++] = vid(geti(rec.v, j));
+        v0 = z[0];
+        v1 = z[1];
+        v2 = z[2];
+      }
+      unsigned bal = __ballot_sync(FULLMASK, pred);
+      int pos = nbnd + __popc(bal & ((1u << lane) - 1));
+      if (pred && pos < C::CAPB) {
+        w.bin[pos] = bi;
+        w.bout[pos] = bo;
+        w.bv[3 * pos] = v0;
+        w.bv[3 * pos + 1] = v1;
+        w.bv[3 * pos + 2] = v2;
+      }
+      nbnd += __popc(bal);
+    }
+    if (nbnd > C::CAPB) {
+      retry = true;
+      goto done;
+    }
+  }
+  if (ncav > kCavLimit) {
+    outcome = OUT_UNSPL;
+    reason = RS_OVERFLOW;
+    goto done;
+  }
+  __syncwarp();
+
+  // ------------------------------------------------ preservation checks
+  {
+    // every cavity vertex lies on a boundary face
+    bool lost = false;
+    int items = ncav * 4;
+    for (int base = 0; base < items && !lost; base += 32) {
+      int it = base + lane;
+      bool miss = false;
+      if (it < items) {
+        int v = vid(geti(m.T[w.cav[it >> 2]].v, it & 3));
+        miss = !in_list(w.bv, 3 * nbnd, v);
+      }
+      lost = __any_sync(FULLMASK, miss);
+    }
+    // every facet boundary edge lies on a boundary face
+    for (int base = 0; base < nfb && !lost; base += 32) {
+      int it = base + lane;
+      bool miss = false;
+      if (it < nfb) {
+        int u = w.fbv[3 * it], x = w.fbv[3 * it + 1];
+        bool found = false;
+        for (int j = 0; j < nbnd && !found; ++j) {
+          const int* F = w.bv + 3 * j;
+          found = (F[0] == u || F[1] == u || F[2] == u) && (F[0] == x || F[1] == x || F[2] == x);
+        }
+        miss = !found;
+      }
+      lost = __any_sync(FULLMASK, miss);
+    }
+    if (lost) {
+      outcome = OUT_UNSPL;
+      reason = RS_CLOSURE;
+      goto done;
+    }
+  }
+  // ------------------------------------------------ star check
+  {
+    // topology first: every star edge is shared by at most two boundary faces
+    bool topo = false, nondel = false;
+    int items = nbnd * 3;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int base = 0; base < items; base += 32) {
+        int it = base + lane;
+        bool bad = false;
+        if (it < items) {
+          int j = it / 3, q = it % 3;
+          const int* F = w.bv + 3 * j;
+          int u = F[(q + 1) % 3], x = F[(q + 2) % 3];  // edge opposite face vertex q
+          int partner = -1, cnt = 0;
+          for (int k = 0; k < nbnd; ++k) {
+            if (k == j) continue;
+            const int* G = w.bv + 3 * k;
+            bool hu = G[0] == u || G[1] == u || G[2] == u;
+            bool hx = G[0] == x || G[1] == x || G[2] == x;
+            if (hu && hx) {
+              ++cnt;
+              partner = k;
+            }
+          }
+          if (pass == 0) {
+            bad = cnt > 1;
+          } else if (cnt == 1 && j < partner) {
+            bool isnew = false;
+            for (int z = 0; z < nfb && !isnew; ++z) {
+              int a = w.fbv[3 * z], b = w.fbv[3 * z + 1];
+              isnew = (a == u && b == x) || (a == x && b == u);
+            }
+            if (!isnew) {
+              const int* G = w.bv + 3 * partner;
+              int apex = (G[0] != u && G[0] != x) ? G[0] : ((G[1] != u && G[1] != x) ? G[1] : G[2]);
+              int bij = w.bin[j];
+              TetRec rec = ld_tet(m, bij >> 2);
+              int f = bij & 3;
+              D3 a = f == 0 ? p : vtx(m, vid(rec.v.x));
+              D3 b = f == 1 ? p : vtx(m, vid(rec.v.y));
+              D3 c = f == 2 ? p : vtx(m, vid(rec.v.z));
+              D3 d = f == 3 ? p : vtx(m, vid(rec.v.w));
+              bad = insphere(a, b, c, d, vtx(m, apex)) > 0;
+            }
+          }
+        }
+        if (pass == 0) topo |= __any_sync(FULLMASK, bad);
+        else nondel |= __any_sync(FULLMASK, bad);
+      }
+      if (pass == 0 && topo) break;
+    }
+    if (topo) {
+      outcome = OUT_UNSPL;
+      reason = RS_CLOSURE;
+      goto done;
+    }
+    if (nondel) {
+      outcome = OUT_UNSPL;
+      reason = RS_STARDEL;
+      goto done;
+    }
+  }
+  // ------------------------------------------------ shortest-edge guard
+  {
+    bool g = false;
+    int items = ncav * 4;
+    for (int base = 0; base < items; base += 32) {
+      int it = base + lane;
+      bool near = false;
+      if (it < items) {
+        int v = vid(geti(m.T[w.cav[it >> 2]].v, it & 3));
+        near = dist2_fixed(p, vtx(m, v)) <= m.guard2;
+      }
+      g |= __any_sync(FULLMASK, near);
+    }
+    if (g) {
+      outcome = OUT_UNSPL;
+      reason = RS_GUARD;
+      goto done;
+    }
+  }
+  // ------------------------------------------------ encroachment
+  {
+    bool rej = false, runspl = false;
+    if (cls == CLS_TET) {
+      for (int base = 0; base < nbnd; base += 32) {
+        int it = base + lane;
+        bool enc = false, un = false;
+        if (it < nbnd) {
+          int bij = w.bin[it];
+          int t = bij >> 2, f = bij & 3;
+          if (face_sub(m.T[t].v, f)) {
+            const int* F = w.bv + 3 * it;
+            if (equatorial(vtx(m, F[0]), vtx(m, F[1]), vtx(m, F[2]), p) < 0) {
+              int s = ts_ptr(m, t)[f];
+              enc = true;
+              if (s >= 0 && s < m.nS) {
+                un = (m.Sflag[s] & F_UNSPL) != 0;
+                m.Smust[s] = 1;
+              } else {
+                atomicAdd(&r.stats[ST_ITER], 1ULL);
+              }
+            }
+          }
+        }
+        rej |= __any_sync(FULLMASK, enc);
+        runspl |= __any_sync(FULLMASK, un);
+      }
+    }
+    // subsegments on cavity tetrahedra: encroached, or deleted by the insertion
+    int items = ncav * 6;
+    for (int base = 0; base < items; base += 32) {
+      int it = base + lane;
+      bool flag = false, un = false;
+      if (it < items) {
+        int t = w.cav[it / 6], e = it % 6;
+        int4 v = m.T[t].v;
+        if (edge_bit(v, e)) {
+          int u = vid(geti(v, edge_i(e))), x = vid(geti(v, edge_j(e)));
+          bool split = sa >= 0 && ((u == sa && x == sb) || (u == sb && x == sa));
+          if (!split) {
+            bool enc = false;
+            if (cls == CLS_TET || cls == CLS_SUBFACE) enc = diametral(vtx(m, u), vtx(m, x), p) < 0;
+            if (!enc) {
+              bool on = false;
+              for (int j = 0; j < nbnd && !on; ++j) {
+                const int* F = w.bv + 3 * j;
+                on = (F[0] == u || F[1] == u || F[2] == u) && (F[0] == x || F[1] == x || F[2] == x);
+              }
+              enc = !on;
+            }
+            if (enc) {
+              int g = hash_lookup(m, ekey(u, x));
+              if (g >= 0) {
+                flag = true;
+                un = (m.Gflag[g] & F_UNSPL) != 0;
+                m.Gmust[g] = 1;
+              }
+            }
+          }
+        }
+      }
+      rej |= __any_sync(FULLMASK, flag);
+      runspl |= __any_sync(FULLMASK, un);
+    }
+    if (rej) {
+      outcome = runspl ? OUT_UNSPL : OUT_REJECT;
+      reason = runspl ? RS_ENCROACH_UNSPL : RS_ENCROACH;
+      goto done;
+    }
+  }
+  // ------------------------------------------------ priority marks
+  {
+    const unsigned long long mk = (r.epoch << 32) | (unsigned long long)(unsigned)i;
+    for (int k = lane; k < ncav; k += 32) atomicMin(&m.Tmark[w.cav[k]], mk);
+    for (int k = lane; k < nbnd; k += 32)
+      if (w.bout[k] >= 0) atomicMin(&m.Tmark[w.bout[k] >> 2], mk);
+    for (int k = lane; k < nf; k += 32) atomicMin(&m.Smark[w.fcav[k]], mk);
+    for (int k = lane; k < nfb; k += 32) {
+      int sk = w.fbnd[k];
+      int nb = sn_ptr(m, sk >> 2)[sk & 3];
+      if (nb >= 0) atomicMin(&m.Smark[nb], mk);
+    }
+  }
+
+done:
+  __syncwarp();
+  if (retry) {
+    if (lane == 0) {
+      set_status(r, i, OUT_RETRY, RS_NONE);
+      slab[0] = slab[1] = slab[2] = slab[3] = 0;
+    }
+    return;
+  }
+  if (lane == 0) {
+    set_status(r, i, outcome, reason);
+    slab[0] = ncav;
+    slab[1] = nbnd;
+    slab[2] = nf;
+    slab[3] = nfb;
+  }
+  if (outcome == OUT_OK) {
+    // lists for selection and insertion (tier 2 works in place)
+    if (w.cav != slab + L::OFF_CAV) {
+      for (int k = lane; k < ncav; k += 32) slab[L::OFF_CAV + k] = w.cav[k];
+      for (int k = lane; k < nbnd; k += 32) {
+        slab[L::OFF_BIN + k] = w.bin[k];
+        slab[L::OFF_BOUT + k] = w.bout[k];
+      }
+      for (int k = lane; k < nf; k += 32) slab[L::OFF_FCAV + k] = w.fcav[k];
+      for (int k = lane; k < nfb; k += 32) slab[L::OFF_FBND + k] = w.fbnd[k];
+      for (int k = lane; k < 3 * nbnd; k += 32) slab[L::OFF_BV + k] = w.bv[k];
+      for (int k = lane; k < 3 * nfb; k += 32) slab[L::OFF_FBV + k] = w.fbv[k];
+    }
+  } else if (outcome == OUT_REJECT || reason == RS_GUARD || reason == RS_STARDEL ||
+             reason == RS_ENCROACH_UNSPL) {
+    // the cavity is complete: keep its tets for the round report
+    if (w.cav != slab + L::OFF_CAV)
+      for (int k = lane; k < min(ncav, C::CAPC); k += 32) slab[L::OFF_CAV + k] = w.cav[k];
+  }
+}
+
+// tier 1: shared-memory workspaces, one per warp
+constexpr int kWarps1 = 8;
+struct Smem1 {
+  int cav[Tier1::CAPC];
+  int hset[Tier1::HCAP];
+  int bin[Tier1::CAPB];
+  int bout[Tier1::CAPB];
+  int bv[3 * Tier1::CAPB];
+  int fcav[Tier1::CAPF];
+  int fbnd[Tier1::CAPFB];
+  int fbv[3 * Tier1::CAPFB];
+};
+
+__global__ void __launch_bounds__(32 * kWarps1) k_grow1(DevMesh m, DevRound r) {
+  extern __shared__ int smraw[];
+  Smem1* sm = reinterpret_cast<Smem1*>(smraw) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  Ws w{sm->cav, sm->hset, sm->bin, sm->bout, sm->bv, sm->fcav, sm->fbnd, sm->fbv};
+  int warp = blockIdx.x * kWarps1 + (threadIdx.x >> 5);
+  int nw = gridDim.x * kWarps1;
+  for (int i = warp; i < r.n; i += nw) {
+    int* slab = r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
+    grow_one<Tier1>(m, r, i, w, slab, lane);
+    __syncwarp();
+  }
+}
+
+// tier 2: global-memory workspaces; the slab doubles as the list storage
+constexpr int kWs2Extra = Tier2::HCAP;
+__global__ void k_grow2(DevMesh m, DevRound r) {
+  int lane = threadIdx.x & 31;
+  int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int nw = gridDim.x * (blockDim.x >> 5);
+  using L = SlabLayout<Tier2>;
+  int* extra = r.ws2 + (size_t)warp * kWs2Extra;
+  for (int j = warp; j < r.n2; j += nw) {
+    int i = r.list2[j];
+    int* slab = r.slab2 + (size_t)j * L::STRIDE;
+    Ws w{slab + L::OFF_CAV, extra, slab + L::OFF_BIN, slab + L::OFF_BOUT,
+         slab + L::OFF_BV, slab + L::OFF_FCAV, slab + L::OFF_FBND, slab + L::OFF_FBV};
+    grow_one<Tier2>(m, r, i, w, slab, lane);
+    __syncwarp();
+    if (lane == 0 && r.status[i] == OUT_RETRY) set_status(r, i, OUT_UNSPL, RS_OVERFLOW);
+  }
+}
+
+// ============================================================== selection
+__device__ __forceinline__ const int* slab_of(const DevRound& r, int i, bool& tier2) {
+  int j = r.slab2_of ? r.slab2_of[i] : -1;
+  tier2 = j >= 0;
+  if (tier2) return r.slab2 + (size_t)j * SlabLayout<Tier2>::STRIDE;
+  return r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
+}
+
+__global__ void k_select(DevMesh m, DevRound r) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < r.n; i += nw) {
+    int st = r.status[i];
+    int outcome = st & 0xff;
+    bool t2;
+    const int* slab = slab_of(r, i, t2);
+    int ncav = slab[0], nbnd = slab[1], nf = slab[2], nfb = slab[3];
+    int offC = t2 ? SlabLayout<Tier2>::OFF_CAV : SlabLayout<Tier1>::OFF_CAV;
+    int offBO = t2 ? SlabLayout<Tier2>::OFF_BOUT : SlabLayout<Tier1>::OFF_BOUT;
+    int offF = t2 ? SlabLayout<Tier2>::OFF_FCAV : SlabLayout<Tier1>::OFF_FCAV;
+    int offFB = t2 ? SlabLayout<Tier2>::OFF_FBND : SlabLayout<Tier1>::OFF_FBND;
+    bool surv = false;
+    if (outcome == OUT_OK) {
+      const unsigned long long mk = (r.epoch << 32) | (unsigned long long)(unsigned)i;
+      bool lost = false;
+      for (int k = lane; k < ncav; k += 32) lost |= m.Tmark[slab[offC + k]] != mk;
+      for (int k = lane; k < nbnd; k += 32) {
+        int b = slab[offBO + k];
+        if (b >= 0) lost |= m.Tmark[b >> 2] != mk;
+      }
+      for (int k = lane; k < nf; k += 32) lost |= m.Smark[slab[offF + k]] != mk;
+      for (int k = lane; k < nfb; k += 32) {
+        int sk = slab[offFB + k];
+        int nb = sn_ptr(m, sk >> 2)[sk & 3];
+        if (nb >= 0) lost |= m.Smark[nb] != mk;
+      }
+      surv = !__any_sync(FULLMASK, lost);
+    }
+    if (lane == 0) {
+      r.survived[i] = surv ? 1 : 0;
+      int4 c = make_int4(0, 0, 0, 0);
+      if (surv) c = make_int4(r.cls == CLS_POINT ? 0 : 1, nbnd, nfb, r.cls == CLS_SUBSEG ? 1 : 0);
+      r.counts[i] = c;
+      int e = r.cand[i];
+      if (outcome == OUT_UNSPL) {
+        if (r.cls == CLS_SUBSEG) m.Gflag[e] |= F_UNSPL;
+        else if (r.cls == CLS_SUBFACE) m.Sflag[e] |= F_UNSPL;
+        else if (r.cls == CLS_TET) m.Tflag[e] |= F_UNSPL;
+        else r.point_state[e] = 2;
+      }
+      if (outcome == OUT_OK) atomicAdd(&r.stats[surv ? ST_SURV : ST_OK], 1ULL);
+      else if (outcome == OUT_REJECT) atomicAdd(&r.stats[ST_REJECT], 1ULL);
+      else atomicAdd(&r.stats[ST_UNSPL], 1ULL);
+    }
+  }
+}
+
+// ============================================================== insertion
+// One warp per kept point: new tetrahedra p + boundary face, links to the shell
+// and inside the star, new subfaces p + facet boundary edge, retire the region.
+__global__ void k_insert(DevMesh m, DevRound r, int* hint) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < r.n; i += nw) {
+    if (!r.survived[i]) continue;
+    bool t2;
+    const int* slab = slab_of(r, i, t2);
+#define SLAB_OFF(name) (t2 ? SlabLayout<Tier2>::name : SlabLayout<Tier1>::name)
+    const int ncav = slab[0], nbnd = slab[1], nf = slab[2], nfb = slab[3];
+    const int* cav = slab + SLAB_OFF(OFF_CAV);
+    const int* bin = slab + SLAB_OFF(OFF_BIN);
+    const int* bout = slab + SLAB_OFF(OFF_BOUT);
+    const int* fcav = slab + SLAB_OFF(OFF_FCAV);
+    const int* fbnd = slab + SLAB_OFF(OFF_FBND);
+    const int* bv = slab + SLAB_OFF(OFF_BV);
+    const int* fbv = slab + SLAB_OFF(OFF_FBV);
+#undef SLAB_OFF
+    const int4 off = r.offs[i];
+    const int e = r.cand[i];
+    const int vp = r.cls == CLS_POINT ? e : m.nV + off.x;
+    const int t0 = m.nT + off.y;
+    const int s0 = m.nS + off.z;
+    int sa = -1, sb = -1;
+    if (r.cls == CLS_SUBSEG) {
+      int4 G = m.GV[e];
+      sa = G.x;
+      sb = G.y;
+    }
+    if (lane == 0 && r.cls != CLS_POINT) m.V[vp] = r.sp[i];
+    // step 1: new tetrahedra (p replaces the vertex opposite each boundary face)
+    for (int j = lane; j < nbnd; j += 32) {
+      int t = bin[j] >> 2, f = bin[j] & 3;
+      TetRec R = ld_tet(m, t);
+      int nid = t0 + j;
+      int4 nv;
+      for (int k = 0; k < 4; ++k) seti(nv, k, k == f ? vp : vid(geti(R.v, k)));
+      if (face_sub(R.v, f)) seti(nv, f, geti(nv, f) | (1 << kSubBit));
+      for (int ed = 0; ed < 6; ++ed) {
+        int a = edge_i(ed), b = edge_j(ed);
+        bool mark;
+        if (a != f && b != f) {
+          mark = edge_bit(R.v, ed);
+        } else {
+          int other = vid(geti(R.v, a == f ? b : a));
+          mark = r.cls == CLS_SUBSEG && (other == sa || other == sb);
+        }
+        if (mark) seti(nv, ed >> 1, geti(nv, ed >> 1) | (1 << (29 + (ed & 1))));
+      }
+      TetRec N;
+      N.v = nv;
+      N.n = make_int4(-1, -1, -1, -1);
+      seti(N.n, f, bout[j]);
+      m.T[nid] = N;
+      int4 ts = make_int4(-1, -1, -1, -1);
+      if (face_sub(R.v, f)) {
+        int s = ts_ptr(m, t)[f];
+        seti(ts, f, s);
+        if (s >= 0 && s < m.nS) m.SN[s].w = (nid << 2) | f;
+        else atomicAdd(&r.stats[ST_ITER], 1ULL);
+      }
+      m.TS[nid] = ts;
+      m.Tmark[nid] = ~0ULL;
+      m.Tfwd[nid] = -1;
+      if (bout[j] >= 0) tet_n_ptr(m, bout[j] >> 2)[bout[j] & 3] = (nid << 2) | f;
+    }
+    __syncwarp();
+    // step 2: links inside the star, matched by the boundary faces' shared edges
+    for (int it = lane; it < nbnd * 3; it += 32) {
+      int j = it / 3, q = it % 3;
+      const int* F = bv + 3 * j;
+      int u = F[(q + 1) % 3], x = F[(q + 2) % 3];
+      int t = bin[j] >> 2, f = bin[j] & 3;
+      // position in tet j of the face vertex q (the apex across the new face)
+      TetRec R = ld_tet(m, t);
+      int g = -1;
+      for (int k = 0; k < 4; ++k)
+        if (k != f && vid(geti(R.v, k)) == F[q]) g = k;
+      int link = -1;
+      for (int k2 = 0; k2 < nbnd; ++k2) {
+        if (k2 == j) continue;
+        const int* G = bv + 3 * k2;
+        int pu = G[0] == u ? 0 : (G[1] == u ? 1 : (G[2] == u ? 2 : -1));
+        int px = G[0] == x ? 0 : (G[1] == x ? 1 : (G[2] == x ? 2 : -1));
+        if (pu >= 0 && px >= 0) {
+          int apexv = G[3 - pu - px];
+          int t2_ = bin[k2] >> 2, f2 = bin[k2] & 3;
+          TetRec R2 = ld_tet(m, t2_);
+          int h = -1;
+          for (int k = 0; k < 4; ++k)
+            if (k != f2 && vid(geti(R2.v, k)) == apexv) h = k;
+          link = h >= 0 ? (((t0 + k2) << 2) | h) : -1;
+          break;
+        }
+      }
+      if (g >= 0) tet_n_ptr(m, t0 + j)[g] = link;
+      else atomicAdd(&r.stats[ST_ITER], 1ULL);
+    }
+    __syncwarp();
+    // step 3: new subfaces (p joined to each facet boundary edge)
+    for (int k = lane; k < nfb; k += 32) {
+      int s = fbnd[k] >> 2, ke = fbnd[k] & 3;
+      int u = fbv[3 * k], x = fbv[3 * k + 1], fid = fbv[3 * k + 2];
+      int ns = s0 + k;
+      m.SV[ns] = make_int4(vp, u, x, fid);
+      int outer = geti(m.SN[s], ke);
+      int4 sn = make_int4(outer, -1, -1, -1);
+      if (outer >= 0) {
+        int* o = sn_ptr(m, outer);
+        for (int q = 0; q < 3; ++q)
+          if (o[q] == s) o[q] = ns;
+      }
+      // across (x, p) and (p, u): the other new subface of this facet there
+      for (int k2 = 0; k2 < nfb; ++k2) {
+        if (k2 == k || fbv[3 * k2 + 2] != fid) continue;
+        int u2 = fbv[3 * k2], x2 = fbv[3 * k2 + 1];
+        if (u2 == x || x2 == x) sn.y = s0 + k2;
+        if (u2 == u || x2 == u) sn.z = s0 + k2;
+      }
+      if (sa >= 0 && (x == sa || x == sb)) sn.y = -1;  // a new subsegment bounds it
+      if (sa >= 0 && (u == sa || u == sb)) sn.z = -1;
+      // the new tetrahedra on either side of the new subface
+      int tw = -1;
+      for (int j = 0; j < nbnd; ++j) {
+        const int* F = bv + 3 * j;
+        bool hu = F[0] == u || F[1] == u || F[2] == u;
+        bool hx = F[0] == x || F[1] == x || F[2] == x;
+        if (!(hu && hx)) continue;
+        int apexv = (F[0] != u && F[0] != x) ? F[0] : ((F[1] != u && F[1] != x) ? F[1] : F[2]);
+        int t = bin[j] >> 2, f = bin[j] & 3;
+        TetRec R = ld_tet(m, t);
+        int g = -1;
+        for (int q = 0; q < 4; ++q)
+          if (q != f && vid(geti(R.v, q)) == apexv) g = q;
+        int nid = t0 + j;
+        if (g < 0) {
+          atomicAdd(&r.stats[ST_ITER], 1ULL);
+          continue;
+        }
+        ts_ptr(m, nid)[g] = ns;
+        atomicOr(&tet_v_ptr(m, nid)[g], 1 << kSubBit);
+        if (tw < 0) tw = (nid << 2) | g;
+      }
+      sn.w = tw;
+      m.SN[ns] = sn;
+      m.Sflag[ns] = 0;
+      m.Smust[ns] = 0;
+      m.Smark[ns] = ~0ULL;
+    }
+    __syncwarp();
+    // step 4: retire the cavity and the facet part
+    for (int k = lane; k < ncav; k += 32) {
+      int t = cav[k];
+      m.Tflag[t] |= F_DEAD;
+      m.Tfwd[t] = t0;
+    }
+    for (int k = lane; k < nf; k += 32) m.Sflag[fcav[k]] |= F_DEAD;
+    // step 5: the split subsegment becomes (a, p) and (p, b)
+    if (r.cls == CLS_SUBSEG) {
+      int ta = -1, tb = -1;
+      for (int j = lane; j < nbnd; j += 32) {
+        const int* F = bv + 3 * j;
+        if (F[0] == sa || F[1] == sa || F[2] == sa) ta = t0 + j;
+        if (F[0] == sb || F[1] == sb || F[2] == sb) tb = t0 + j;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        ta = max(ta, __shfl_xor_sync(FULLMASK, ta, o));
+        tb = max(tb, __shfl_xor_sync(FULLMASK, tb, o));
+      }
+      if (lane == 0) {
+        int4 G = m.GV[e];
+        int g2 = m.nG + off.w;
+        m.GV[e] = make_int4(G.x, vp, G.z, ta);
+        m.GV[g2] = make_int4(vp, G.y, G.z, tb);
+        m.Gflag[e] = 0;
+        m.Gmust[e] = 0;
+        m.Gflag[g2] = 0;
+        m.Gmust[g2] = 0;
+        hash_insert(m, ekey(G.x, vp), e);
+        hash_insert(m, ekey(vp, G.y), g2);
+      }
+    }
+    __syncwarp();
+    // step 6: subsegment tet references and quality of the new tetrahedra
+    for (int j = lane; j < nbnd; j += 32) {
+      int nid = t0 + j;
+      int4 v = m.T[nid].v;
+      for (int ed = 0; ed < 6; ++ed) {
+        if (!edge_bit(v, ed)) continue;
+        int a = vid(geti(v, edge_i(ed))), b = vid(geti(v, edge_j(ed)));
+        if (a == vp || b == vp) continue;
+        int g = hash_lookup(m, ekey(a, b));
+        if (g >= 0) m.GV[g].w = nid;
+      }
+      int s4[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
+      sort4(s4);
+      bool bad = tet_bad_fixed(vtx(m, s4[0]), vtx(m, s4[1]), vtx(m, s4[2]), vtx(m, s4[3]), r.B);
+      m.Tflag[nid] = bad ? F_BAD : 0;
+    }
+    if (lane == 0 && r.cls == CLS_POINT) {
+      r.point_state[e] = 1;
+      hint[e] = t0;
+    }
+  }
+}
+
+// ============================================================ maintenance
+__global__ void k_follow_fwd(DevMesh m, int* hint, const int* state, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (state[i] != 0) continue;
+    int t = hint[i];
+    for (int it = 0; it < 1 << 20 && (m.Tflag[t] & F_DEAD); ++it) t = m.Tfwd[t];
+    hint[i] = t;
+  }
+}
+
+__global__ void k_compact_flags(DevMesh m, int* alive) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x)
+    alive[t] = (m.Tflag[t] & F_DEAD) ? 0 : 1;
+}
+// newid = exclusive scan of alive; move live tets to T2 with remapped links
+__global__ void k_compact_move(DevMesh m, const int* newid, TetRec* T2, int4* TS2,
+                               unsigned char* F2) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x) {
+    if (m.Tflag[t] & F_DEAD) continue;
+    TetRec R = m.T[t];
+    for (int f = 0; f < 4; ++f) {
+      int nb = geti(R.n, f);
+      if (nb >= 0) seti(R.n, f, (newid[nb >> 2] << 2) | (nb & 3));
+    }
+    int d = newid[t];
+    T2[d] = R;
+    TS2[d] = m.TS[t];
+    F2[d] = m.Tflag[t];
+  }
+}
+__global__ void k_compact_hints(DevMesh m, const int* newid, int* hint, int nh) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nh; i += gridDim.x * blockDim.x) {
+    int t = hint[i];
+    for (int it = 0; it < 1 << 20 && (m.Tflag[t] & F_DEAD); ++it) t = m.Tfwd[t];
+    hint[i] = newid[t];
+  }
+}
+__global__ void k_compact_fix(DevMesh m, const int* newid) {
+  int n = m.nS + m.nG;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < m.nS) {
+      if (m.Sflag[i] & F_DEAD) continue;
+      int w = m.SN[i].w;
+      m.SN[i].w = (newid[w >> 2] << 2) | (w & 3);
+    } else {
+      int g = i - m.nS;
+      if (m.Gflag[g] & F_DEAD) continue;
+      m.GV[g].w = newid[m.GV[g].w];
+    }
+  }
+}
+
+// ================================================================= export
+__global__ void k_live_flags(const unsigned char* flag, int n, int* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = (flag[i] & F_DEAD) ? 0 : 1;
+}
+__global__ void k_gather_tets(DevMesh m, const int* pos, int4* out, unsigned char* oflag) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x) {
+    if (m.Tflag[t] & F_DEAD) continue;
+    int4 v = m.T[t].v;
+    int d = pos[t];
+    out[d] = make_int4(vid(v.x), vid(v.y), vid(v.z), vid(v.w));
+    oflag[d] = (m.Tflag[t] & F_UNSPL) ? 2 : 0;
+  }
+}
+__global__ void k_gather_subfaces(DevMesh m, const int* pos, int4* out, unsigned char* oflag) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m.nS; s += gridDim.x * blockDim.x) {
+    if (m.Sflag[s] & F_DEAD) continue;
+    int d = pos[s];
+    out[d] = m.SV[s];
+    oflag[d] = (m.Smust[s] ? 1 : 0) | ((m.Sflag[s] & F_UNSPL) ? 2 : 0);
+  }
+}
+__global__ void k_gather_subsegs(DevMesh m, const int* pos, int4* out, unsigned char* oflag) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < m.nG; g += gridDim.x * blockDim.x) {
+    if (m.Gflag[g] & F_DEAD) continue;
+    int d = pos[g];
+    out[d] = m.GV[g];
+    oflag[d] = (m.Gmust[g] ? 1 : 0) | ((m.Gflag[g] & F_UNSPL) ? 2 : 0);
+  }
+}
+// cavity tets of each reported candidate as sorted vertex ids
+__global__ void k_report_cav(DevMesh m, DevRound r, const int* offs, int4* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
+    bool t2;
+    const int* slab = slab_of(r, i, t2);
+    int n = offs[i + 1] - offs[i];
+    const int* cav = slab + (t2 ? SlabLayout<Tier2>::OFF_CAV : SlabLayout<Tier1>::OFF_CAV);
+    for (int k = 0; k < n; ++k) {
+      int4 v = m.T[cav[k]].v;
+      int s[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
+      sort4(s);
+      out[offs[i] + k] = make_int4(s[0], s[1], s[2], s[3]);
+    }
+  }
+}
+
+// ================================================================ wrappers
+static inline int grid_for(long n, int block) {
+  long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)g;
+}
+
+void launch_init_tets(const DevMesh& m, const int4* tets, int n, cudaStream_t s) {
+  k_init_tets<<<grid_for(n, 256), 256, 0, s>>>(m, tets, n);
+}
+void launch_face_keys(const DevMesh& m, unsigned long long* hi, unsigned int* lo, int* val,
+                      cudaStream_t s) {
+  k_face_keys<<<grid_for(4L * m.nT, 256), 256, 0, s>>>(m, hi, lo, val);
+}
+void launch_pair_faces(const DevMesh& m, const unsigned long long* hi, const unsigned int* lo,
+                       const int* val, int n, int* err, cudaStream_t s) {
+  k_pair_faces<<<grid_for(n, 256), 256, 0, s>>>(m, hi, lo, val, n, err);
+}
+void launch_label_subfaces(const DevMesh& m, const int4* tris, int n, const unsigned long long* hi,
+                           const unsigned int* lo, const int* val, int nfaces, int* err,
+                           cudaStream_t s) {
+  k_label_subfaces<<<grid_for(n, 256), 256, 0, s>>>(m, tris, n, hi, lo, val, nfaces, err);
+}
+void launch_subface_edge_keys(const DevMesh& m, unsigned long long* hi, unsigned int* lo,
+                              int* val, cudaStream_t s) {
+  k_subface_edge_keys<<<grid_for(3L * m.nS, 256), 256, 0, s>>>(m, hi, lo, val);
+}
+void launch_pair_subface_edges(const DevMesh& m, const unsigned long long* hi,
+                               const unsigned int* lo, const int* val, int n, int* err,
+                               cudaStream_t s) {
+  k_pair_subface_edges<<<grid_for(n, 256), 256, 0, s>>>(m, hi, lo, val, n, err);
+}
+void launch_hash_clear(const DevMesh& m, cudaStream_t s) {
+  k_hash_clear<<<grid_for((long)m.hmask + 1, 256), 256, 0, s>>>(m);
+}
+void launch_hash_insert_subsegs(const DevMesh& m, int g0, int g1, cudaStream_t s) {
+  if (g1 > g0) k_hash_insert_subsegs<<<grid_for(g1 - g0, 256), 256, 0, s>>>(m, g0, g1);
+}
+void launch_mark_edges(const DevMesh& m, cudaStream_t s) {
+  k_mark_edges<<<grid_for(m.nT, 256), 256, 0, s>>>(m);
+}
+void launch_check_create(const DevMesh& m, int* err, cudaStream_t s) {
+  k_check_create<<<grid_for((long)m.nT + m.nG, 256), 256, 0, s>>>(m, err);
+}
+void launch_recompute_bad(const DevMesh& m, double B, cudaStream_t s) {
+  k_recompute_bad<<<grid_for(m.nT, 256), 256, 0, s>>>(m, B);
+}
+void launch_classify(const DevMesh& m, unsigned char* candS, unsigned char* candG,
+                     unsigned char* candT, int* err, cudaStream_t s) {
+  k_classify<<<grid_for((long)m.nG + m.nS + m.nT, 256), 256, 0, s>>>(m, candS, candG, candT, err);
+}
+void launch_prio(const DevMesh& m, int cls, const int* elems, int n, unsigned long long* keys,
+                 cudaStream_t s) {
+  if (n > 0) k_prio<<<grid_for(n, 256), 256, 0, s>>>(m, cls, elems, n, keys);
+}
+void launch_tiefix(const DevMesh& m, int cls, const unsigned long long* keys, int* elems, int n,
+                   cudaStream_t s) {
+  if (n > 1) k_tiefix<<<grid_for(n, 256), 256, 0, s>>>(m, cls, keys, elems, n);
+}
+void launch_split(const DevMesh& m, const DevRound& r, cudaStream_t s) {
+  if (r.n > 0) k_split<<<grid_for(r.n, 256), 256, 0, s>>>(m, r);
+}
+void launch_locate(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s) {
+  if (r.n > 0) k_locate<<<grid_for(r.n, 128), 128, 0, s>>>(m, r, hint);
+}
+void launch_grow1(const DevMesh& m, const DevRound& r, cudaStream_t s) {
+  if (r.n <= 0) return;
+  static bool attr = false;
+  size_t smem = sizeof(Smem1) * kWarps1;
+  if (!attr) {
+    cudaFuncSetAttribute(k_grow1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  long blocks = ((long)r.n + kWarps1 - 1) / kWarps1;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_grow1<<<(int)blocks, 32 * kWarps1, smem, s>>>(m, r);
+}
+void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s) {
+  if (r.n2 <= 0) return;
+  int blocks = (nwarps + 1) / 2;
+  k_grow2<<<blocks, 64, 0, s>>>(m, r);
+}
+void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s) {
+  if (r.n > 0) k_select<<<grid_for(32L * r.n, 256), 256, 0, s>>>(m, r);
+}
+void launch_insert(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s) {
+  if (r.n > 0) k_insert<<<grid_for(32L * r.n, 256), 256, 0, s>>>(m, r, hint);
+}
+void launch_compact_flags(const DevMesh& m, int* alive, cudaStream_t s) {
+  k_compact_flags<<<grid_for(m.nT, 256), 256, 0, s>>>(m, alive);
+}
+void launch_compact_move(const DevMesh& m, const int* newid, TetRec* T2, int4* TS2,
+                         unsigned char* F2, int* hint, int nhint, cudaStream_t s) {
+  if (nhint > 0) k_compact_hints<<<grid_for(nhint, 256), 256, 0, s>>>(m, newid, hint, nhint);
+  k_compact_move<<<grid_for(m.nT, 256), 256, 0, s>>>(m, newid, T2, TS2, F2);
+}
+void launch_compact_fix(const DevMesh& m, const int* newid, cudaStream_t s) {
+  k_compact_fix<<<grid_for((long)m.nS + m.nG, 256), 256, 0, s>>>(m, newid);
+}
+void launch_follow_fwd(const DevMesh& m, int* hint, const int* state, int n, cudaStream_t s) {
+  if (n > 0) k_follow_fwd<<<grid_for(n, 256), 256, 0, s>>>(m, hint, state, n);
+}
+void launch_live_flags(const unsigned char* flag, int n, int* out, cudaStream_t s) {
+  if (n > 0) k_live_flags<<<grid_for(n, 256), 256, 0, s>>>(flag, n, out);
+}
+void launch_gather_tets(const DevMesh& m, const int* pos, int4* out, unsigned char* oflag,
+                        cudaStream_t s) {
+  if (m.nT > 0) k_gather_tets<<<grid_for(m.nT, 256), 256, 0, s>>>(m, pos, out, oflag);
+}
+void launch_gather_subfaces(const DevMesh& m, const int* pos, int4* out, unsigned char* oflag,
+                            cudaStream_t s) {
+  if (m.nS > 0) k_gather_subfaces<<<grid_for(m.nS, 256), 256, 0, s>>>(m, pos, out, oflag);
+}
+void launch_gather_subsegs(const DevMesh& m, const int* pos, int4* out, unsigned char* oflag,
+                           cudaStream_t s) {
+  if (m.nG > 0) k_gather_subsegs<<<grid_for(m.nG, 256), 256, 0, s>>>(m, pos, out, oflag);
+}
+void launch_report_cav(const DevMesh& m, const DevRound& r, const int* offs, int4* out,
+                       cudaStream_t s) {
+  if (r.n > 0) k_report_cav<<<grid_for(r.n, 128), 128, 0, s>>>(m, r, offs, out);
+}
+
+
+// =========================================================== predicate probe
+// Batch evaluation of the device predicates and formulas (for checking them
+// against an exact reference). Each item holds 16 doubles of input.
+__global__ void k_eval_pred(int kind, const double* in, int n, int* sign, double* outp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double* q = in + 16 * (size_t)i;
+    D3 a{q[0], q[1], q[2]}, b{q[3], q[4], q[5]}, c{q[6], q[7], q[8]}, d{q[9], q[10], q[11]},
+        e{q[12], q[13], q[14]};
+    int sg = 0;
+    D3 o{0, 0, 0};
+    switch (kind) {
+      case 0: sg = orient3d(a, b, c, d); break;
+      case 1: sg = insphere(a, b, c, d, e); break;
+      case 2: sg = diametral(a, b, c); break;
+      case 3: sg = equatorial(a, b, c, d); break;
+      case 4: {
+        D3 off;
+        sg = tet_circumcenter_fixed(a, b, c, d, o, off) ? 1 : 0;
+        break;
+      }
+      case 5: sg = tri_circumcenter_fixed(a, b, c, o) ? 1 : 0; break;
+      case 6: o = midpoint_fixed(a, b); sg = 1; break;
+      case 7: sg = tet_bad_fixed(a, b, c, d, q[12]) ? 1 : 0; break;
+      case 8: sg = orient3d_exact(a, b, c, d); break;
+      case 9: sg = insphere_exact(a, b, c, d, e); break;
+      case 10: sg = equatorial_exact(a, b, c, d); break;
+      case 11: sg = diametral_exact(a, b, c); break;
+    }
+    sign[i] = sg;
+    if (outp) {
+      outp[3 * (size_t)i] = o.x;
+      outp[3 * (size_t)i + 1] = o.y;
+      outp[3 * (size_t)i + 2] = o.z;
+    }
+  }
+}
+void launch_eval_pred(int kind, const double* in, int n, int* sign, double* outp, cudaStream_t s) {
+  if (n > 0) k_eval_pred<<<grid_for(n, 128), 128, 0, s>>>(kind, in, n, sign, outp);
+}
+
+int exact_overflow_flag(cudaStream_t s, bool reset) {
+  int v = 0;
+  cudaMemcpyFromSymbolAsync(&v, g_exact_overflow, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (reset && v) {
+    int z = 0;
+    cudaMemcpyToSymbolAsync(g_exact_overflow, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+  }
+  return v;
+}
+
+}  // namespace cdr

@@ -1,0 +1,66 @@
+// Launch wrappers exported by kernels.cu to the host driver (api.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mesh.cuh"
+
+namespace cdr {
+
+// create / labels
+void launch_init_tets(const DevMesh& m, const int4* tets, int n, cudaStream_t s);
+void launch_face_keys(const DevMesh& m, unsigned long long* hi, unsigned int* lo, int* val,
+                      cudaStream_t s);
+void launch_pair_faces(const DevMesh& m, const unsigned long long* hi, const unsigned int* lo,
+                       const int* val, int n, int* err, cudaStream_t s);
+void launch_label_subfaces(const DevMesh& m, const int4* tris, int n, const unsigned long long* hi,
+                           const unsigned int* lo, const int* val, int nfaces, int* err,
+                           cudaStream_t s);
+void launch_subface_edge_keys(const DevMesh& m, unsigned long long* hi, unsigned int* lo,
+                              int* val, cudaStream_t s);
+void launch_pair_subface_edges(const DevMesh& m, const unsigned long long* hi,
+                               const unsigned int* lo, const int* val, int n, int* err,
+                               cudaStream_t s);
+void launch_hash_clear(const DevMesh& m, cudaStream_t s);
+void launch_hash_insert_subsegs(const DevMesh& m, int g0, int g1, cudaStream_t s);
+void launch_mark_edges(const DevMesh& m, cudaStream_t s);
+void launch_check_create(const DevMesh& m, int* err, cudaStream_t s);
+void launch_recompute_bad(const DevMesh& m, double B, cudaStream_t s);
+
+// classification and queues
+void launch_classify(const DevMesh& m, unsigned char* candS, unsigned char* candG,
+                     unsigned char* candT, int* err, cudaStream_t s);
+void launch_prio(const DevMesh& m, int cls, const int* elems, int n, unsigned long long* keys,
+                 cudaStream_t s);
+void launch_tiefix(const DevMesh& m, int cls, const unsigned long long* keys, int* elems, int n,
+                   cudaStream_t s);
+
+// one round
+void launch_split(const DevMesh& m, const DevRound& r, cudaStream_t s);
+void launch_locate(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s);
+void launch_grow1(const DevMesh& m, const DevRound& r, cudaStream_t s);
+void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s);
+void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s);
+void launch_insert(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s);
+
+// maintenance
+void launch_compact_flags(const DevMesh& m, int* alive, cudaStream_t s);
+void launch_compact_move(const DevMesh& m, const int* newid, TetRec* T2, int4* TS2,
+                         unsigned char* F2, int* hint, int nhint, cudaStream_t s);
+void launch_compact_fix(const DevMesh& m, const int* newid, cudaStream_t s);
+void launch_follow_fwd(const DevMesh& m, int* hint, const int* state, int n, cudaStream_t s);
+
+// export helpers
+void launch_live_flags(const unsigned char* flag, int n, int* out, cudaStream_t s);
+void launch_gather_tets(const DevMesh& m, const int* pos, int4* out, unsigned char* oflag,
+                        cudaStream_t s);
+void launch_gather_subfaces(const DevMesh& m, const int* pos, int4* out, unsigned char* oflag,
+                            cudaStream_t s);
+void launch_gather_subsegs(const DevMesh& m, const int* pos, int4* out, unsigned char* oflag,
+                           cudaStream_t s);
+void launch_report_cav(const DevMesh& m, const DevRound& r, const int* offs, int4* out,
+                       cudaStream_t s);
+
+void launch_eval_pred(int kind, const double* in, int n, int* sign, double* outp, cudaStream_t s);
+int exact_overflow_flag(cudaStream_t s, bool reset);
+
+}  // namespace cdr

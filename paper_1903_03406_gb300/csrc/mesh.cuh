@@ -1,0 +1,147 @@
+// Device mesh layout and the per-round buffers.
+//
+// Layout (GB300: every gather is a 32-byte sector, the mesh of the 100k-point
+// workload fits the 129 MB L2):
+//   V      V4 per vertex (x, y, z, unused)            one sector per vertex
+//   T      TetRec per tetrahedron: int4 v, int4 n           one sector per tet
+//          v.k : vertex id (bits 0..27) | face k is a subface (bit 28) |
+//                edge marks (bits 29..30 of v.x, v.y, v.z: subsegment on edges
+//                01 02 | 03 12 | 13 23)
+//          n.k : neighbour across face k as (tet << 2 | its face), -1 on the hull
+//   TS     int4 per tet: subface id on each face (-1), read only for marked faces
+//   Tflag  bit0 dead, bit1 bad, bit2 unsplittable
+//   Tmark  64-bit priority marks (round epoch << 32 | candidate rank)
+//   Tfwd   for a dead tet, one tet of the star that replaced it
+//   SV     int4 per subface (a, b, c, facet)
+//   SN     int4 per subface: facet neighbour across edge k (opposite vertex k),
+//          -1 across a subsegment; .w = one adjacent tet as (tet << 2 | face)
+//   Sflag  bit0 dead, bit2 unsplittable; Smust: split first (set by refusals)
+//   GV     int4 per subsegment (a, b, segment id, one tet containing the edge)
+//   Gflag  bit0 dead, bit2 unsplittable; Gmust as Smust
+//   FQ     V4 per facet: reference point off the facet's plane
+//   HK/HV  open-addressing hash (min<<32|max) -> subsegment id
+// Paper passages: elements, subsegments, subfaces (Sec. 1, Sec. 2).
+#pragma once
+#include <cstdint>
+
+namespace cdr {
+
+// 32-byte vertex / point record: one sector per gather
+struct __align__(32) V4 {
+  double x, y, z, w;
+};
+__host__ __device__ inline V4 make_v4(double x, double y, double z, double w) {
+  V4 v;
+  v.x = x;
+  v.y = y;
+  v.z = z;
+  v.w = w;
+  return v;
+}
+
+constexpr int kVidMask = 0x0FFFFFFF;
+constexpr int kSubBit = 28;
+constexpr int kMaxVerts = 1 << 28;
+constexpr int kMaxTets = 1 << 29;
+
+enum : uint8_t { F_DEAD = 1, F_BAD = 2, F_UNSPL = 4 };
+enum { CLS_SUBSEG = 0, CLS_SUBFACE = 1, CLS_TET = 2, CLS_POINT = 3 };
+enum { OUT_OK = 0, OUT_REJECT = 1, OUT_UNSPL = 2, OUT_RETRY = 3 };
+enum {
+  RS_NONE = 0,
+  RS_BADPOINT = 1,
+  RS_WALK_SUBFACE = 2,
+  RS_WALK_SUBSEG = 3,
+  RS_WALK_LIMIT = 4,
+  RS_WALK_HULL = 5,
+  RS_CLOSURE = 6,
+  RS_OVERFLOW = 7,
+  RS_GUARD = 8,
+  RS_ENCROACH = 9,
+  RS_STRUCT = 10,
+  RS_ENCROACH_UNSPL = 11,
+  RS_STARDEL = 12,
+};
+
+struct __align__(32) TetRec {
+  int4 v;
+  int4 n;
+};
+
+struct DevMesh {
+  V4* V;
+  TetRec* T;
+  int4* TS;
+  uint8_t* Tflag;
+  unsigned long long* Tmark;
+  int* Tfwd;
+  int4* SV;
+  int4* SN;
+  uint8_t* Sflag;
+  uint8_t* Smust;
+  unsigned long long* Smark;
+  int4* GV;
+  uint8_t* Gflag;
+  uint8_t* Gmust;
+  V4* FQ;
+  unsigned long long* HK;
+  int* HV;
+  int hmask;
+  int nV, nT, nS, nG, nF;
+  double guard2;
+  int walk_limit;
+};
+
+// Tier capacities of the region-growth workspace. Tier 1 lives in shared
+// memory (one workspace per warp); candidates whose region does not fit are
+// re-run in tier 2, whose workspace lives in global memory. Tier 2's cavity cap
+// is the method's limit: a larger cavity makes the element unsplittable.
+template <int CAPC_, int CAPB_, int CAPF_, int CAPFB_, int HCAP_>
+struct Caps {
+  static constexpr int CAPC = CAPC_, CAPB = CAPB_, CAPF = CAPF_, CAPFB = CAPFB_, HCAP = HCAP_;
+};
+using Tier1 = Caps<64, 160, 32, 48, 256>;
+using Tier2 = Caps<4096, 16384, 8192, 24576, 32768>;
+constexpr int kCavLimit = 4096;
+
+// Per-candidate slab in global memory (written by growth, read by selection
+// and insertion): counts then lists.
+template <class C>
+struct SlabLayout {
+  static constexpr int OFF_CAV = 4;
+  static constexpr int OFF_BIN = OFF_CAV + C::CAPC;
+  static constexpr int OFF_BOUT = OFF_BIN + C::CAPB;
+  static constexpr int OFF_FCAV = OFF_BOUT + C::CAPB;
+  static constexpr int OFF_FBND = OFF_FCAV + C::CAPF;
+  static constexpr int OFF_BV = OFF_FBND + C::CAPFB;   // 3 vertex ids per boundary face
+  static constexpr int OFF_FBV = OFF_BV + 3 * C::CAPB;  // (u, x, facet) per facet edge
+  static constexpr int STRIDE = OFF_FBV + 3 * C::CAPFB;
+};
+
+struct DevRound {
+  int cls;
+  int n;                       // candidates
+  const int* cand;             // element ids in priority order
+  const double* given;         // CLS_POINT: point coordinates (xyz), by element id
+  int* loc;                    // located tet / subface (or start hint for points)
+  V4* sp;                 // splitting points
+  int* status;                 // outcome | reason << 8
+  unsigned long long epoch;    // mark = epoch << 32 | rank
+  int* slab1;                  // tier-1 slabs (n * STRIDE1)
+  int* slab2;                  // tier-2 slabs (n2 * STRIDE2)
+  int* slab2_of;               // candidate -> tier-2 slab index (-1)
+  int* ws2;                    // tier-2 workspaces (per warp)
+  int n2;                      // tier-2 candidates
+  const int* list2;            // tier-2 candidate indices
+  int* survived;
+  int4* counts;                // new (verts, tets, subfaces, subsegs) per candidate
+  const int4* offs;            // exclusive scan of counts
+  int* point_state;            // CLS_POINT: 0 pending, 1 inserted, 2 skipped
+  unsigned long long* stats;   // device counters
+  double B;
+};
+
+// device counters
+enum { ST_REJECT = 0, ST_UNSPL, ST_OK, ST_SURV, ST_RETRY, ST_ITER, ST_COUNT };
+
+}  // namespace cdr
