@@ -1,0 +1,396 @@
+"""Benchmark: Steiner points inserted per second by the refinement rounds on GB300.
+
+One step = the whole refinement (every round, every kernel of the hot path) of
+one instance of the workload, from its initial constrained Delaunay mesh (kept
+on the device and restored at the start of the step) to the end.
+
+Workload (default): 100,000 points uniform in [0,1000]^3 plus the 8 box corners,
+1,000 segments and 1,000 triangles inside the box (constraints chosen among the
+Delaunay edges and faces; seed 1), B = 1.4. The initial Delaunay mesh is built
+on the GPU by the library's point-insertion rounds (untimed set-up).
+
+--impl reference times the CPU oracle (sequential refinement) on the same
+workload, a bounded number of insertions per step, on the host cores.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "uniform100k": dict(kind="uniform", n=100_000, seed=1, B=1.4, n_seg=1000, n_tri=1000),
+    "cube2k": dict(kind="cube", n=2000, seed=0, B=2.0, n_seg=0, n_tri=0),
+    "clustered500k": dict(kind="clustered", n=500_000, seed=2, B=1.4, n_seg=5000, n_tri=5000),
+}
+METRIC = "Steiner pts inserted/s on 1 GB300"
+UNIT = "Steiner points/s"
+
+
+def log(*a):
+    print("[bench %.1fs]" % (time.perf_counter() - T0), *a, file=sys.stderr, flush=True)
+
+
+T0 = time.perf_counter()
+MAX_ROUNDS = 200000
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- workload
+def make_workload(name, rank, cdr, stream):
+    """Points, the GPU-built initial Delaunay mesh and constraint labels."""
+    from paper_1903_03406_gb300 import inputs
+    w = WORKLOADS[name]
+    pts, _, _ = inputs.box_points(w["kind"], w["n"], w["seed"] + 1000 * rank)
+    log("building the initial Delaunay mesh on the GPU (%d points)" % len(pts))
+    dt = cdr.Handle.delaunay_box(pts, stream=stream)
+    log("delaunay: %d rounds, %d skipped" % (dt.dt_rounds, dt.skipped))
+    ex = dt.export()
+    dt.close()
+    plc = inputs.plc_from_delaunay(pts, ex["tets"], w["n_seg"], w["n_tri"], w["seed"] + 1000 * rank)
+    return pts, ex, plc
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "predicates.cuh", "mesh.cuh"):
+        with open(os.path.join(ROOT, "paper_1903_03406_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernels (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("kernels_sha") == kernel_hash():
+            return float(e["dram_bytes_per_launch_full"])
+    except Exception:
+        pass
+    return None
+
+
+# Algorithmic bytes of the region-growth kernel, from its device counters:
+#  * each neighbour tetrahedron tested: its 32 B record and the one vertex
+#    across the shared face (24 B of coordinates);
+#  * each cavity tetrahedron: its 32 B record, an 8 B priority mark read and
+#    written (atomicMin), a 4 B id written to the slab;
+#  * each boundary face: the shell tetrahedron's 8 B mark read and written and
+#    12 B of face vertex ids plus 8 B of face links written to the slab.
+def grow_bytes(ctr):
+    return ctr["tested"] * (32 + 24) + ctr["cavity"] * (32 + 16 + 4) + ctr["boundary"] * (16 + 20)
+
+
+# -------------------------------------------------------------------- GPU arm
+def gpu_arm(args, rank, world):
+    import torch
+    from paper_1903_03406_gb300 import cdr
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    cdr.lib()
+    stream = torch.cuda.current_stream()
+    w = WORKLOADS[args.workload]
+    B = w["B"]
+    pts, ex, plc = make_workload(args.workload, rank, cdr, stream)
+    log("workload ready: %d points, %d tets, %d subfaces, %d subsegments" %
+        (len(ex["xyz"]), len(ex["tets"]), len(plc["tris"]), len(plc["segs"])))
+    al = cdr.TorchAllocator()
+    h = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
+                          plc["facet_id"], plc["nfacets"], allocator=al, stream=stream)
+    h.checkpoint()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for k in range(args.warmup):
+        h.restore()
+        t0 = time.perf_counter()
+        st = h.refine(B, MAX_ROUNDS)
+        log("warmup %d: %.3fs rounds %d inserted %d status %d" %
+            (k, time.perf_counter() - t0, st["rounds"], st["steiner_inserted"], st["status"]))
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    h.profile(enable=1, reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    total_ms = 0.0
+    inserted = 0
+    last = None
+    for k in range(args.steps):
+        flush.fill_(float(k))  # L2 flush between timed steps, outside the events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.restore()
+        last = h.refine(B, MAX_ROUNDS)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        inserted += last["steiner_inserted"]
+        log("step %d: %.3f ms, %d inserted" % (k, e0.elapsed_time(e1), last["steiner_inserted"]))
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    prof = h.profile(enable=0)
+    clk = clocks.stop()
+
+    # end to end through the C-ABI with host buffers: create (host -> device),
+    # refine, export (device -> host), every step
+    n_e2e = max(1, min(args.steps, 3))
+    h2d = sum(a.nbytes for a in (ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
+                                 plc["facet_id"]))
+    d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ins_e2e = 0
+    for _ in range(n_e2e):
+        he = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
+                               plc["facet_id"], plc["nfacets"], allocator=al, stream=stream)
+        st = he.refine(B, MAX_ROUNDS)
+        out = he.export()
+        torch.cuda.synchronize()
+        ins_e2e += st["steiner_inserted"]
+        d2h = sum(v.nbytes for v in out.values())
+        he.close()
+    t_e2e = time.perf_counter() - t0
+
+    # max over ranks of the time, sum of the work
+    tot = torch.tensor([total_ms, float(inserted), t_e2e, float(ins_e2e)], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        mx = tot.clone().cuda()
+        sm = tot.clone().cuda()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms_max, ins_sum = float(mx[0]), float(sm[1])
+        e2e_max, e2e_ins = float(mx[2]), float(sm[3])
+    else:
+        total_ms_max, ins_sum, e2e_max, e2e_ins = total_ms, float(inserted), t_e2e, float(ins_e2e)
+    if rank != 0:
+        return None
+
+    peak, peak_kind = load_peaks()
+    ms = prof["ms"]
+    dom = max(ms, key=lambda g: ms[g])
+    calls = prof["calls"]
+    gb = grow_bytes(prof["counters"]) / 1e9
+    grow_ms = ms["grow1"]
+    achieved = gb / (grow_ms / 1e3) if grow_ms > 0 else 0.0
+    traffic = ncu_traffic("k_grow1")
+    per_launch_traffic = traffic if traffic is not None else None
+    launches = prof["counters"].get("launches", None)
+    value = ins_sum / (total_ms_max / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "points": w["n"] + 8, "segments": w["n_seg"],
+                   "triangles": w["n_tri"], "B": B, "parallelism": "instance-sharded x%d" % world,
+                   "l2": "flushed between steps (256 MB write)",
+                   "steiner_per_step": last["steiner_inserted"], "rounds_per_step": last["rounds"],
+                   "final_tets": last["n_tets"], "bad_left": last["n_bad_left"],
+                   "wall_s": t_wall},
+        "e2e": {"value": e2e_ins / e2e_max, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"kernel": "k_grow1 (region growth, tier 1)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None,
+                     "peak_source": peak_kind,
+                     "traffic": per_launch_traffic,
+                     "algorithmic_bytes_per_launch": gb * 1e9 / max(calls["grow1"], 1),
+                     "avg_launch_ms": grow_ms / max(calls["grow1"], 1),
+                     "dominant_group": dom,
+                     "group_ms_per_step": {g: v / args.steps for g, v in ms.items() if v > 0}},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    return line
+
+
+# ---------------------------------------------------------- CPU (oracle) arm
+def oracle_workload(name):
+    import oracle
+    from paper_1903_03406_gb300 import inputs
+    w = WORKLOADS[name]
+    pts, _, _ = inputs.box_points(w["kind"], w["n"], w["seed"])
+    om = oracle.Mesh.box_delaunay(pts)
+    e = om.export()
+    plc = inputs.plc_from_delaunay(pts, e["tets"], w["n_seg"], w["n_tri"], w["seed"])
+    om.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"], plc["nfacets"])
+    return om, e, plc
+
+
+def cpu_sample(om, B, seconds):
+    """Sequential refinement for about `seconds` of CPU time, in chunks."""
+    ins, t = 0, 0.0
+    chunk = 2000
+    while t < seconds:
+        t0 = time.perf_counter()
+        st = om.refine_S(B, chunk)
+        t += time.perf_counter() - t0
+        ins += st["inserted"]
+        if st["steps"] < chunk:
+            break
+    return ins, t
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return None
+    w = WORKLOADS[args.workload]
+    om, e, plc = oracle_workload(args.workload)
+    import oracle
+    ins, t = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        i, dt = cpu_sample(om, w["B"], args.ref_seconds)
+        if i == 0:  # refinement finished: start a fresh instance
+            om = oracle.Mesh.create(e["xyz"], e["tets"])
+            om.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"],
+                               plc["nfacets"])
+            i, dt = cpu_sample(om, w["B"], args.ref_seconds)
+        if k >= args.warmup:
+            ins += i
+            t += dt
+    v = ins / t
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "points": w["n"] + 8, "segments": w["n_seg"],
+                   "triangles": w["n_tri"], "B": w["B"]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "sequential refinement, %.0f s of insertions per step" %
+                                   args.ref_seconds},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uniform100k", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=5.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        line = reference_arm(args, rank, world)
+    else:
+        line = gpu_arm(args, rank, world)
+        if line is not None and world == 1 and not args.no_cpu_baseline:
+            log("cpu baseline: building the oracle's Delaunay mesh")
+            om, _, _ = oracle_workload(args.workload)
+            ins, t = cpu_sample(om, WORKLOADS[args.workload]["B"], args.cpu_seconds)
+            line["cpu_baseline"] = {
+                "value": ins / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "sequential refinement of the same workload for %.1f s "
+                          "(%d insertions, initial Delaunay excluded)" % (t, ins)}
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

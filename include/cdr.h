@@ -195,6 +195,22 @@ int cdr_delaunay_box(const double* xyz, int32_t n, const cdr_options* opt,
 /* Text for a status code. */
 const char* cdr_status_string(int status);
 
+/* Timing of the kernel groups of each round with CUDA events recorded on the
+ * handle's stream, and device work counters (always accumulated).
+ *   enable   1 on, 0 off, -1 unchanged;  reset  nonzero clears the totals first
+ *   ms[16]   accumulated milliseconds per group: 0 classify, 1 order, 2 split,
+ *            3 locate, 4 grow (tier 1), 5 grow (tier 2), 6 select, 7 scan,
+ *            8 insert, 9 compact
+ *   calls[16] launches timed per group
+ *   counters[16] 0 refused, 1 unsplittable, 2 eligible-but-blasted, 3 inserted,
+ *            4 retried in tier 2, 5 invariant failures, 6 neighbour tetrahedra
+ *            tested by growth, 7 cavity tetrahedra, 8 boundary faces, 9 new
+ *            tetrahedra written, 15 kernels of this library launched (library
+ *            primitives such as sorts and scans excluded)
+ * Any output pointer may be NULL. */
+int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_t* calls,
+                int64_t* counters);
+
 /* Library self-description: sm architecture compiled for, e.g. 103. */
 int cdr_device_arch(void);
 

@@ -703,6 +703,26 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
     for (int s : dec[i].shellS) ok = ok && sm[s] == i;
     surv[i] = ok;
   }
+  // A subsegment round can stall: every candidate refused only because its
+  // insertion would delete another subsegment that is itself a candidate (two
+  // nearby segments whose midpoints encroach one another). Then nothing changes
+  // and the next round would be the same; the refused candidates become
+  // unsplittable instead.
+  if (cls == CLS_SUBSEG) {
+    bool progress = false;
+    std::unordered_set<int> isCand(q[0].begin(), q[0].end());
+    for (int i = 0; i < n && !progress; ++i) {
+      if (surv[i] || dec[i].outcome == OUT_UNSPL) progress = true;
+      for (int g : dec[i].flagG)
+        if (!isCand.count(g)) progress = true;
+    }
+    if (!progress)
+      for (int i = 0; i < n; ++i)
+        if (dec[i].outcome == OUT_REJECT) {
+          dec[i].outcome = OUT_UNSPL;
+          dec[i].reason = RS_STRUCT;
+        }
+  }
   if (rep) rep->record(M, cls, cands, dec, surv);
   for (int i = 0; i < n; ++i) apply_flags(M, dec[i]);
   int inserted = 0;
@@ -767,6 +787,7 @@ long refine_S(Mesh& M, double B, long max_steps, SeqStats* st) {
   for (int t = 0; t < (int)M.T.size(); ++t) refresh(CLS_TET, t);
 
   std::vector<std::pair<int, int>> forced;
+  std::unordered_set<int> refusedSeg;  // subsegments refused since the last insertion
   long steps = 0;
   while (steps < max_steps) {
     int cls = -1, e = -1;
@@ -791,6 +812,17 @@ long refine_S(Mesh& M, double B, long max_steps, SeqStats* st) {
     ++steps;
     Decision d = evaluate(M, cls, e, nullptr, -1);
     if (st) st->evaluated++;
+    if (cls == CLS_SUBSEG && d.outcome == OUT_REJECT) {
+      // refused only in favour of subsegments that were refused themselves
+      // since the last insertion: a cycle, so give this one up
+      bool circular = !d.flagG.empty();
+      for (int g : d.flagG) circular = circular && refusedSeg.count(g);
+      refusedSeg.insert(e);
+      if (circular) {
+        d.outcome = OUT_UNSPL;
+        d.reason = RS_STRUCT;
+      }
+    }
     if (d.outcome != OUT_OK) {
       apply_flags(M, d);
       if (d.outcome == OUT_UNSPL) {
@@ -815,6 +847,7 @@ long refine_S(Mesh& M, double B, long max_steps, SeqStats* st) {
     if (cls == CLS_SUBSEG) drop(CLS_SUBSEG, e);
     std::vector<int> nT, nS, nG;
     apply(M, d, (int)M.P.size(), &nT, &nS, &nG);
+    refusedSeg.clear();
     if (st) st->inserted++;
     ensure();
     std::set<int> sfs, sgs;

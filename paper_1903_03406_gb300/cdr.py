@@ -113,6 +113,10 @@ def lib():
             L.cdr_status_string.argtypes = [ctypes.c_int]
             L.cdr_status_string.restype = ctypes.c_char_p
             L.cdr_device_arch.restype = ctypes.c_int
+            L.cdr_profile.argtypes = [P, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64)]
             L.cdr_eval_predicates.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                               ctypes.c_int32, i32p,
                                               ctypes.POINTER(ctypes.c_double), P]
@@ -243,6 +247,23 @@ class Handle:
         d = s.as_dict()
         d["cls"] = cls_.value
         return d
+
+    GROUPS = ["classify", "order", "split", "locate", "grow1", "grow2", "select", "scan",
+              "insert", "compact"]
+    COUNTERS = ["refused", "unsplittable", "blasted", "inserted", "retried", "invariant",
+                "tested", "cavity", "boundary", "new_tets", "c10", "c11", "c12", "c13", "c14",
+                "launches"]
+
+    def profile(self, enable=-1, reset=False):
+        ms = np.zeros(16)
+        calls = np.zeros(16, dtype=np.int64)
+        ctr = np.zeros(16, dtype=np.int64)
+        _check(lib().cdr_profile(self.ptr, int(enable), int(bool(reset)), _p(ms, ctypes.c_double),
+                                 _p(calls, ctypes.c_int64), _p(ctr, ctypes.c_int64)),
+               "cdr_profile")
+        return dict(ms={g: float(ms[i]) for i, g in enumerate(self.GROUPS)},
+                    calls={g: int(calls[i]) for i, g in enumerate(self.GROUPS)},
+                    counters={c: int(ctr[i]) for i, c in enumerate(self.COUNTERS)})
 
     def checkpoint(self):
         _check(lib().cdr_checkpoint(self.ptr), "cdr_checkpoint")

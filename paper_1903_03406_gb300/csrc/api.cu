@@ -59,6 +59,12 @@ struct cdr_handle {
   int npts = 0;
   // last round, for the report
   int lastN = 0, lastCls = -1, lastN2 = 0;
+  // profiling: events around each kernel group, accumulated per round
+  bool prof = false;
+  cudaEvent_t ev[2 * 16] = {};
+  double prof_ms[16] = {};
+  long long prof_calls[16] = {};
+  long long prof_ctr[16] = {};
   // checkpoint
   std::vector<Buf> ck;
   DevMesh ckm{};
@@ -367,6 +373,27 @@ __global__ void k_report_sizes(DevRound r, int* ncav, int* nbnd, int* nfcav) {
 
 unsigned next_epoch(cdr_handle* h) { return 0xFFFFFFFFu - (++h->epoch); }
 
+// kernel groups timed when profiling is on
+enum { PG_CLASSIFY = 0, PG_ORDER, PG_SPLIT, PG_LOCATE, PG_GROW1, PG_GROW2, PG_SELECT, PG_SCAN,
+       PG_INSERT, PG_COMPACT, PG_N };
+inline void pmark(cdr_handle* h, int g, int which) {
+  if (!h->prof) return;
+  if (!h->ev[2 * g + which]) cudaEventCreate(&h->ev[2 * g + which]);
+  cudaEventRecord(h->ev[2 * g + which], h->stream);
+}
+// after the round's final synchronisation
+inline void pcollect(cdr_handle* h, const bool* used) {
+  if (!h->prof) return;
+  for (int g = 0; g < PG_N; ++g) {
+    if (!used[g]) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[2 * g], h->ev[2 * g + 1]) == cudaSuccess) {
+      h->prof_ms[g] += ms;
+      h->prof_calls[g] += 1;
+    }
+  }
+}
+
 bool ensure_round(cdr_handle* h, int n) {
   if (n <= h->capR && h->bCand.p) return true;
   int c = std::max(n, 1024);
@@ -377,7 +404,7 @@ bool ensure_round(cdr_handle* h, int n) {
             ensure(h, h->bCounts, (size_t)c * 16) && ensure(h, h->bOffs, (size_t)(c + 1) * 16) &&
             ensure(h, h->bSlab1, (size_t)c * SlabLayout<Tier1>::STRIDE * 4) &&
             ensure(h, h->bSlab2of, (size_t)c * 4) && ensure(h, h->bList2, (size_t)c * 4) &&
-            ensure(h, h->bCkey, (size_t)c * 16) && ensure(h, h->bStats, 8 * 16) &&
+            ensure(h, h->bCkey, (size_t)c * 16) && ensure(h, h->bStats, 32 * 8) &&
             ensure(h, h->bErr, 64) && ensure(h, h->bI32, (size_t)(c + 1) * 4);
   if (ok) h->capR = c;
   return ok;
@@ -403,6 +430,7 @@ DevRound make_round(cdr_handle* h, int cls, int n, double B) {
   r.offs = ptr<int4>(h->bOffs);
   r.point_state = ptr<int>(h->bPstate);
   r.stats = ptr<unsigned long long>(h->bStats);
+  r.candG = (cls == CLS_SUBSEG) ? ptr<uint8_t>(h->bCandG) : nullptr;
   r.B = B;
   return r;
 }
@@ -464,20 +492,34 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   DevMesh& m = h->m;
   cudaStream_t s = h->stream;
   DevRound r = make_round(h, cls, n, B);
-  cudaMemsetAsync(h->bStats.p, 0, 8 * 16, s);
+  cudaMemsetAsync(h->bStats.p, 0, ST_COUNT * 8, s);
   k_fill_int<<<gridn(n), 256, 0, s>>>(ptr<int>(h->bSlab2of), n, -1);
   k_cand_keys<<<gridn(n), 256, 0, s>>>(m, cls, r.cand, n, ptr<int4>(h->bCkey));
+  h->prof_ctr[15] += 2;
+  bool used[PG_N] = {};
+  pmark(h, PG_SPLIT, 0);
   launch_split(m, r, s);
+  pmark(h, PG_SPLIT, 1);
+  h->prof_ctr[15] += 1;
+  used[PG_SPLIT] = true;
   if (cls == CLS_POINT)
     launch_follow_fwd(m, ptr<int>(h->bHint), ptr<int>(h->bPstate), h->npts, s);
+  pmark(h, PG_LOCATE, 0);
   launch_locate(m, r, ptr<int>(h->bHint), s);
+  pmark(h, PG_LOCATE, 1);
+  h->prof_ctr[15] += cls == CLS_POINT ? 4 : 1;
+  used[PG_LOCATE] = true;
   if (cls == CLS_POINT) {
     unsigned long long e0 = next_epoch(h);
     k_point_prefilter<<<gridn(n), 256, 0, s>>>(m, r.status, r.loc, n, e0, 0);
     k_point_prefilter<<<gridn(n), 256, 0, s>>>(m, r.status, r.loc, n, e0, 1);
   }
   r.epoch = next_epoch(h);
+  pmark(h, PG_GROW1, 0);
   launch_grow1(m, r, s);
+  pmark(h, PG_GROW1, 1);
+  h->prof_ctr[15] += 2;  // growth + retry flags
+  used[PG_GROW1] = true;
   // tier 2 for regions that did not fit
   {
     int* flag = ptr<int>(h->bSurv);  // scratch before selection
@@ -503,12 +545,20 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
       r.ws2 = ptr<int>(h->bWs2);
       r.n2 = n2;
       k_scatter_slab2<<<gridn(n2), 256, 0, s>>>(r.list2, n2, r.slab2_of);
+      pmark(h, PG_GROW2, 0);
       launch_grow2(m, r, warps, s);
+      pmark(h, PG_GROW2, 1);
+      h->prof_ctr[15] += 2;
+      used[PG_GROW2] = true;
     }
     h->lastN2 = n2;
   }
   if (cls == CLS_POINT) k_undefer<<<gridn(n), 256, 0, s>>>(r.status, n);
+  pmark(h, PG_SELECT, 0);
   launch_select(m, r, s);
+  pmark(h, PG_SELECT, 1);
+  h->prof_ctr[15] += cls == CLS_POINT ? 2 : 1;
+  used[PG_SELECT] = true;
   // allocation: exclusive scan of (verts, tets, subfaces, subsegs)
   {
     size_t tb = 0;
@@ -528,6 +578,12 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   if (cuda_status(h)) return h->err;
   int4 tot = make_int4(lastOff.x + lastCnt.x, lastOff.y + lastCnt.y, lastOff.z + lastCnt.z,
                        lastOff.w + lastCnt.w);
+  if (cls == CLS_SUBSEG && st[ST_SURV] == 0 && st[ST_UNSPL] == 0 && st[ST_NEWCAND] == 0) {
+    launch_stall(m, r, s);
+    h->prof_ctr[15] += 1;
+    st[ST_UNSPL] += st[ST_REJECT];
+    st[ST_REJECT] = 0;
+  }
   if (!grow_verts(h, m.nV + tot.x) || !grow_tets(h, m.nT + tot.y) ||
       !grow_subfaces(h, m.nS + tot.z) || !grow_subsegs(h, m.nG + tot.w))
     return h->err ? h->err : CDR_ERR_OOM;
@@ -537,7 +593,11 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   r = make_round(h, cls, n, B);  // rebind after any reallocation
   r.epoch = 0;
   r.n2 = h->lastN2;
+  pmark(h, PG_INSERT, 0);
   launch_insert(m, r, ptr<int>(h->bHint), s);
+  pmark(h, PG_INSERT, 1);
+  h->prof_ctr[15] += 1;
+  used[PG_INSERT] = true;
   m.nV += cls == CLS_POINT ? 0 : tot.x;
   m.nT += tot.y;
   m.nS += tot.z;
@@ -555,10 +615,12 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   }
   if (exact_overflow_flag(s, true)) return set_err(h, CDR_ERR_INTERNAL);
   {
-    unsigned long long it = 0;
-    cudaMemcpyAsync(&it, ptr<unsigned long long>(h->bStats) + ST_ITER, 8, cudaMemcpyDeviceToHost, s);
+    unsigned long long ctr[ST_COUNT];
+    cudaMemcpyAsync(ctr, h->bStats.p, sizeof(ctr), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    if (it) return set_err(h, CDR_ERR_INTERNAL);  // an invariant check failed on the device
+    if (ctr[ST_ITER]) return set_err(h, CDR_ERR_INTERNAL);  // a device invariant check failed
+    pcollect(h, used);
+    for (int k = 0; k < ST_COUNT && k < 15; ++k) h->prof_ctr[k] += (long long)ctr[k];
   }
   return cuda_status(h);
 }
@@ -577,6 +639,7 @@ int order_candidates(cdr_handle* h, int cls, int n) {
                                   ptr<unsigned long long>(h->bKeys2), ptr<int>(h->bCand),
                                   ptr<int>(h->bCand2), n, 0, 64, s);
   launch_tiefix(h->m, cls, ptr<unsigned long long>(h->bKeys2), ptr<int>(h->bCand2), n, s);
+  h->prof_ctr[15] += 2;  // priorities + tie fix
   return cuda_status(h);
 }
 
@@ -585,14 +648,18 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
   cudaStream_t s = h->stream;
   if (B != h->lastB) {
     launch_recompute_bad(m, B, s);
+    h->prof_ctr[15] += 1;
     h->lastB = B;
   }
   int st = maybe_compact(h, false);
   if (st) return st;
   if (!ensure_round(h, 1024)) return CDR_ERR_OOM;
   cudaMemsetAsync(h->bErr.p, 0, 64, s);
+  pmark(h, PG_CLASSIFY, 0);
   launch_classify(m, ptr<uint8_t>(h->bCandS), ptr<uint8_t>(h->bCandG), ptr<uint8_t>(h->bCandT),
                   ptr<int>(h->bErr), s);
+  pmark(h, PG_CLASSIFY, 1);
+  h->prof_ctr[15] += 2;  // classification + counts
   unsigned long long* cnt = ptr<unsigned long long>(h->bStats);
   cudaMemsetAsync(cnt, 0, 24, s);
   k_count3<<<gridn((long)m.nG + m.nS + m.nT), 256, 0, s>>>(
@@ -605,6 +672,11 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
   cudaStreamSynchronize(s);
   if (cuda_status(h)) return h->err;
   if (cerr) return set_err(h, CDR_ERR_INTERNAL);
+  {
+    bool used[PG_N] = {};
+    used[PG_CLASSIFY] = true;
+    pcollect(h, used);
+  }
   int cls = -1;
   for (int c = 0; c < 3; ++c)
     if (c3[c] > 0) {
@@ -632,8 +704,8 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
 }
 
 int count_bad(cdr_handle* h, long long* out) {
-  if (!ensure(h, h->bStats, 8 * 16)) return CDR_ERR_OOM;
-  unsigned long long* c = ptr<unsigned long long>(h->bStats) + 8;
+  if (!ensure(h, h->bStats, 32 * 8)) return CDR_ERR_OOM;
+  unsigned long long* c = ptr<unsigned long long>(h->bStats) + 24;
   cudaMemsetAsync(c, 0, 8, h->stream);
   k_count_bad<<<gridn(h->m.nT), 256, 0, h->stream>>>(h->m, c);
   unsigned long long v = 0;
@@ -706,6 +778,8 @@ void cdr_destroy(cdr_handle* h) {
                 &h->bTmp, &h->bStats, &h->bErr, &h->bI32, &h->bPts, &h->bHint, &h->bPstate};
   for (Buf* b : all) dfree(h, *b);
   for (Buf& b : h->ck) dfree(h, b);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
   cudaStreamSynchronize(h->stream);
   delete h;
 }
@@ -1399,6 +1473,26 @@ int cdr_eval_predicates(int32_t kind, const double* in, int32_t n, int32_t* sign
   cudaFree(dout);
   if (cudaGetLastError() != cudaSuccess) return CDR_ERR_CUDA;
   return ov ? CDR_ERR_INTERNAL : CDR_OK;
+}
+
+int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_t* calls,
+                int64_t* counters) {
+  if (!h) return CDR_ERR_INVALID_INPUT;
+  if (reset) {
+    for (int g = 0; g < 16; ++g) {
+      h->prof_ms[g] = 0;
+      h->prof_calls[g] = 0;
+      h->prof_ctr[g] = 0;
+    }
+  }
+  if (ms)
+    for (int g = 0; g < 16; ++g) ms[g] = h->prof_ms[g];
+  if (calls)
+    for (int g = 0; g < 16; ++g) calls[g] = h->prof_calls[g];
+  if (counters)
+    for (int g = 0; g < 16; ++g) counters[g] = h->prof_ctr[g];
+  if (enable >= 0) h->prof = enable != 0;
+  return CDR_OK;
 }
 
 }  // extern "C"

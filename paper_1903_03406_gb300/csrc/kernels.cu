@@ -686,6 +686,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
     sb = G.y;
   }
   int ncav = 0, nf = 0, nbnd = 0, nfb = 0;
+  int ntested = 0;  // per lane
   int outcome = OUT_OK, reason = RS_NONE;
   bool retry = false;  // tier-1 capacity exceeded
 
@@ -913,6 +914,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           bool add = false;
           if (leader) {
             bool in = tet_in_sphere(m, ld_tet(m, cand), p);
+            ++ntested;
             int res = hs_put(w.hset, C::HCAP, cand, in ? 1 : 2, false);
             if (res < 0) retry = true;
             add = in && res == 1;
@@ -1201,6 +1203,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
                 flag = true;
                 un = (m.Gflag[g] & F_UNSPL) != 0;
                 m.Gmust[g] = 1;
+                if (r.candG && !r.candG[g]) atomicAdd(&r.stats[ST_NEWCAND], 1ULL);
               }
             }
           }
@@ -1231,6 +1234,14 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
 
 done:
   __syncwarp();
+  for (int o = 16; o > 0; o >>= 1) ntested += __shfl_xor_sync(FULLMASK, ntested, o);
+  if (lane == 0) {
+    atomicAdd(&r.stats[ST_TESTED], (unsigned long long)ntested);
+    if (!retry) {
+      atomicAdd(&r.stats[ST_CAV], (unsigned long long)ncav);
+      atomicAdd(&r.stats[ST_BND], (unsigned long long)nbnd);
+    }
+  }
   if (retry) {
     if (lane == 0) {
       set_status(r, i, OUT_RETRY, RS_NONE);
@@ -1403,6 +1414,7 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       sb = G.y;
     }
     if (lane == 0 && r.cls != CLS_POINT) m.V[vp] = r.sp[i];
+    if (lane == 0) atomicAdd(&r.stats[ST_NEWT], (unsigned long long)nbnd);
     // step 1: new tetrahedra (p replaces the vertex opposite each boundary face)
     for (int j = lane; j < nbnd; j += 32) {
       int t = bin[j] >> 2, f = bin[j] & 3;
@@ -1839,6 +1851,20 @@ __global__ void k_eval_pred(int kind, const double* in, int n, int* sign, double
 }
 void launch_eval_pred(int kind, const double* in, int n, int* sign, double* outp, cudaStream_t s) {
   if (n > 0) k_eval_pred<<<grid_for(n, 128), 128, 0, s>>>(kind, in, n, sign, outp);
+}
+
+
+// A subsegment round that inserted nothing, gave up nothing and flagged no new
+// candidate would repeat itself: its refused candidates become unsplittable.
+__global__ void k_stall(DevMesh m, DevRound r) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
+    if ((r.status[i] & 0xff) != OUT_REJECT) continue;
+    r.status[i] = OUT_UNSPL | (RS_STRUCT << 8);
+    m.Gflag[r.cand[i]] |= F_UNSPL;
+  }
+}
+void launch_stall(const DevMesh& m, const DevRound& r, cudaStream_t s) {
+  if (r.n > 0) k_stall<<<grid_for(r.n, 256), 256, 0, s>>>(m, r);
 }
 
 int exact_overflow_flag(cudaStream_t s, bool reset) {

@@ -41,6 +41,7 @@ void launch_grow1(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s);
 void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_insert(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s);
+void launch_stall(const DevMesh& m, const DevRound& r, cudaStream_t s);
 
 // maintenance
 void launch_compact_flags(const DevMesh& m, int* alive, cudaStream_t s);

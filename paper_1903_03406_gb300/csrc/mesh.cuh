@@ -138,10 +138,24 @@ struct DevRound {
   const int4* offs;            // exclusive scan of counts
   int* point_state;            // CLS_POINT: 0 pending, 1 inserted, 2 skipped
   unsigned long long* stats;   // device counters
+  const uint8_t* candG;        // this round's subsegment candidates (classification)
   double B;
 };
 
 // device counters
-enum { ST_REJECT = 0, ST_UNSPL, ST_OK, ST_SURV, ST_RETRY, ST_ITER, ST_COUNT };
+enum {
+  ST_REJECT = 0,
+  ST_UNSPL,
+  ST_OK,
+  ST_SURV,
+  ST_RETRY,
+  ST_ITER,
+  ST_TESTED,  // neighbour tetrahedra tested (insphere) by region growth
+  ST_CAV,     // cavity tetrahedra of evaluated regions
+  ST_BND,     // boundary faces of evaluated regions
+  ST_NEWT,    // tetrahedra written by insertion
+  ST_NEWCAND,  // refusals that flagged a subsegment not yet a candidate
+  ST_COUNT
+};
 
 }  // namespace cdr
