@@ -198,6 +198,7 @@ def gpu_arm(args, rank, world):
     barrier()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
     total_ms = 0.0
     inserted = 0
     last = None
@@ -214,6 +215,7 @@ def gpu_arm(args, rank, world):
         inserted += last["steiner_inserted"]
         log("step %d: %.3f ms, %d inserted" % (k, e0.elapsed_time(e1), last["steiner_inserted"]))
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier()
     t_wall = time.perf_counter() - t_wall0
     prof = h.profile(enable=0)
