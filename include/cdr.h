@@ -165,7 +165,8 @@ int cdr_export(cdr_handle* h, const cdr_mesh_out* out);
  * buffers:
  *   keys[n_cand*4]      the element's sorted vertex ids (-1 padded)
  *   pts[n_cand*3]       splitting point
- *   outcome[n_cand]     0 eligible, 1 refused (encroachment), 2 unsplittable
+ *   outcome[n_cand]     0 eligible, 1 refused (encroachment), 2 unsplittable,
+ *                       4 stopped on a higher-priority start tetrahedron
  *   reason[n_cand]      detail code (see DESIGN notes in the repository)
  *   survived[n_cand]    1 if inserted
  *   n_cav[n_cand], n_bnd[n_cand], n_fcav[n_cand]  region sizes
@@ -205,7 +206,8 @@ const char* cdr_status_string(int status);
  *   counters[16] 0 refused, 1 unsplittable, 2 eligible-but-blasted, 3 inserted,
  *            4 retried in tier 2, 5 invariant failures, 6 neighbour tetrahedra
  *            tested by growth, 7 cavity tetrahedra, 8 boundary faces, 9 new
- *            tetrahedra written, 15 kernels of this library launched (library
+ *            tetrahedra written, 10 refusals flagging a new candidate, 11 regions
+ *            stopped on a higher-priority start, 15 kernels of this library launched (library
  *            primitives such as sorts and scans excluded)
  * Any output pointer may be NULL. */
 int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_t* calls,

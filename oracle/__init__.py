@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 CLS_SUBSEG, CLS_SUBFACE, CLS_TET, CLS_POINT = 0, 1, 2, 3
-OUT_OK, OUT_REJECT, OUT_UNSPL = 0, 1, 2
+OUT_OK, OUT_REJECT, OUT_UNSPL, OUT_BLASTED = 0, 1, 2, 4
 
 
 def build(force: bool = False) -> str:

@@ -193,7 +193,7 @@ struct Mesh {
 // Candidate classes, in the order the rounds serve them (Sec. 2), plus the
 // plain point-insertion class used to build the initial Delaunay mesh.
 enum { CLS_SUBSEG = 0, CLS_SUBFACE = 1, CLS_TET = 2, CLS_POINT = 3 };
-enum { OUT_OK = 0, OUT_REJECT = 1, OUT_UNSPL = 2 };
+enum { OUT_OK = 0, OUT_REJECT = 1, OUT_UNSPL = 2, OUT_BLASTED = 4 };
 
 struct Cand {
   uint64_t h;

@@ -1,6 +1,7 @@
 // Oracle internal interfaces shared by its translation units.
 // TEST INFRASTRUCTURE ONLY (see geom.hpp).
 #pragma once
+#include <unordered_map>
 #include <vector>
 
 #include "mesh.hpp"
@@ -29,7 +30,8 @@ struct RoundReport {
 
 void cand_key(const Mesh& M, int cls, int elem, Cand& c);
 bool split_point(const Mesh& M, int cls, int elem, const double* given, double* p);
-Decision evaluate(const Mesh& M, int cls, int elem, const double* given, int hint);
+Decision evaluate(const Mesh& M, int cls, int elem, const double* given, int hint,
+                  const std::unordered_map<int, int>* seeds, int rank, std::vector<int>* starts);
 void apply(Mesh& M, const Decision& d, int vp, std::vector<int>* newT, std::vector<int>* newS,
            std::vector<int>* newG);
 bool subseg_encroached(const Mesh& M, int g);

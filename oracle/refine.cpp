@@ -185,10 +185,11 @@ static bool is_split_edge(int u, int w, int sa, int sb) {
 // strictly encloses p, grown from the start subfaces across edges that are not
 // subsegments, then closed so that every boundary edge sees p strictly inside
 // (a non-visible boundary edge adds the subface beyond it; a non-visible
-// subsegment edge is a failure). The subsegment being split (sa,sb) is never a
-// boundary edge.
+// subsegment edge is a failure, recorded in *failed while the growth goes on).
+// The subsegment being split (sa,sb) is never a boundary edge.
 static bool grow_facet(const Mesh& M, const std::vector<int>& start, const double* p, int sa,
-                       int sb, std::vector<int>& fcav, std::vector<std::pair<int, int>>& fbnd) {
+                       int sb, std::vector<int>& fcav, std::vector<std::pair<int, int>>& fbnd,
+                       bool* failed) {
   std::unordered_set<int> in;
   std::unordered_map<int, int> tested;
   std::vector<int> stack;
@@ -237,7 +238,10 @@ static bool grow_facet(const Mesh& M, const std::vector<int>& start, const doubl
         int n = across(s, k);
         if (n >= 0 && in.count(n)) continue;
         if (sf_orient_replace(M, s, k, p) == sf_wind(M, s)) continue;
-        if (n < 0) return false;
+        if (n < 0) {
+          *failed = true;  // recorded; growth goes on so the region is complete
+          continue;
+        }
         in.insert(n);
         fcav.push_back(n);
         stack.push_back(n);
@@ -263,11 +267,11 @@ static bool grow_facet(const Mesh& M, const std::vector<int>& start, const doubl
 // side and that are neither subfaces (except those of the facet part, which are
 // removed) nor on the hull, then closed so that every boundary face sees p
 // strictly on its inner side (a face that does not is crossed, unless it is a
-// subface or on the hull, which is a failure).
-// 0: ok; RS_CLOSURE; RS_OVERFLOW.
+// subface or on the hull: a failure, recorded in *failed while the growth goes
+// on). Returns 0, or RS_OVERFLOW when the cavity outgrows the limit.
 static int grow_tets(const Mesh& M, const std::vector<int>& start, const double* p,
                      const std::unordered_set<int>& fset, std::vector<int>& cav,
-                     std::vector<std::pair<int, int>>& bnd) {
+                     std::vector<std::pair<int, int>>& bnd, bool* failed) {
   std::unordered_set<int> in;
   std::unordered_map<int, int> tested;
   std::vector<int> stack;
@@ -277,6 +281,7 @@ static int grow_tets(const Mesh& M, const std::vector<int>& start, const double*
       cav.push_back(t);
       stack.push_back(t);
     }
+  if ((int)cav.size() > M.cav_limit) return RS_OVERFLOW;
   // -1: face removed with the facet part; -2: not crossable; else neighbour
   auto face_kind = [&](int t, int f, int* nb) -> int {
     K3 k = Mesh::face_key(M.T[t], f);
@@ -321,7 +326,10 @@ static int grow_tets(const Mesh& M, const std::vector<int>& start, const double*
         if (kind == -1) continue;
         if (kind == 0 && in.count(n)) continue;
         if (orient_replace(M, M.T[t], f, p) > 0) continue;
-        if (kind == -2) return RS_CLOSURE;
+        if (kind == -2) {
+          *failed = true;
+          continue;
+        }
         in.insert(n);
         cav.push_back(n);
         stack.push_back(n);
@@ -344,7 +352,14 @@ static int grow_tets(const Mesh& M, const std::vector<int>& start, const double*
 }
 
 // ------------------------------------------------------------- evaluation
-Decision evaluate(const Mesh& M, int cls, int elem, const double* given, int hint) {
+// seeds (nullable): start tetrahedron -> smallest priority rank of a candidate
+// of this round starting there. A candidate whose region touches a start
+// tetrahedron of a higher-priority candidate is blasted (Sec. 2: regions that
+// meet an element claimed with a higher predetermined priority are stopped).
+// starts (nullable): only locate and return the candidate's start tetrahedra.
+Decision evaluate(const Mesh& M, int cls, int elem, const double* given, int hint,
+                  const std::unordered_map<int, int>* seeds, int rank,
+                  std::vector<int>* starts) {
   Decision d;
   d.cls = cls;
   d.elem = elem;
@@ -405,12 +420,31 @@ Decision evaluate(const Mesh& M, int cls, int elem, const double* given, int hin
     d.loc = elem;
   }
 
+  if (starts) {
+    // the start tetrahedra a candidate claims first: the located tetrahedron,
+    // the two sides of the located subface, or the ring of the subsegment
+    starts->clear();
+    if (cls == CLS_SUBFACE) {
+      auto it = M.faceT.find(M.sf_key(d.loc));
+      if (it != M.faceT.end())
+        for (int t : it->second)
+          if (t >= 0) starts->push_back(t);
+    } else {
+      *starts = tstart;
+    }
+    return d;
+  }
+  auto blasted = [&](int t) {
+    if (!seeds) return false;
+    auto it = seeds->find(t);
+    return it != seeds->end() && it->second < rank;
+  };
+
   // facet part
+  bool failed = false;
   std::unordered_set<int> fset;
   if (cls == CLS_SUBFACE || cls == CLS_SUBSEG) {
-    if (!fstart.empty()) {
-      if (!grow_facet(M, fstart, p, sa, sb, d.fcav, d.fbnd)) return unspl(RS_CLOSURE);
-    }
+    if (!fstart.empty()) grow_facet(M, fstart, p, sa, sb, d.fcav, d.fbnd, &failed);
     for (int s : d.fcav) {
       fset.insert(s);
       auto it = M.faceT.find(M.sf_key(s));
@@ -419,8 +453,22 @@ Decision evaluate(const Mesh& M, int cls, int elem, const double* given, int hin
         if (t >= 0) tstart.push_back(t);
     }
   }
-  int r = grow_tets(M, tstart, p, fset, d.cav, d.bnd);
+  int r = grow_tets(M, tstart, p, fset, d.cav, d.bnd, &failed);
+  // blasted: the region (cavity and shell) touches a higher-priority start
+  for (int t : d.cav)
+    if (blasted(t)) {
+      d.outcome = OUT_BLASTED;
+      return d;
+    }
   if (r) return unspl(r);
+  for (auto& b : d.bnd) {
+    int n = M.nbr(b.first, b.second);
+    if (n >= 0 && blasted(n)) {
+      d.outcome = OUT_BLASTED;
+      return d;
+    }
+  }
+  if (failed) return unspl(RS_CLOSURE);
 
   // Everything that must outlive the insertion lies on the cavity boundary:
   // every cavity vertex and every facet-part boundary edge (otherwise the star
@@ -684,7 +732,16 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
   std::sort(cands.begin(), cands.end());
   int n = (int)cands.size();
   std::vector<Decision> dec(n);
-  for (int i = 0; i < n; ++i) dec[i] = evaluate(M, cls, cands[i].elem, nullptr, -1);
+  // every candidate that locates its point claims its start tetrahedra
+  std::unordered_map<int, int> seeds;
+  for (int i = 0; i < n; ++i) {
+    std::vector<int> st;
+    Decision d0 = evaluate(M, cls, cands[i].elem, nullptr, -1, nullptr, -1, &st);
+    if (d0.outcome != OUT_OK) continue;
+    for (int t : st) seeds.emplace(t, i);
+  }
+  for (int i = 0; i < n; ++i)
+    dec[i] = evaluate(M, cls, cands[i].elem, nullptr, -1, &seeds, i, nullptr);
   std::unordered_map<int, int> tm, sm;
   for (int i = 0; i < n; ++i) {
     if (dec[i].outcome != OUT_OK) continue;
@@ -810,7 +867,7 @@ long refine_S(Mesh& M, double B, long max_steps, SeqStats* st) {
     }
     if (cls < 0) break;
     ++steps;
-    Decision d = evaluate(M, cls, e, nullptr, -1);
+    Decision d = evaluate(M, cls, e, nullptr, -1, nullptr, -1, nullptr);
     if (st) st->evaluated++;
     if (cls == CLS_SUBSEG && d.outcome == OUT_REJECT) {
       // refused only in favour of subsegments that were refused themselves
@@ -946,7 +1003,7 @@ int build_box_delaunay(Mesh& M, const double* pts, int n) {
   for (auto& o : order) {
     int i = o.second;
     while (!M.talive[hint]) --hint;
-    Decision d = evaluate(M, CLS_POINT, i, M.X(i), hint);
+    Decision d = evaluate(M, CLS_POINT, i, M.X(i), hint, nullptr, -1, nullptr);
     if (d.outcome != OUT_OK) {
       ++skipped;
       continue;

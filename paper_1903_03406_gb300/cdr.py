@@ -251,8 +251,8 @@ class Handle:
     GROUPS = ["classify", "order", "split", "locate", "grow1", "grow2", "select", "scan",
               "insert", "compact"]
     COUNTERS = ["refused", "unsplittable", "blasted", "inserted", "retried", "invariant",
-                "tested", "cavity", "boundary", "new_tets", "c10", "c11", "c12", "c13", "c14",
-                "launches"]
+                "tested", "cavity", "boundary", "new_tets", "new_candidates", "blasted_early",
+                "c12", "c13", "c14", "launches"]
 
     def profile(self, enable=-1, reset=False):
         ms = np.zeros(16)

@@ -45,7 +45,7 @@ struct cdr_handle {
   unsigned epoch = 0;
   bool dt_mode = false;
   // mesh arrays
-  Buf bV, bT, bTS, bTflag, bTmark, bTfwd, bSV, bSN, bSflag, bSmust, bSmark, bGV, bGflag, bGmust,
+  Buf bV, bT, bTS, bTflag, bTmark, bTseed, bTfwd, bSV, bSN, bSflag, bSmust, bSmark, bGV, bGflag, bGmust,
       bFQ, bHK, bHV;
   // classification
   Buf bCandS, bCandG, bCandT;
@@ -130,6 +130,7 @@ void bind(cdr_handle* h) {
   m.TS = ptr<int4>(h->bTS);
   m.Tflag = ptr<uint8_t>(h->bTflag);
   m.Tmark = ptr<unsigned long long>(h->bTmark);
+  m.Tseed = ptr<unsigned long long>(h->bTseed);
   m.Tfwd = ptr<int>(h->bTfwd);
   m.SV = ptr<int4>(h->bSV);
   m.SN = ptr<int4>(h->bSN);
@@ -162,6 +163,7 @@ bool grow_tets(cdr_handle* h, int need) {
             ensure(h, h->bTS, cap * sizeof(int4), n * sizeof(int4)) &&
             ensure(h, h->bTflag, cap, n) &&
             ensure(h, h->bTmark, cap * sizeof(unsigned long long), n * 8) &&
+            ensure(h, h->bTseed, cap * sizeof(unsigned long long), n * 8) &&
             ensure(h, h->bTfwd, cap * sizeof(int), n * 4) && ensure(h, h->bCandT, cap, 0);
   if (!ok) return false;
   h->capT = cap;
@@ -481,6 +483,7 @@ int maybe_compact(cdr_handle* h, bool force) {
   m.nT = live;
   bind(h);
   cudaMemsetAsync(h->bTmark.p, 0xff, (size_t)h->capT * 8, h->stream);
+  cudaMemsetAsync(h->bTseed.p, 0xff, (size_t)h->capT * 8, h->stream);
   cudaMemsetAsync(h->bTfwd.p, 0xff, (size_t)h->capT * 4, h->stream);
   dfree(h, alive);
   dfree(h, newid);
@@ -514,6 +517,9 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
     k_point_prefilter<<<gridn(n), 256, 0, s>>>(m, r.status, r.loc, n, e0, 0);
     k_point_prefilter<<<gridn(n), 256, 0, s>>>(m, r.status, r.loc, n, e0, 1);
   }
+  r.seed_epoch = next_epoch(h);
+  launch_seed(m, r, s);
+  h->prof_ctr[15] += 1;
   r.epoch = next_epoch(h);
   pmark(h, PG_GROW1, 0);
   launch_grow1(m, r, s);
@@ -611,7 +617,7 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
     ro->ins = (long long)st[ST_SURV];
     ro->rej = (long long)st[ST_REJECT];
     ro->unspl = (long long)st[ST_UNSPL];
-    ro->blasted = (long long)st[ST_OK];
+    ro->blasted = (long long)st[ST_OK] + (long long)st[ST_BLAST];
   }
   if (exact_overflow_flag(s, true)) return set_err(h, CDR_ERR_INTERNAL);
   {
@@ -770,7 +776,7 @@ int cdr_device_arch(void) { return 103; }
 
 void cdr_destroy(cdr_handle* h) {
   if (!h) return;
-  Buf* all[] = {&h->bV, &h->bT, &h->bTS, &h->bTflag, &h->bTmark, &h->bTfwd, &h->bSV, &h->bSN,
+  Buf* all[] = {&h->bV, &h->bT, &h->bTS, &h->bTflag, &h->bTmark, &h->bTseed, &h->bTfwd, &h->bSV, &h->bSN,
                 &h->bSflag, &h->bSmust, &h->bSmark, &h->bGV, &h->bGflag, &h->bGmust, &h->bFQ,
                 &h->bHK, &h->bHV, &h->bCandS, &h->bCandG, &h->bCandT, &h->bCand, &h->bCand2,
                 &h->bKeys, &h->bKeys2, &h->bSp, &h->bLoc, &h->bStatus, &h->bSurv, &h->bCounts,
@@ -1315,6 +1321,7 @@ int cdr_restore(cdr_handle* h) {
   h->err = 0;
   bind(h);
   cudaMemsetAsync(h->bTmark.p, 0xff, (size_t)h->capT * 8, h->stream);
+  cudaMemsetAsync(h->bTseed.p, 0xff, (size_t)h->capT * 8, h->stream);
   cudaMemsetAsync(h->bSmark.p, 0xff, (size_t)h->capS * 8, h->stream);
   cudaStreamSynchronize(h->stream);
   return cuda_status(h);

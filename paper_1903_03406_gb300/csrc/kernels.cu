@@ -148,6 +148,7 @@ __global__ void k_init_tets(DevMesh m, const int4* tets, int n) {
     m.TS[i] = make_int4(-1, -1, -1, -1);
     m.Tflag[i] = 0;
     m.Tmark[i] = ~0ULL;
+    m.Tseed[i] = ~0ULL;
     m.Tfwd[i] = -1;
   }
 }
@@ -612,6 +613,33 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
   }
 }
 
+
+// Start claims: every candidate whose point was located claims the tetrahedra
+// its region starts from (the located tetrahedron; both sides of the located
+// subface; the ring of the subsegment) with its priority rank.
+__global__ void k_seed(DevMesh m, DevRound r) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
+    if (r.status[i] != OUT_OK) continue;
+    const unsigned long long mk = (r.seed_epoch << 32) | (unsigned long long)(unsigned)i;
+    if (r.cls == CLS_TET || r.cls == CLS_POINT) {
+      atomicMin(&m.Tseed[r.loc[i]], mk);
+    } else if (r.cls == CLS_SUBFACE) {
+      int tf = m.SN[r.loc[i]].w;
+      if (tf < 0) continue;
+      atomicMin(&m.Tseed[tf >> 2], mk);
+      int nb = tet_n_ptr(m, tf >> 2)[tf & 3];
+      if (nb >= 0) atomicMin(&m.Tseed[nb >> 2], mk);
+    } else {
+      int4 G = m.GV[r.cand[i]];
+      edge_ring(m, G.w, G.x, G.y, [&](int t, const TetRec&) { atomicMin(&m.Tseed[t], mk); });
+    }
+  }
+}
+__device__ __forceinline__ bool seed_blasts(const DevMesh& m, const DevRound& r, int t, int i) {
+  unsigned long long v = m.Tseed[t];
+  return (v >> 32) == r.seed_epoch && (unsigned)(v & 0xffffffffu) < (unsigned)i;
+}
+
 // =============================================================== growth
 struct Ws {
   int* cav;   // cavity tets
@@ -689,6 +717,8 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   int ntested = 0;  // per lane
   int outcome = OUT_OK, reason = RS_NONE;
   bool retry = false;  // tier-1 capacity exceeded
+  bool blast = false;  // the region met a higher-priority start (warp-uniform)
+  bool cfail = false;  // a closure failure was met (the growth goes on)
 
   for (int k = lane; k < C::HCAP; k += 32) w.hset[k] = -1;
   __syncwarp();
@@ -700,6 +730,10 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       hs_put(w.hset, C::HCAP, r.loc[i], 1, false);
     }
     ncav = 1;
+    if (seed_blasts(m, r, r.loc[i], i)) {
+      blast = true;
+      goto done;
+    }
   } else if (cls == CLS_SUBFACE) {
     if (lane == 0) w.fcav[0] = r.loc[i];
     nf = 1;
@@ -710,6 +744,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       bool ok = edge_ring(m, G.w, sa, sb, [&](int t, const TetRec& rec) {
         if (nc < C::CAPC) w.cav[nc] = t;
         ++nc;
+        if (seed_blasts(m, r, t, i)) bad |= 2;
         hs_put(w.hset, C::HCAP, t, 1, false);
         for (int f = 0; f < 4; ++f) {
           int x = vid(geti(rec.v, f));
@@ -725,11 +760,15 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           }
         }
       });
-      bad = ok ? 0 : 1;
+      bad |= ok ? 0 : 1;
     }
     nc = __shfl_sync(FULLMASK, nc, 0);
     nfl = __shfl_sync(FULLMASK, nfl, 0);
     bad = __shfl_sync(FULLMASK, bad, 0);
+    if (bad & 2) {
+      blast = true;
+      goto done;
+    }
     if (bad) {
       outcome = OUT_UNSPL;
       reason = RS_WALK_LIMIT;
@@ -809,11 +848,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         __syncwarp();
         if (nf > C::CAPF) break;
       }
-      if (fail) {
-        outcome = OUT_UNSPL;
-        reason = RS_CLOSURE;
-        goto done;
-      }
+      cfail |= fail;
       if (nf > C::CAPF) {
         retry = true;
         goto done;
@@ -872,17 +907,20 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         }
         for (int side = 0; side < 2; ++side) {
           int c = side == 0 ? c0 : c1;
-          bool pred = false;
+          bool pred = false, bl = false;
           if (c >= 0) {
             int res = hs_put(w.hset, C::HCAP, c, 1, false);
             if (res < 0) retry = true;
             pred = res == 1;
+            bl = seed_blasts(m, r, c, i);
           }
           retry = __any_sync(FULLMASK, retry);
+          blast |= __any_sync(FULLMASK, bl);
           wappend(w.cav, ncav, C::CAPC, pred, c, lane);
         }
         __syncwarp();
       }
+      if (blast) goto done;
       if (retry || ncav > C::CAPC) {
         retry = true;
         goto done;
@@ -911,22 +949,25 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           }
           unsigned grp = __match_any_sync(FULLMASK, cand);
           bool leader = cand >= 0 && (__ffs(grp) - 1) == lane;
-          bool add = false;
+          bool add = false, bl = false;
           if (leader) {
             bool in = tet_in_sphere(m, ld_tet(m, cand), p);
             ++ntested;
             int res = hs_put(w.hset, C::HCAP, cand, in ? 1 : 2, false);
             if (res < 0) retry = true;
             add = in && res == 1;
+            bl = add && seed_blasts(m, r, cand, i);
           }
           retry = __any_sync(FULLMASK, retry);
+          blast |= __any_sync(FULLMASK, bl);
           wappend(w.cav, ncav, C::CAPC, add, cand, lane);
           __syncwarp();
-          if (retry || ncav > C::CAPC) break;
+          if (blast || retry || ncav > C::CAPC) break;
         }
         head = end;
-        if (retry || ncav > C::CAPC) break;
+        if (blast || retry || ncav > C::CAPC) break;
       }
+      if (blast) goto done;
       if (retry || ncav > C::CAPC) {
         retry = true;
         goto done;
@@ -953,17 +994,16 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         fail |= __any_sync(FULLMASK, f_);
         unsigned grp = __match_any_sync(FULLMASK, cand);
         bool leader = cand >= 0 && (__ffs(grp) - 1) == lane;
-        bool add = false;
+        bool add = false, bl = false;
         if (leader) {
+          // (a tet tested out before has its state forced to in)
           int res = hs_put(w.hset, C::HCAP, cand, 1, true);
           if (res < 0) retry = true;
           add = true;
-          if (res == 0) {
-            // it was tested out before (state now forced to in); append it
-            add = true;
-          }
+          bl = seed_blasts(m, r, cand, i);
         }
         retry = __any_sync(FULLMASK, retry);
+        blast |= __any_sync(FULLMASK, bl);
         __syncwarp();
         // a tet appended earlier in this pass is already in; skip duplicates
         if (add && in_list(w.cav, min(ncav, C::CAPC), cand)) add = false;
@@ -974,11 +1014,8 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         __syncwarp();
         if (retry || ncav > C::CAPC) break;
       }
-      if (fail) {
-        outcome = OUT_UNSPL;
-        reason = RS_CLOSURE;
-        goto done;
-      }
+      cfail |= fail;
+      if (blast) goto done;
       if (retry || ncav > C::CAPC) {
         retry = true;
         goto done;
@@ -1023,10 +1060,22 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       retry = true;
       goto done;
     }
+    // the shell counts as touched
+    for (int base = 0; base < nbnd; base += 32) {
+      int it = base + lane;
+      bool bl = it < nbnd && w.bout[it] >= 0 && seed_blasts(m, r, w.bout[it] >> 2, i);
+      blast |= __any_sync(FULLMASK, bl);
+    }
+    if (blast) goto done;
   }
   if (ncav > kCavLimit) {
     outcome = OUT_UNSPL;
     reason = RS_OVERFLOW;
+    goto done;
+  }
+  if (cfail) {
+    outcome = OUT_UNSPL;
+    reason = RS_CLOSURE;
     goto done;
   }
   __syncwarp();
@@ -1242,6 +1291,13 @@ done:
       atomicAdd(&r.stats[ST_BND], (unsigned long long)nbnd);
     }
   }
+  if (blast) {
+    if (lane == 0) {
+      set_status(r, i, OUT_BLASTED, RS_NONE);
+      slab[0] = slab[1] = slab[2] = slab[3] = 0;
+    }
+    return;
+  }
   if (retry) {
     if (lane == 0) {
       set_status(r, i, OUT_RETRY, RS_NONE);
@@ -1376,6 +1432,7 @@ __global__ void k_select(DevMesh m, DevRound r) {
       }
       if (outcome == OUT_OK) atomicAdd(&r.stats[surv ? ST_SURV : ST_OK], 1ULL);
       else if (outcome == OUT_REJECT) atomicAdd(&r.stats[ST_REJECT], 1ULL);
+      else if (outcome == OUT_BLASTED) atomicAdd(&r.stats[ST_BLAST], 1ULL);
       else atomicAdd(&r.stats[ST_UNSPL], 1ULL);
     }
   }
@@ -1448,6 +1505,7 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       }
       m.TS[nid] = ts;
       m.Tmark[nid] = ~0ULL;
+      m.Tseed[nid] = ~0ULL;
       m.Tfwd[nid] = -1;
       if (bout[j] >= 0) tet_n_ptr(m, bout[j] >> 2)[bout[j] & 3] = (nid << 2) | f;
     }
@@ -1754,6 +1812,9 @@ void launch_split(const DevMesh& m, const DevRound& r, cudaStream_t s) {
 }
 void launch_locate(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s) {
   if (r.n > 0) k_locate<<<grid_for(r.n, 128), 128, 0, s>>>(m, r, hint);
+}
+void launch_seed(const DevMesh& m, const DevRound& r, cudaStream_t s) {
+  if (r.n > 0) k_seed<<<grid_for(r.n, 256), 256, 0, s>>>(m, r);
 }
 void launch_grow1(const DevMesh& m, const DevRound& r, cudaStream_t s) {
   if (r.n <= 0) return;

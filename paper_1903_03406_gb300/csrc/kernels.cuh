@@ -37,6 +37,7 @@ void launch_tiefix(const DevMesh& m, int cls, const unsigned long long* keys, in
 // one round
 void launch_split(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_locate(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s);
+void launch_seed(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_grow1(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s);
 void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s);

@@ -11,6 +11,7 @@
 //   TS     int4 per tet: subface id on each face (-1), read only for marked faces
 //   Tflag  bit0 dead, bit1 bad, bit2 unsplittable
 //   Tmark  64-bit priority marks (round epoch << 32 | candidate rank)
+//   Tseed  64-bit claims of start tetrahedra, same encoding
 //   Tfwd   for a dead tet, one tet of the star that replaced it
 //   SV     int4 per subface (a, b, c, facet)
 //   SN     int4 per subface: facet neighbour across edge k (opposite vertex k),
@@ -46,7 +47,7 @@ constexpr int kMaxTets = 1 << 29;
 
 enum : uint8_t { F_DEAD = 1, F_BAD = 2, F_UNSPL = 4 };
 enum { CLS_SUBSEG = 0, CLS_SUBFACE = 1, CLS_TET = 2, CLS_POINT = 3 };
-enum { OUT_OK = 0, OUT_REJECT = 1, OUT_UNSPL = 2, OUT_RETRY = 3 };
+enum { OUT_OK = 0, OUT_REJECT = 1, OUT_UNSPL = 2, OUT_RETRY = 3, OUT_BLASTED = 4 };
 enum {
   RS_NONE = 0,
   RS_BADPOINT = 1,
@@ -74,6 +75,7 @@ struct DevMesh {
   int4* TS;
   uint8_t* Tflag;
   unsigned long long* Tmark;
+  unsigned long long* Tseed;  // start-tetrahedron claims (round epoch << 32 | rank)
   int* Tfwd;
   int4* SV;
   int4* SN;
@@ -127,6 +129,7 @@ struct DevRound {
   V4* sp;                 // splitting points
   int* status;                 // outcome | reason << 8
   unsigned long long epoch;    // mark = epoch << 32 | rank
+  unsigned long long seed_epoch;  // start claims of this round
   int* slab1;                  // tier-1 slabs (n * STRIDE1)
   int* slab2;                  // tier-2 slabs (n2 * STRIDE2)
   int* slab2_of;               // candidate -> tier-2 slab index (-1)
@@ -155,6 +158,7 @@ enum {
   ST_BND,     // boundary faces of evaluated regions
   ST_NEWT,    // tetrahedra written by insertion
   ST_NEWCAND,  // refusals that flagged a subsegment not yet a candidate
+  ST_BLAST,    // regions stopped on a higher-priority start tetrahedron
   ST_COUNT
 };
 
