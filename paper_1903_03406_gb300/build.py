@@ -28,8 +28,11 @@ def nvcc() -> str:
 
 
 def _flags():
-    return [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-            "-diag-suppress", "1444"]
+    f = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
+         "-diag-suppress", "1444"]
+    if os.environ.get("CDR_CHECKED"):
+        f.append("-DCDR_CHECKED")  # bounds-checked diagnostic build
+    return f
 
 
 def up_to_date() -> bool:

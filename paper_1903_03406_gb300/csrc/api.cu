@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -143,6 +144,10 @@ void bind(cdr_handle* h) {
   m.FQ = ptr<V4>(h->bFQ);
   m.HK = ptr<unsigned long long>(h->bHK);
   m.HV = ptr<int>(h->bHV);
+  m.capV = h->capV;
+  m.capT = h->capT;
+  m.capS = h->capS;
+  m.capG = h->capG;
 }
 
 bool grow_verts(cdr_handle* h, int need) {
@@ -544,11 +549,13 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
     if (n2 > 0) {
       const size_t stride2 = SlabLayout<Tier2>::STRIDE;
       int warps = std::min(n2, 152 * 4);
+      warps += warps & 1;  // the launch runs two warps per block
       if (!ensure(h, h->bSlab2, (size_t)n2 * stride2 * 4) ||
           !ensure(h, h->bWs2, (size_t)warps * Tier2::HCAP * 4))
         return CDR_ERR_OOM;
       r.slab2 = ptr<int>(h->bSlab2);
       r.ws2 = ptr<int>(h->bWs2);
+      r.nws2 = warps;
       r.n2 = n2;
       k_scatter_slab2<<<gridn(n2), 256, 0, s>>>(r.list2, n2, r.slab2_of);
       pmark(h, PG_GROW2, 0);
@@ -620,6 +627,14 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
     ro->blasted = (long long)st[ST_OK] + (long long)st[ST_BLAST];
   }
   if (exact_overflow_flag(s, true)) return set_err(h, CDR_ERR_INTERNAL);
+  {
+    int info[4];
+    if (checked_error(info, s)) {
+      fprintf(stderr, "cdr checked build: bad index %d (bound %d) at kernels.cu:%d, round %u\n",
+              info[2], info[3], info[1], h->epoch);
+      return set_err(h, CDR_ERR_INTERNAL);
+    }
+  }
   {
     unsigned long long ctr[ST_COUNT];
     cudaMemcpyAsync(ctr, h->bStats.p, sizeof(ctr), cudaMemcpyDeviceToHost, s);

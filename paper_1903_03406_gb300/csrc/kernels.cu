@@ -20,6 +20,27 @@ namespace cdr {
 
 #define FULLMASK 0xffffffffu
 
+// Checked build (CDR_CHECKED): every mesh-array index is bounds-checked; a bad
+// index is recorded (site = source line, index, bound) and replaced by 0 so
+// that nothing is read or written out of bounds.
+#ifdef CDR_CHECKED
+static __device__ int g_chk[4];
+__device__ __noinline__ int cdr_bad_index(int site, long long idx, int cap) {
+  if (atomicCAS(&g_chk[0], 0, 1) == 0) {
+    g_chk[1] = site;
+    g_chk[2] = (int)idx;
+    g_chk[3] = cap;
+  }
+  return 0;
+}
+#define CKI(idx, cap) (((unsigned long long)(long long)(idx) < (unsigned long long)(cap)) ? (idx) : cdr_bad_index(__LINE__, (long long)(idx), (cap)))
+// a neighbour link (tet << 2 | face) or -1 whose tet is below `bound`
+#define CKL(link, bound) do { int l_ = (link); if (l_ < -1 || (l_ >= 0 && (l_ >> 2) >= (bound))) cdr_bad_index(__LINE__, (long long)l_, (bound)); } while (0)
+#else
+#define CKI(idx, cap) (idx)
+#define CKL(link, bound) do { } while (0)
+#endif
+
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ int geti(const int4& a, int k) {
   return k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? a.z : a.w));
@@ -32,14 +53,14 @@ __device__ __forceinline__ void seti(int4& a, int k, int v) {
 }
 __device__ __forceinline__ int vid(int x) { return x & kVidMask; }
 __device__ __forceinline__ D3 vtx(const DevMesh& m, int v) {
-  V4 q = m.V[v];
+  V4 q = m.V[CKI(v, m.capV)];
   return D3{q.x, q.y, q.z};
 }
-__device__ __forceinline__ TetRec ld_tet(const DevMesh& m, int t) { return m.T[t]; }
-__device__ __forceinline__ int* tet_n_ptr(const DevMesh& m, int t) { return &m.T[t].n.x; }
-__device__ __forceinline__ int* tet_v_ptr(const DevMesh& m, int t) { return &m.T[t].v.x; }
-__device__ __forceinline__ int* ts_ptr(const DevMesh& m, int t) { return &m.TS[t].x; }
-__device__ __forceinline__ int* sn_ptr(const DevMesh& m, int s) { return &m.SN[s].x; }
+__device__ __forceinline__ TetRec ld_tet(const DevMesh& m, int t) { return m.T[CKI(t, m.capT)]; }
+__device__ __forceinline__ int* tet_n_ptr(const DevMesh& m, int t) { return &m.T[CKI(t, m.capT)].n.x; }
+__device__ __forceinline__ int* tet_v_ptr(const DevMesh& m, int t) { return &m.T[CKI(t, m.capT)].v.x; }
+__device__ __forceinline__ int* ts_ptr(const DevMesh& m, int t) { return &m.TS[CKI(t, m.capT)].x; }
+__device__ __forceinline__ int* sn_ptr(const DevMesh& m, int s) { return &m.SN[CKI(s, m.capS)].x; }
 
 // edge e of a tetrahedron: 0:(0,1) 1:(0,2) 2:(0,3) 3:(1,2) 4:(1,3) 5:(2,3)
 __device__ __forceinline__ int edge_i(int e) { return e < 3 ? 0 : (e < 5 ? 1 : 2); }
@@ -144,12 +165,12 @@ __global__ void k_init_tets(DevMesh m, const int4* tets, int n) {
     TetRec r;
     r.v = tets[i];
     r.n = make_int4(-1, -1, -1, -1);
-    m.T[i] = r;
-    m.TS[i] = make_int4(-1, -1, -1, -1);
-    m.Tflag[i] = 0;
-    m.Tmark[i] = ~0ULL;
-    m.Tseed[i] = ~0ULL;
-    m.Tfwd[i] = -1;
+    m.T[CKI(i, m.capT)] = r;
+    m.TS[CKI(i, m.capT)] = make_int4(-1, -1, -1, -1);
+    m.Tflag[CKI(i, m.capT)] = 0;
+    m.Tmark[CKI(i, m.capT)] = ~0ULL;
+    m.Tseed[CKI(i, m.capT)] = ~0ULL;
+    m.Tfwd[CKI(i, m.capT)] = -1;
   }
 }
 
@@ -157,7 +178,7 @@ __global__ void k_face_keys(DevMesh m, unsigned long long* hi, unsigned int* lo,
   int n = m.nT * 4;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int t = i >> 2, f = i & 3;
-    int4 v = m.T[t].v;
+    int4 v = m.T[CKI(t, m.capT)].v;
     int w[3], k = 0;
     for (int j = 0; j < 4; ++j)
       if (j != f) w[k++] = vid(geti(v, j));
@@ -176,6 +197,8 @@ __global__ void k_pair_faces(DevMesh m, const unsigned long long* hi, const unsi
     if (eqn && eqp) atomicOr(err, 1);  // a face shared by three tetrahedra
     if (eqn) {
       int a = val[i], b = val[i + 1];
+      CKL(a, m.nT);
+      CKL(b, m.nT);
       tet_n_ptr(m, a >> 2)[a & 3] = b;
       tet_n_ptr(m, b >> 2)[b & 3] = a;
     }
@@ -197,11 +220,11 @@ __global__ void k_label_subfaces(DevMesh m, const int4* tris, int n, const unsig
                                  const unsigned int* lo, const int* val, int nfaces, int* err) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     int4 S = tris[s];
-    m.SV[s] = S;
-    m.SN[s] = make_int4(-1, -1, -1, -1);
-    m.Sflag[s] = 0;
-    m.Smust[s] = 0;
-    m.Smark[s] = ~0ULL;
+    m.SV[CKI(s, m.capS)] = S;
+    m.SN[CKI(s, m.capS)] = make_int4(-1, -1, -1, -1);
+    m.Sflag[CKI(s, m.capS)] = 0;
+    m.Smust[CKI(s, m.capS)] = 0;
+    m.Smark[CKI(s, m.capS)] = ~0ULL;
     int a = S.x, b = S.y, c = S.z;
     if (a < 0 || b < 0 || c < 0 || a >= m.nV || b >= m.nV || c >= m.nV || S.w < 0 || S.w >= m.nF) {
       atomicOr(err, 8);
@@ -215,7 +238,7 @@ __global__ void k_label_subfaces(DevMesh m, const int4* tris, int n, const unsig
       continue;
     }
     int first = val[j];
-    m.SN[s].w = first;
+    m.SN[CKI(s, m.capS)].w = first;
     for (int q = j; q < nfaces && q < j + 2 && hi[q] == h && lo[q] == (unsigned)c; ++q) {
       int tf = val[q];
       ts_ptr(m, tf >> 2)[tf & 3] = s;
@@ -228,7 +251,7 @@ __global__ void k_subface_edge_keys(DevMesh m, unsigned long long* hi, unsigned 
   int n = m.nS * 3;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int s = i / 3, k = i % 3;
-    int4 S = m.SV[s];
+    int4 S = m.SV[CKI(s, m.capS)];
     int u = geti(S, (k + 1) % 3), w = geti(S, (k + 2) % 3);
     if (u > w) { int t = u; u = w; w = t; }
     hi[i] = ((unsigned long long)(unsigned)u << 32) | (unsigned)w;
@@ -261,21 +284,21 @@ __global__ void k_hash_clear(DevMesh m) {
 }
 __global__ void k_hash_insert_subsegs(DevMesh m, int g0, int g1) {
   for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += gridDim.x * blockDim.x) {
-    if (m.Gflag[g] & F_DEAD) continue;
-    int4 G = m.GV[g];
+    if (m.Gflag[CKI(g, m.capG)] & F_DEAD) continue;
+    int4 G = m.GV[CKI(g, m.capG)];
     hash_insert(m, ekey(G.x, G.y), g);
   }
 }
 __global__ void k_mark_edges(DevMesh m) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x) {
-    if (m.Tflag[t] & F_DEAD) continue;
-    int4 v = m.T[t].v;
+    if (m.Tflag[CKI(t, m.capT)] & F_DEAD) continue;
+    int4 v = m.T[CKI(t, m.capT)].v;
     for (int e = 0; e < 6; ++e) {
       int a = vid(geti(v, edge_i(e))), b = vid(geti(v, edge_j(e)));
       int g = hash_lookup(m, ekey(a, b));
       if (g >= 0) {
         atomicOr(&tet_v_ptr(m, t)[e >> 1], 1 << (29 + (e & 1)));
-        m.GV[g].w = t;
+        m.GV[CKI(g, m.capG)].w = t;
       }
     }
   }
@@ -284,26 +307,26 @@ __global__ void k_check_create(DevMesh m, int* err) {
   int n = m.nT + m.nG;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < m.nT) {
-      TetRec r = m.T[i];
+      TetRec r = m.T[CKI(i, m.capT)];
       int a = vid(r.v.x), b = vid(r.v.y), c = vid(r.v.z), d = vid(r.v.w);
       if (orient3d(vtx(m, a), vtx(m, b), vtx(m, c), vtx(m, d)) <= 0) atomicOr(err, 2);
       for (int f = 0; f < 4; ++f)
         if (geti(r.n, f) < 0 && !face_sub(r.v, f)) atomicOr(err, 4);  // hull face not a subface
     } else {
       int g = i - m.nT;
-      if (m.GV[g].w < 0) atomicOr(err, 64);  // subsegment label is not a mesh edge
+      if (m.GV[CKI(g, m.capG)].w < 0) atomicOr(err, 64);  // subsegment label is not a mesh edge
     }
   }
 }
 __global__ void k_recompute_bad(DevMesh m, double B) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x) {
-    uint8_t f = m.Tflag[t];
+    uint8_t f = m.Tflag[CKI(t, m.capT)];
     if (f & F_DEAD) continue;
-    int4 v = m.T[t].v;
+    int4 v = m.T[CKI(t, m.capT)].v;
     int s[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
     sort4(s);
     bool bad = tet_bad_fixed(vtx(m, s[0]), vtx(m, s[1]), vtx(m, s[2]), vtx(m, s[3]), B);
-    m.Tflag[t] = bad ? (f | F_BAD) : (f & ~F_BAD);
+    m.Tflag[CKI(t, m.capT)] = bad ? (f | F_BAD) : (f & ~F_BAD);
   }
 }
 
@@ -313,7 +336,7 @@ __global__ void k_recompute_bad(DevMesh m, double B) {
 // start tet is invalid or the ring is longer than the step limit.
 template <class F>
 __device__ bool edge_ring(const DevMesh& m, int t0, int a, int b, F visit) {
-  if (t0 < 0 || t0 >= m.nT || (m.Tflag[t0] & F_DEAD)) return false;
+  if (t0 < 0 || t0 >= m.nT || (m.Tflag[CKI(t0, m.capT)] & F_DEAD)) return false;
   TetRec r0 = ld_tet(m, t0);
   int ia = -1, ib = -1;
   for (int k = 0; k < 4; ++k) {
@@ -359,16 +382,16 @@ __global__ void k_classify(DevMesh m, unsigned char* candS, unsigned char* candG
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < m.nG) {
       int g = i;
-      uint8_t f = m.Gflag[g];
+      uint8_t f = m.Gflag[CKI(g, m.capG)];
       if (f & (F_DEAD | F_UNSPL)) {
         candG[g] = 0;
         continue;
       }
-      if (m.Gmust[g]) {
+      if (m.Gmust[CKI(g, m.capG)]) {
         candG[g] = 1;
         continue;
       }
-      int4 G = m.GV[g];
+      int4 G = m.GV[CKI(g, m.capG)];
       D3 A = vtx(m, G.x), Bp = vtx(m, G.y);
       bool enc = false;
       bool ok = edge_ring(m, G.w, G.x, G.y, [&](int t, const TetRec& r) {
@@ -382,17 +405,17 @@ __global__ void k_classify(DevMesh m, unsigned char* candS, unsigned char* candG
       candG[g] = enc ? 1 : 0;
     } else if (i < m.nG + m.nS) {
       int s = i - m.nG;
-      uint8_t f = m.Sflag[s];
+      uint8_t f = m.Sflag[CKI(s, m.capS)];
       if (f & (F_DEAD | F_UNSPL)) {
         candS[s] = 0;
         continue;
       }
-      if (m.Smust[s]) {
+      if (m.Smust[CKI(s, m.capS)]) {
         candS[s] = 1;
         continue;
       }
-      int4 S = m.SV[s];
-      int w = m.SN[s].w;
+      int4 S = m.SV[CKI(s, m.capS)];
+      int w = m.SN[CKI(s, m.capS)].w;
       if (w < 0 || (w >> 2) >= m.nT) {
         atomicOr(err, 2);
         candS[s] = 0;
@@ -409,7 +432,7 @@ __global__ void k_classify(DevMesh m, unsigned char* candS, unsigned char* candG
       candS[s] = enc ? 1 : 0;
     } else {
       int t = i - m.nG - m.nS;
-      uint8_t f = m.Tflag[t];
+      uint8_t f = m.Tflag[CKI(t, m.capT)];
       candT[t] = ((f & (F_DEAD | F_UNSPL | F_BAD)) == F_BAD) ? 1 : 0;
     }
   }
@@ -417,13 +440,13 @@ __global__ void k_classify(DevMesh m, unsigned char* candS, unsigned char* candG
 
 __device__ int elem_key(const DevMesh& m, int cls, int e, int* ids) {
   if (cls == CLS_SUBSEG) {
-    int4 G = m.GV[e];
+    int4 G = m.GV[CKI(e, m.capG)];
     ids[0] = min(G.x, G.y);
     ids[1] = max(G.x, G.y);
     return 2;
   }
   if (cls == CLS_SUBFACE) {
-    int4 S = m.SV[e];
+    int4 S = m.SV[CKI(e, m.capS)];
     ids[0] = S.x;
     ids[1] = S.y;
     ids[2] = S.z;
@@ -431,7 +454,7 @@ __device__ int elem_key(const DevMesh& m, int cls, int e, int* ids) {
     return 3;
   }
   if (cls == CLS_TET) {
-    int4 v = m.T[e].v;
+    int4 v = m.T[CKI(e, m.capT)].v;
     ids[0] = vid(v.x);
     ids[1] = vid(v.y);
     ids[2] = vid(v.z);
@@ -484,7 +507,7 @@ __global__ void k_split(DevMesh m, DevRound r) {
     D3 p{0, 0, 0};
     bool ok = true;
     if (r.cls == CLS_SUBSEG) {
-      int4 G = m.GV[e];
+      int4 G = m.GV[CKI(e, m.capG)];
       p = midpoint_fixed(vtx(m, min(G.x, G.y)), vtx(m, max(G.x, G.y)));
       ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
     } else if (r.cls == CLS_SUBFACE) {
@@ -550,12 +573,12 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
             done = true;
             break;
           }
-          if (m.Sflag[s] & F_UNSPL) {
+          if (m.Sflag[CKI(s, m.capS)] & F_UNSPL) {
             set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
           } else {
             set_status(r, i, OUT_REJECT, RS_WALK_SUBFACE);
           }
-          m.Smust[s] = 1;
+          m.Smust[CKI(s, m.capS)] = 1;
           done = true;
           break;
         }
@@ -572,7 +595,7 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
       int s = e;
       bool done = false;
       for (int it = 0; it < m.walk_limit && !done; ++it) {
-        int4 S = m.SV[s];
+        int4 S = m.SV[CKI(s, m.capS)];
         int w = sf_wind(m, S);
         int best = -1, b0 = 0, b1 = 0;
         for (int k = 0; k < 3; ++k) {
@@ -591,15 +614,15 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
           done = true;
           break;
         }
-        int nb = geti(m.SN[s], best);
+        int nb = geti(m.SN[CKI(s, m.capS)], best);
         if (nb < 0) {
           int g = hash_lookup(m, ekey(b0, b1));
           if (g < 0) {
             set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
           } else {
-            if (m.Gflag[g] & F_UNSPL) set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
+            if (m.Gflag[CKI(g, m.capG)] & F_UNSPL) set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
             else set_status(r, i, OUT_REJECT, RS_WALK_SUBSEG);
-            m.Gmust[g] = 1;
+            m.Gmust[CKI(g, m.capG)] = 1;
           }
           done = true;
           break;
@@ -622,23 +645,36 @@ __global__ void k_seed(DevMesh m, DevRound r) {
     if (r.status[i] != OUT_OK) continue;
     const unsigned long long mk = (r.seed_epoch << 32) | (unsigned long long)(unsigned)i;
     if (r.cls == CLS_TET || r.cls == CLS_POINT) {
-      atomicMin(&m.Tseed[r.loc[i]], mk);
+      atomicMin(&m.Tseed[CKI(r.loc[i], m.capT)], mk);
     } else if (r.cls == CLS_SUBFACE) {
-      int tf = m.SN[r.loc[i]].w;
+      int tf = m.SN[CKI(r.loc[i], m.capS)].w;
       if (tf < 0) continue;
-      atomicMin(&m.Tseed[tf >> 2], mk);
+      atomicMin(&m.Tseed[CKI(tf >> 2, m.capT)], mk);
       int nb = tet_n_ptr(m, tf >> 2)[tf & 3];
-      if (nb >= 0) atomicMin(&m.Tseed[nb >> 2], mk);
+      if (nb >= 0) atomicMin(&m.Tseed[CKI(nb >> 2, m.capT)], mk);
     } else {
-      int4 G = m.GV[r.cand[i]];
-      edge_ring(m, G.w, G.x, G.y, [&](int t, const TetRec&) { atomicMin(&m.Tseed[t], mk); });
+      int4 G = m.GV[CKI(r.cand[i], m.capG)];
+      edge_ring(m, G.w, G.x, G.y, [&](int t, const TetRec&) { atomicMin(&m.Tseed[CKI(t, m.capT)], mk); });
     }
   }
 }
+#ifdef CDR_CHECKED
+#define seed_blasts(m, r, t, i) seed_blasts_at(m, r, t, i, __LINE__)
+__device__ __forceinline__ bool seed_blasts_at(const DevMesh& m, const DevRound& r, int t, int i,
+                                               int site) {
+  if ((unsigned)t >= (unsigned)m.nT) {
+    cdr_bad_index(site * 10 + r.cls, (long long)t, m.nT);
+    return false;
+  }
+  unsigned long long v = m.Tseed[t];
+  return (v >> 32) == r.seed_epoch && (unsigned)(v & 0xffffffffu) < (unsigned)i;
+}
+#else
 __device__ __forceinline__ bool seed_blasts(const DevMesh& m, const DevRound& r, int t, int i) {
   unsigned long long v = m.Tseed[t];
   return (v >> 32) == r.seed_epoch && (unsigned)(v & 0xffffffffu) < (unsigned)i;
 }
+#endif
 
 // =============================================================== growth
 struct Ws {
@@ -709,7 +745,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   const D3 p{q4.x, q4.y, q4.z};
   int sa = -1, sb = -1;
   if (cls == CLS_SUBSEG) {
-    int4 G = m.GV[elem];
+    int4 G = m.GV[CKI(elem, m.capG)];
     sa = G.x;
     sb = G.y;
   }
@@ -740,7 +776,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   } else {  // subsegment: the ring of its edge, and the subfaces on the edge
     int nc = 0, nfl = 0, bad = 0;
     if (lane == 0) {
-      int4 G = m.GV[elem];
+      int4 G = m.GV[CKI(elem, m.capG)];
       bool ok = edge_ring(m, G.w, sa, sb, [&](int t, const TetRec& rec) {
         if (nc < C::CAPC) w.cav[nc] = t;
         ++nc;
@@ -795,17 +831,17 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           int cand = -1;
           if (it < items) {
             int s = w.fcav[head + it / 3], k = it % 3;
-            int4 S = m.SV[s];
+            int4 S = m.SV[CKI(s, m.capS)];
             int u = geti(S, (k + 1) % 3), x = geti(S, (k + 2) % 3);
             bool split = sa >= 0 && ((u == sa && x == sb) || (u == sb && x == sa));
-            int nb = geti(m.SN[s], k);
+            int nb = geti(m.SN[CKI(s, m.capS)], k);
             if (!split && nb >= 0 && !in_list(w.fcav, min(nf, C::CAPF), nb)) cand = nb;
           }
           // one lane per distinct neighbour tests it
           unsigned grp = __match_any_sync(FULLMASK, cand);
           bool leader = cand >= 0 && (__ffs(grp) - 1) == lane;
           bool add = false;
-          if (leader) add = sf_incircle(m, m.SV[cand], p);
+          if (leader) add = sf_incircle(m, m.SV[CKI(cand, m.capS)], p);
           wappend(w.fcav, nf, C::CAPF, add, cand, lane);
           __syncwarp();
         }
@@ -825,10 +861,10 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         bool f_ = false;
         if (it < items) {
           int s = w.fcav[it / 3], k = it % 3;
-          int4 S = m.SV[s];
+          int4 S = m.SV[CKI(s, m.capS)];
           int u = geti(S, (k + 1) % 3), x = geti(S, (k + 2) % 3);
           bool split = sa >= 0 && ((u == sa && x == sb) || (u == sb && x == sa));
-          int nb = geti(m.SN[s], k);
+          int nb = geti(m.SN[CKI(s, m.capS)], k);
           if (!split && !(nb >= 0 && in_list(w.fcav, nf, nb))) {
             if (sf_orient_rep(m, S, k, p) != sf_wind(m, S)) {
               if (nb < 0) f_ = true;
@@ -864,12 +900,12 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         int val = 0, eu = 0, ew = 0, fid = 0;
         if (it < items) {
           int s = w.fcav[it / 3], k = it % 3;
-          int4 S = m.SV[s];
+          int4 S = m.SV[CKI(s, m.capS)];
           eu = geti(S, (k + 1) % 3);
           ew = geti(S, (k + 2) % 3);
           fid = S.w;
           bool split = sa >= 0 && ((eu == sa && ew == sb) || (eu == sb && ew == sa));
-          int nb = geti(m.SN[s], k);
+          int nb = geti(m.SN[CKI(s, m.capS)], k);
           pred = !split && !(nb >= 0 && in_list(w.fcav, nf, nb));
           val = (s << 2) | k;
         }
@@ -896,7 +932,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         int it = base + lane;
         int c0 = -1, c1 = -1;
         if (it < nf) {
-          int tf = m.SN[w.fcav[it]].w;
+          int tf = m.SN[CKI(w.fcav[it], m.capS)].w;
           if (tf >= 0 && (tf >> 2) < m.nT) {
             c0 = tf >> 2;
             int nb = tet_n_ptr(m, c0)[tf & 3];
@@ -942,6 +978,8 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
             int t = w.cav[head + (it >> 2)], f = it & 3;
             TetRec rec = ld_tet(m, t);
             int nb = geti(rec.n, f);
+            CKL(nb, m.nT);
+            CKI(t, m.nT);
             if (nb >= 0 && !face_sub(rec.v, f)) {
               int nt = nb >> 2;
               if (hs_find(w.hset, C::HCAP, nt) == 0 && orient_rep(m, rec, f, p) > 0) cand = nt;
@@ -1038,6 +1076,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         pred = !removed && !interior;
         bi = (t << 2) | f;
         bo = nb;
+        CKL(nb, m.nT);
         int z[3], k = 0;
         for (int j = 0; j < 4; ++j)
           if (j != f) z[k++] = vid(geti(rec.v, j));
@@ -1056,6 +1095,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       }
       nbnd += __popc(bal);
     }
+    __syncwarp();  // the lists written above are read by other lanes below
     if (nbnd > C::CAPB) {
       retry = true;
       goto done;
@@ -1089,7 +1129,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       int it = base + lane;
       bool miss = false;
       if (it < items) {
-        int v = vid(geti(m.T[w.cav[it >> 2]].v, it & 3));
+        int v = vid(geti(m.T[CKI(w.cav[it >> 2], m.capT)].v, it & 3));
         miss = !in_list(w.bv, 3 * nbnd, v);
       }
       lost = __any_sync(FULLMASK, miss);
@@ -1185,7 +1225,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       int it = base + lane;
       bool near = false;
       if (it < items) {
-        int v = vid(geti(m.T[w.cav[it >> 2]].v, it & 3));
+        int v = vid(geti(m.T[CKI(w.cav[it >> 2], m.capT)].v, it & 3));
         near = dist2_fixed(p, vtx(m, v)) <= m.guard2;
       }
       g |= __any_sync(FULLMASK, near);
@@ -1206,14 +1246,14 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         if (it < nbnd) {
           int bij = w.bin[it];
           int t = bij >> 2, f = bij & 3;
-          if (face_sub(m.T[t].v, f)) {
+          if (face_sub(m.T[CKI(t, m.capT)].v, f)) {
             const int* F = w.bv + 3 * it;
             if (equatorial(vtx(m, F[0]), vtx(m, F[1]), vtx(m, F[2]), p) < 0) {
               int s = ts_ptr(m, t)[f];
               enc = true;
               if (s >= 0 && s < m.nS) {
-                un = (m.Sflag[s] & F_UNSPL) != 0;
-                m.Smust[s] = 1;
+                un = (m.Sflag[CKI(s, m.capS)] & F_UNSPL) != 0;
+                m.Smust[CKI(s, m.capS)] = 1;
               } else {
                 atomicAdd(&r.stats[ST_ITER], 1ULL);
               }
@@ -1231,7 +1271,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       bool flag = false, un = false;
       if (it < items) {
         int t = w.cav[it / 6], e = it % 6;
-        int4 v = m.T[t].v;
+        int4 v = m.T[CKI(t, m.capT)].v;
         if (edge_bit(v, e)) {
           int u = vid(geti(v, edge_i(e))), x = vid(geti(v, edge_j(e)));
           bool split = sa >= 0 && ((u == sa && x == sb) || (u == sb && x == sa));
@@ -1250,8 +1290,8 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
               int g = hash_lookup(m, ekey(u, x));
               if (g >= 0) {
                 flag = true;
-                un = (m.Gflag[g] & F_UNSPL) != 0;
-                m.Gmust[g] = 1;
+                un = (m.Gflag[CKI(g, m.capG)] & F_UNSPL) != 0;
+                m.Gmust[CKI(g, m.capG)] = 1;
                 if (r.candG && !r.candG[g]) atomicAdd(&r.stats[ST_NEWCAND], 1ULL);
               }
             }
@@ -1270,14 +1310,14 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   // ------------------------------------------------ priority marks
   {
     const unsigned long long mk = (r.epoch << 32) | (unsigned long long)(unsigned)i;
-    for (int k = lane; k < ncav; k += 32) atomicMin(&m.Tmark[w.cav[k]], mk);
+    for (int k = lane; k < ncav; k += 32) atomicMin(&m.Tmark[CKI(w.cav[k], m.capT)], mk);
     for (int k = lane; k < nbnd; k += 32)
-      if (w.bout[k] >= 0) atomicMin(&m.Tmark[w.bout[k] >> 2], mk);
-    for (int k = lane; k < nf; k += 32) atomicMin(&m.Smark[w.fcav[k]], mk);
+      if (w.bout[k] >= 0) atomicMin(&m.Tmark[CKI(w.bout[k] >> 2, m.capT)], mk);
+    for (int k = lane; k < nf; k += 32) atomicMin(&m.Smark[CKI(w.fcav[k], m.capS)], mk);
     for (int k = lane; k < nfb; k += 32) {
       int sk = w.fbnd[k];
       int nb = sn_ptr(m, sk >> 2)[sk & 3];
-      if (nb >= 0) atomicMin(&m.Smark[nb], mk);
+      if (nb >= 0) atomicMin(&m.Smark[CKI(nb, m.capS)], mk);
     }
   }
 
@@ -1367,6 +1407,8 @@ __global__ void k_grow2(DevMesh m, DevRound r) {
   int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int nw = gridDim.x * (blockDim.x >> 5);
   using L = SlabLayout<Tier2>;
+  if (warp >= r.nws2) return;  // no workspace for this warp
+  nw = min(nw, r.nws2);
   int* extra = r.ws2 + (size_t)warp * kWs2Extra;
   for (int j = warp; j < r.n2; j += nw) {
     int i = r.list2[j];
@@ -1405,16 +1447,16 @@ __global__ void k_select(DevMesh m, DevRound r) {
     if (outcome == OUT_OK) {
       const unsigned long long mk = (r.epoch << 32) | (unsigned long long)(unsigned)i;
       bool lost = false;
-      for (int k = lane; k < ncav; k += 32) lost |= m.Tmark[slab[offC + k]] != mk;
+      for (int k = lane; k < ncav; k += 32) lost |= m.Tmark[CKI(slab[offC + k], m.capT)] != mk;
       for (int k = lane; k < nbnd; k += 32) {
         int b = slab[offBO + k];
-        if (b >= 0) lost |= m.Tmark[b >> 2] != mk;
+        if (b >= 0) lost |= m.Tmark[CKI(b >> 2, m.capT)] != mk;
       }
-      for (int k = lane; k < nf; k += 32) lost |= m.Smark[slab[offF + k]] != mk;
+      for (int k = lane; k < nf; k += 32) lost |= m.Smark[CKI(slab[offF + k], m.capS)] != mk;
       for (int k = lane; k < nfb; k += 32) {
         int sk = slab[offFB + k];
         int nb = sn_ptr(m, sk >> 2)[sk & 3];
-        if (nb >= 0) lost |= m.Smark[nb] != mk;
+        if (nb >= 0) lost |= m.Smark[CKI(nb, m.capS)] != mk;
       }
       surv = !__any_sync(FULLMASK, lost);
     }
@@ -1425,9 +1467,9 @@ __global__ void k_select(DevMesh m, DevRound r) {
       r.counts[i] = c;
       int e = r.cand[i];
       if (outcome == OUT_UNSPL) {
-        if (r.cls == CLS_SUBSEG) m.Gflag[e] |= F_UNSPL;
-        else if (r.cls == CLS_SUBFACE) m.Sflag[e] |= F_UNSPL;
-        else if (r.cls == CLS_TET) m.Tflag[e] |= F_UNSPL;
+        if (r.cls == CLS_SUBSEG) m.Gflag[CKI(e, m.capG)] |= F_UNSPL;
+        else if (r.cls == CLS_SUBFACE) m.Sflag[CKI(e, m.capS)] |= F_UNSPL;
+        else if (r.cls == CLS_TET) m.Tflag[CKI(e, m.capT)] |= F_UNSPL;
         else r.point_state[e] = 2;
       }
       if (outcome == OUT_OK) atomicAdd(&r.stats[surv ? ST_SURV : ST_OK], 1ULL);
@@ -1466,11 +1508,11 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
     const int s0 = m.nS + off.z;
     int sa = -1, sb = -1;
     if (r.cls == CLS_SUBSEG) {
-      int4 G = m.GV[e];
+      int4 G = m.GV[CKI(e, m.capG)];
       sa = G.x;
       sb = G.y;
     }
-    if (lane == 0 && r.cls != CLS_POINT) m.V[vp] = r.sp[i];
+    if (lane == 0 && r.cls != CLS_POINT) m.V[CKI(vp, m.capV)] = r.sp[i];
     if (lane == 0) atomicAdd(&r.stats[ST_NEWT], (unsigned long long)nbnd);
     // step 1: new tetrahedra (p replaces the vertex opposite each boundary face)
     for (int j = lane; j < nbnd; j += 32) {
@@ -1494,19 +1536,21 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       TetRec N;
       N.v = nv;
       N.n = make_int4(-1, -1, -1, -1);
+      CKL(bout[j], m.nT);
+      CKI(t, m.nT);
       seti(N.n, f, bout[j]);
-      m.T[nid] = N;
+      m.T[CKI(nid, m.capT)] = N;
       int4 ts = make_int4(-1, -1, -1, -1);
       if (face_sub(R.v, f)) {
         int s = ts_ptr(m, t)[f];
         seti(ts, f, s);
-        if (s >= 0 && s < m.nS) m.SN[s].w = (nid << 2) | f;
+        if (s >= 0 && s < m.nS) m.SN[CKI(s, m.capS)].w = (nid << 2) | f;
         else atomicAdd(&r.stats[ST_ITER], 1ULL);
       }
-      m.TS[nid] = ts;
-      m.Tmark[nid] = ~0ULL;
-      m.Tseed[nid] = ~0ULL;
-      m.Tfwd[nid] = -1;
+      m.TS[CKI(nid, m.capT)] = ts;
+      m.Tmark[CKI(nid, m.capT)] = ~0ULL;
+      m.Tseed[CKI(nid, m.capT)] = ~0ULL;
+      m.Tfwd[CKI(nid, m.capT)] = -1;
       if (bout[j] >= 0) tet_n_ptr(m, bout[j] >> 2)[bout[j] & 3] = (nid << 2) | f;
     }
     __syncwarp();
@@ -1538,6 +1582,8 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
           break;
         }
       }
+      CKL(link, m.nT + 0x7fffffff / 8);
+      if (link >= 0 && (link >> 2) < t0) CKL(link, 0);  // must point into this star
       if (g >= 0) tet_n_ptr(m, t0 + j)[g] = link;
       else atomicAdd(&r.stats[ST_ITER], 1ULL);
     }
@@ -1547,8 +1593,8 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       int s = fbnd[k] >> 2, ke = fbnd[k] & 3;
       int u = fbv[3 * k], x = fbv[3 * k + 1], fid = fbv[3 * k + 2];
       int ns = s0 + k;
-      m.SV[ns] = make_int4(vp, u, x, fid);
-      int outer = geti(m.SN[s], ke);
+      m.SV[CKI(ns, m.capS)] = make_int4(vp, u, x, fid);
+      int outer = geti(m.SN[CKI(s, m.capS)], ke);
       int4 sn = make_int4(outer, -1, -1, -1);
       if (outer >= 0) {
         int* o = sn_ptr(m, outer);
@@ -1587,19 +1633,19 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
         if (tw < 0) tw = (nid << 2) | g;
       }
       sn.w = tw;
-      m.SN[ns] = sn;
-      m.Sflag[ns] = 0;
-      m.Smust[ns] = 0;
-      m.Smark[ns] = ~0ULL;
+      m.SN[CKI(ns, m.capS)] = sn;
+      m.Sflag[CKI(ns, m.capS)] = 0;
+      m.Smust[CKI(ns, m.capS)] = 0;
+      m.Smark[CKI(ns, m.capS)] = ~0ULL;
     }
     __syncwarp();
     // step 4: retire the cavity and the facet part
     for (int k = lane; k < ncav; k += 32) {
       int t = cav[k];
-      m.Tflag[t] |= F_DEAD;
-      m.Tfwd[t] = t0;
+      m.Tflag[CKI(t, m.capT)] |= F_DEAD;
+      m.Tfwd[CKI(t, m.capT)] = t0;
     }
-    for (int k = lane; k < nf; k += 32) m.Sflag[fcav[k]] |= F_DEAD;
+    for (int k = lane; k < nf; k += 32) m.Sflag[CKI(fcav[k], m.capS)] |= F_DEAD;
     // step 5: the split subsegment becomes (a, p) and (p, b)
     if (r.cls == CLS_SUBSEG) {
       int ta = -1, tb = -1;
@@ -1613,14 +1659,14 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
         tb = max(tb, __shfl_xor_sync(FULLMASK, tb, o));
       }
       if (lane == 0) {
-        int4 G = m.GV[e];
+        int4 G = m.GV[CKI(e, m.capG)];
         int g2 = m.nG + off.w;
-        m.GV[e] = make_int4(G.x, vp, G.z, ta);
-        m.GV[g2] = make_int4(vp, G.y, G.z, tb);
-        m.Gflag[e] = 0;
-        m.Gmust[e] = 0;
-        m.Gflag[g2] = 0;
-        m.Gmust[g2] = 0;
+        m.GV[CKI(e, m.capG)] = make_int4(G.x, vp, G.z, ta);
+        m.GV[CKI(g2, m.capG)] = make_int4(vp, G.y, G.z, tb);
+        m.Gflag[CKI(e, m.capG)] = 0;
+        m.Gmust[CKI(e, m.capG)] = 0;
+        m.Gflag[CKI(g2, m.capG)] = 0;
+        m.Gmust[CKI(g2, m.capG)] = 0;
         hash_insert(m, ekey(G.x, vp), e);
         hash_insert(m, ekey(vp, G.y), g2);
       }
@@ -1629,18 +1675,18 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
     // step 6: subsegment tet references and quality of the new tetrahedra
     for (int j = lane; j < nbnd; j += 32) {
       int nid = t0 + j;
-      int4 v = m.T[nid].v;
+      int4 v = m.T[CKI(nid, m.capT)].v;
       for (int ed = 0; ed < 6; ++ed) {
         if (!edge_bit(v, ed)) continue;
         int a = vid(geti(v, edge_i(ed))), b = vid(geti(v, edge_j(ed)));
         if (a == vp || b == vp) continue;
         int g = hash_lookup(m, ekey(a, b));
-        if (g >= 0) m.GV[g].w = nid;
+        if (g >= 0) m.GV[CKI(g, m.capG)].w = nid;
       }
       int s4[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
       sort4(s4);
       bool bad = tet_bad_fixed(vtx(m, s4[0]), vtx(m, s4[1]), vtx(m, s4[2]), vtx(m, s4[3]), r.B);
-      m.Tflag[nid] = bad ? F_BAD : 0;
+      m.Tflag[CKI(nid, m.capT)] = bad ? F_BAD : 0;
     }
     if (lane == 0 && r.cls == CLS_POINT) {
       r.point_state[e] = 1;
@@ -1654,35 +1700,35 @@ __global__ void k_follow_fwd(DevMesh m, int* hint, const int* state, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (state[i] != 0) continue;
     int t = hint[i];
-    for (int it = 0; it < 1 << 20 && (m.Tflag[t] & F_DEAD); ++it) t = m.Tfwd[t];
+    for (int it = 0; it < 1 << 20 && (m.Tflag[CKI(t, m.capT)] & F_DEAD); ++it) t = m.Tfwd[CKI(t, m.capT)];
     hint[i] = t;
   }
 }
 
 __global__ void k_compact_flags(DevMesh m, int* alive) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x)
-    alive[t] = (m.Tflag[t] & F_DEAD) ? 0 : 1;
+    alive[t] = (m.Tflag[CKI(t, m.capT)] & F_DEAD) ? 0 : 1;
 }
 // newid = exclusive scan of alive; move live tets to T2 with remapped links
 __global__ void k_compact_move(DevMesh m, const int* newid, TetRec* T2, int4* TS2,
                                unsigned char* F2) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x) {
-    if (m.Tflag[t] & F_DEAD) continue;
-    TetRec R = m.T[t];
+    if (m.Tflag[CKI(t, m.capT)] & F_DEAD) continue;
+    TetRec R = m.T[CKI(t, m.capT)];
     for (int f = 0; f < 4; ++f) {
       int nb = geti(R.n, f);
       if (nb >= 0) seti(R.n, f, (newid[nb >> 2] << 2) | (nb & 3));
     }
     int d = newid[t];
     T2[d] = R;
-    TS2[d] = m.TS[t];
-    F2[d] = m.Tflag[t];
+    TS2[d] = m.TS[CKI(t, m.capT)];
+    F2[d] = m.Tflag[CKI(t, m.capT)];
   }
 }
 __global__ void k_compact_hints(DevMesh m, const int* newid, int* hint, int nh) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nh; i += gridDim.x * blockDim.x) {
     int t = hint[i];
-    for (int it = 0; it < 1 << 20 && (m.Tflag[t] & F_DEAD); ++it) t = m.Tfwd[t];
+    for (int it = 0; it < 1 << 20 && (m.Tflag[CKI(t, m.capT)] & F_DEAD); ++it) t = m.Tfwd[CKI(t, m.capT)];
     hint[i] = newid[t];
   }
 }
@@ -1690,13 +1736,13 @@ __global__ void k_compact_fix(DevMesh m, const int* newid) {
   int n = m.nS + m.nG;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < m.nS) {
-      if (m.Sflag[i] & F_DEAD) continue;
-      int w = m.SN[i].w;
-      m.SN[i].w = (newid[w >> 2] << 2) | (w & 3);
+      if (m.Sflag[CKI(i, m.capS)] & F_DEAD) continue;
+      int w = m.SN[CKI(i, m.capS)].w;
+      m.SN[CKI(i, m.capS)].w = (newid[w >> 2] << 2) | (w & 3);
     } else {
       int g = i - m.nS;
-      if (m.Gflag[g] & F_DEAD) continue;
-      m.GV[g].w = newid[m.GV[g].w];
+      if (m.Gflag[CKI(g, m.capG)] & F_DEAD) continue;
+      m.GV[CKI(g, m.capG)].w = newid[m.GV[CKI(g, m.capG)].w];
     }
   }
 }
@@ -1708,27 +1754,27 @@ __global__ void k_live_flags(const unsigned char* flag, int n, int* out) {
 }
 __global__ void k_gather_tets(DevMesh m, const int* pos, int4* out, unsigned char* oflag) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x) {
-    if (m.Tflag[t] & F_DEAD) continue;
-    int4 v = m.T[t].v;
+    if (m.Tflag[CKI(t, m.capT)] & F_DEAD) continue;
+    int4 v = m.T[CKI(t, m.capT)].v;
     int d = pos[t];
     out[d] = make_int4(vid(v.x), vid(v.y), vid(v.z), vid(v.w));
-    oflag[d] = (m.Tflag[t] & F_UNSPL) ? 2 : 0;
+    oflag[d] = (m.Tflag[CKI(t, m.capT)] & F_UNSPL) ? 2 : 0;
   }
 }
 __global__ void k_gather_subfaces(DevMesh m, const int* pos, int4* out, unsigned char* oflag) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m.nS; s += gridDim.x * blockDim.x) {
-    if (m.Sflag[s] & F_DEAD) continue;
+    if (m.Sflag[CKI(s, m.capS)] & F_DEAD) continue;
     int d = pos[s];
-    out[d] = m.SV[s];
-    oflag[d] = (m.Smust[s] ? 1 : 0) | ((m.Sflag[s] & F_UNSPL) ? 2 : 0);
+    out[d] = m.SV[CKI(s, m.capS)];
+    oflag[d] = (m.Smust[CKI(s, m.capS)] ? 1 : 0) | ((m.Sflag[CKI(s, m.capS)] & F_UNSPL) ? 2 : 0);
   }
 }
 __global__ void k_gather_subsegs(DevMesh m, const int* pos, int4* out, unsigned char* oflag) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < m.nG; g += gridDim.x * blockDim.x) {
-    if (m.Gflag[g] & F_DEAD) continue;
+    if (m.Gflag[CKI(g, m.capG)] & F_DEAD) continue;
     int d = pos[g];
-    out[d] = m.GV[g];
-    oflag[d] = (m.Gmust[g] ? 1 : 0) | ((m.Gflag[g] & F_UNSPL) ? 2 : 0);
+    out[d] = m.GV[CKI(g, m.capG)];
+    oflag[d] = (m.Gmust[CKI(g, m.capG)] ? 1 : 0) | ((m.Gflag[CKI(g, m.capG)] & F_UNSPL) ? 2 : 0);
   }
 }
 // cavity tets of each reported candidate as sorted vertex ids
@@ -1739,7 +1785,7 @@ __global__ void k_report_cav(DevMesh m, DevRound r, const int* offs, int4* out) 
     int n = offs[i + 1] - offs[i];
     const int* cav = slab + (t2 ? SlabLayout<Tier2>::OFF_CAV : SlabLayout<Tier1>::OFF_CAV);
     for (int k = 0; k < n; ++k) {
-      int4 v = m.T[cav[k]].v;
+      int4 v = m.T[CKI(cav[k], m.capT)].v;
       int s[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
       sort4(s);
       out[offs[i] + k] = make_int4(s[0], s[1], s[2], s[3]);
@@ -1829,8 +1875,8 @@ void launch_grow1(const DevMesh& m, const DevRound& r, cudaStream_t s) {
   k_grow1<<<(int)blocks, 32 * kWarps1, smem, s>>>(m, r);
 }
 void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s) {
-  if (r.n2 <= 0) return;
-  int blocks = (nwarps + 1) / 2;
+  if (r.n2 <= 0 || r.nws2 <= 0) return;
+  int blocks = (min(nwarps, r.nws2) + 1) / 2;  // two warps per block
   k_grow2<<<blocks, 64, 0, s>>>(m, r);
 }
 void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s) {
@@ -1921,11 +1967,26 @@ __global__ void k_stall(DevMesh m, DevRound r) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
     if ((r.status[i] & 0xff) != OUT_REJECT) continue;
     r.status[i] = OUT_UNSPL | (RS_STRUCT << 8);
-    m.Gflag[r.cand[i]] |= F_UNSPL;
+    m.Gflag[CKI(r.cand[i], m.capG)] |= F_UNSPL;
   }
 }
 void launch_stall(const DevMesh& m, const DevRound& r, cudaStream_t s) {
   if (r.n > 0) k_stall<<<grid_for(r.n, 256), 256, 0, s>>>(m, r);
+}
+
+// checked build: first out-of-bounds index seen (site line, index, bound), or 0
+int checked_error(int* info, cudaStream_t s) {
+#ifdef CDR_CHECKED
+  int v[4] = {0, 0, 0, 0};
+  cudaMemcpyFromSymbolAsync(v, g_chk, sizeof(v), 0, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  for (int k = 0; k < 4; ++k) info[k] = v[k];
+  return v[0];
+#else
+  (void)s;
+  info[0] = info[1] = info[2] = info[3] = 0;
+  return 0;
+#endif
 }
 
 int exact_overflow_flag(cudaStream_t s, bool reset) {

@@ -64,5 +64,6 @@ void launch_report_cav(const DevMesh& m, const DevRound& r, const int* offs, int
 
 void launch_eval_pred(int kind, const double* in, int n, int* sign, double* outp, cudaStream_t s);
 int exact_overflow_flag(cudaStream_t s, bool reset);
+int checked_error(int* info, cudaStream_t s);
 
 }  // namespace cdr

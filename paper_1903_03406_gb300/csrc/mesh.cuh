@@ -90,6 +90,7 @@ struct DevMesh {
   int* HV;
   int hmask;
   int nV, nT, nS, nG, nF;
+  int capV, capT, capS, capG;  // allocated sizes (bounds of the checked build)
   double guard2;
   int walk_limit;
 };
@@ -134,6 +135,7 @@ struct DevRound {
   int* slab2;                  // tier-2 slabs (n2 * STRIDE2)
   int* slab2_of;               // candidate -> tier-2 slab index (-1)
   int* ws2;                    // tier-2 workspaces (per warp)
+  int nws2;                    // tier-2 workspaces allocated
   int n2;                      // tier-2 candidates
   const int* list2;            // tier-2 candidate indices
   int* survived;
