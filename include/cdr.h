@@ -48,7 +48,8 @@ enum {
   CDR_ERR_OOM = -2,           /* the allocator returned NULL                      */
   CDR_ERR_CUDA = -3,          /* a CUDA call failed                               */
   CDR_ERR_ITER_LIMIT = -4,    /* a bounded device loop gave up                    */
-  CDR_ERR_INTERNAL = -5       /* exact-arithmetic capacity or an invariant failed */
+  CDR_ERR_INTERNAL = -5,      /* exact-arithmetic capacity or an invariant failed */
+  CDR_ERR_TOO_LARGE = -6      /* more items than a fixed-capacity call can hold   */
 };
 
 typedef struct cdr_handle cdr_handle;
@@ -234,6 +235,36 @@ int cdr_device_arch(void);
  * CDR_ERR_INTERNAL if the exact arithmetic ran out of capacity. */
 int cdr_eval_predicates(int32_t kind, const double* in, int32_t n, int32_t* sign, double* out,
                         void* stream);
+
+/* Largest batch cdr_eval_predicates_noalloc accepts. */
+#define CDR_EVAL_NOALLOC_MAX_ITEMS 16384
+
+/* cdr_eval_predicates without device allocation. The paper has no counterpart:
+ * this is a convenience for callers that cannot allocate device memory. Two
+ * kinds of caller cannot: one that keeps kernels running on other streams
+ * (cudaFree waits for the whole device, so each call would stall that work),
+ * and one whose device memory is held by a caching allocator such as
+ * PyTorch's (cudaMalloc can fail while the memory sits reserved in the cache).
+ *
+ * Arguments, results, layout and error codes are those of cdr_eval_predicates.
+ * The device copies of in, sign and out live in one fixed array in the
+ * library's device image (2.44 MiB, present on every GPU that loads the
+ * library until the process exits), so:
+ *   - n > CDR_EVAL_NOALLOC_MAX_ITEMS returns CDR_ERR_TOO_LARGE and does nothing;
+ *   - no call allocates or frees device memory (cudaMalloc, cudaFree or any
+ *     allocating library routine);
+ *   - the first call on a device, with that device current, looks the array
+ *     up (cudaGetSymbolAddress) and caches its address. Make that first call
+ *     before any stream capture;
+ *   - every call on a device shares the array. Calls whose device work
+ *     overlaps (other streams, other host threads) race on it and their results
+ *     are undefined: serialise them. Each call synchronises `stream` before it
+ *     returns, so calls from one host thread never overlap.
+ * The array keeps the last call's contents; each call clears what must start
+ * at zero (the exact-arithmetic overflow flag) and writes every output slot
+ * it reads back. */
+int cdr_eval_predicates_noalloc(int32_t kind, const double* in, int32_t n, int32_t* sign,
+                                double* out, void* stream);
 
 #ifdef __cplusplus
 }

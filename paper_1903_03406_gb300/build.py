@@ -1,7 +1,7 @@
 """Build the CUDA library in place: paper_1903_03406_gb300/libcdr.so (sm_103a).
 
-Two translation units (the kernels and the host driver) compile in parallel with
-nvcc; host code is compiled without floating-point contraction so that the
+The translation units (the kernels, the host driver and the no-allocation
+predicate entry point) compile in parallel with nvcc; host code is compiled without floating-point contraction so that the
 host-side FP64 set-up (facet reference points, the shortest-edge guard) rounds
 exactly as written.
 """
@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcdr.so")
-SOURCES = ["kernels.cu", "api.cu"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
 HEADERS = ["kernels.cuh", "mesh.cuh", "predicates.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

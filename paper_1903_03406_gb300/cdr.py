@@ -120,6 +120,7 @@ def lib():
             L.cdr_eval_predicates.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                               ctypes.c_int32, i32p,
                                               ctypes.POINTER(ctypes.c_double), P]
+            L.cdr_eval_predicates_noalloc.argtypes = L.cdr_eval_predicates.argtypes
             _lib = L
     return _lib
 
@@ -335,4 +336,34 @@ def eval_predicates(kind, items, stream=None):
     _check(lib().cdr_eval_predicates(k, _p(items, ctypes.c_double), n, _p(sign, ctypes.c_int32),
                                      _p(out, ctypes.c_double), _stream_handle(stream)),
            "cdr_eval_predicates")
+    return sign, out
+
+
+# largest batch of eval_predicates_noalloc (CDR_EVAL_NOALLOC_MAX_ITEMS in cdr.h)
+EVAL_NOALLOC_MAX_ITEMS = 16384
+
+
+def eval_predicates_noalloc(kind, items, stream=None):
+    """eval_predicates without device allocation (cdr_eval_predicates_noalloc).
+
+    For callers that cannot allocate device memory: code that keeps kernels
+    running on other streams (cudaFree would wait for the whole device) and
+    processes whose device memory is held by a caching allocator (cudaMalloc can
+    fail there). The device copies live in a fixed array of the library, so at
+    most EVAL_NOALLOC_MAX_ITEMS items go in one call, and calls whose device work
+    overlaps (other streams or threads) race. The first call on a device looks
+    that array up; make it before any stream capture. Host buffers only (numpy).
+    """
+    items = np.ascontiguousarray(items, dtype=np.float64).reshape(-1, 16)
+    n = len(items)
+    sign = np.zeros(n, dtype=np.int32)
+    out = np.zeros((n, 3))
+    k = PRED[kind] if isinstance(kind, str) else int(kind)
+    st = lib().cdr_eval_predicates_noalloc(k, _p(items, ctypes.c_double), n,
+                                           _p(sign, ctypes.c_int32), _p(out, ctypes.c_double),
+                                           _stream_handle(stream))
+    if st == -6:
+        raise CdrError(st, "cdr_eval_predicates_noalloc: %d items, at most %d fit its fixed "
+                       "device scratch" % (n, EVAL_NOALLOC_MAX_ITEMS))
+    _check(st, "cdr_eval_predicates_noalloc")
     return sign, out

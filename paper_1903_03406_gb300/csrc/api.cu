@@ -783,6 +783,7 @@ const char* cdr_status_string(int s) {
     case CDR_ERR_CUDA: return "CUDA error";
     case CDR_ERR_ITER_LIMIT: return "a bounded device loop gave up";
     case CDR_ERR_INTERNAL: return "internal error (exact-arithmetic capacity or invariant)";
+    case CDR_ERR_TOO_LARGE: return "more items than the fixed scratch of a no-allocation call holds";
   }
   return "unknown status";
 }
