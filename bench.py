@@ -116,13 +116,15 @@ def make_workload(name, rank, cdr, stream):
     """Points, the GPU-built initial Delaunay mesh and constraint labels."""
     from paper_1903_03406_gb300 import inputs
     w = WORKLOADS[name]
-    pts, _, _ = inputs.box_points(w["kind"], w["n"], w["seed"] + 1000 * rank)
+    from paper_1903_03406_gb300 import replicas
+    seed = replicas.instance_seed(w["seed"], rank)
+    pts, _, _ = inputs.box_points(w["kind"], w["n"], seed)
     log("building the initial Delaunay mesh on the GPU (%d points)" % len(pts))
     dt = cdr.Handle.delaunay_box(pts, stream=stream)
     log("delaunay: %d rounds, %d skipped" % (dt.dt_rounds, dt.skipped))
     ex = dt.export()
     dt.close()
-    plc = inputs.plc_from_delaunay(pts, ex["tets"], w["n_seg"], w["n_tri"], w["seed"] + 1000 * rank)
+    plc = inputs.plc_from_delaunay(pts, ex["tets"], w["n_seg"], w["n_tri"], seed)
     return pts, ex, plc
 
 
@@ -241,18 +243,10 @@ def gpu_arm(args, rank, world):
         he.close()
     t_e2e = time.perf_counter() - t0
 
-    # max over ranks of the time, sum of the work
-    tot = torch.tensor([total_ms, float(inserted), t_e2e, float(ins_e2e)], dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        mx = tot.clone().cuda()
-        sm = tot.clone().cuda()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms_max, ins_sum = float(mx[0]), float(sm[1])
-        e2e_max, e2e_ins = float(mx[2]), float(sm[3])
-    else:
-        total_ms_max, ins_sum, e2e_max, e2e_ins = total_ms, float(inserted), t_e2e, float(ins_e2e)
+    # max over ranks of the time, sum of the work (independent instances)
+    from paper_1903_03406_gb300 import replicas
+    (total_ms_max, e2e_max), (ins_sum, e2e_ins) = replicas.reduce_measurement(
+        [total_ms, t_e2e], [inserted, ins_e2e], world, device="cuda")
     if rank != 0:
         return None
 
@@ -272,12 +266,9 @@ def gpu_arm(args, rank, world):
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "points": w["n"] + 8, "segments": w["n_seg"],
-                   "triangles": w["n_tri"], "B": B, "parallelism": "instance-sharded x%d" % world,
-                   "l2": "flushed between steps (256 MB write)",
-                   "steiner_per_step": last["steiner_inserted"], "rounds_per_step": last["rounds"],
-                   "final_tets": last["n_tets"], "bad_left": last["n_bad_left"],
-                   "wall_s": t_wall},
+        "config": dict(workload_config(args, world), l2="flushed between steps (256 MB write)",
+                       steiner_per_step=last["steiner_inserted"], rounds_per_step=last["rounds"],
+                       final_tets=last["n_tets"], bad_left=last["n_bad_left"], wall_s=t_wall),
         "e2e": {"value": e2e_ins / e2e_max, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": {"kernel": "k_grow1 (region growth, tier 1)", "bound": "hbm",
@@ -293,6 +284,14 @@ def gpu_arm(args, rank, world):
         "clocks": clk,
     }
     return line
+
+
+def workload_config(args, world):
+    """The workload named in both arms' JSON lines."""
+    w = WORKLOADS[args.workload]
+    return {"workload": args.workload, "points": w["n"] + 8, "segments": w["n_seg"],
+            "triangles": w["n_tri"], "B": w["B"],
+            "parallelism": "independent instances x%d (replicas)" % world}
 
 
 # ---------------------------------------------------------- CPU (oracle) arm
@@ -345,8 +344,7 @@ def reference_arm(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "points": w["n"] + 8, "segments": w["n_seg"],
-                   "triangles": w["n_tri"], "B": w["B"]},
+        "config": workload_config(args, world),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "sequential refinement, %.0f s of insertions per step" %
                                    args.ref_seconds},
@@ -369,23 +367,26 @@ def main():
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        # the oracle on the host cores: rank 0 alone runs it, the others exit
+        line = reference_arm(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    if args.impl == "reference":
-        line = reference_arm(args, rank, world)
-    else:
-        line = gpu_arm(args, rank, world)
-        if line is not None and world == 1 and not args.no_cpu_baseline:
-            log("cpu baseline: building the oracle's Delaunay mesh")
-            om, _, _ = oracle_workload(args.workload)
-            ins, t = cpu_sample(om, WORKLOADS[args.workload]["B"], args.cpu_seconds)
-            line["cpu_baseline"] = {
-                "value": ins / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": "sequential refinement of the same workload for %.1f s "
-                          "(%d insertions, initial Delaunay excluded)" % (t, ins)}
+    line = gpu_arm(args, rank, world)
+    if line is not None and world == 1 and not args.no_cpu_baseline:
+        log("cpu baseline: building the oracle's Delaunay mesh")
+        om, _, _ = oracle_workload(args.workload)
+        ins, t = cpu_sample(om, WORKLOADS[args.workload]["B"], args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": ins / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "sequential refinement of the same workload for %.1f s "
+                      "(%d insertions, initial Delaunay excluded)" % (t, ins)}
     if line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:
