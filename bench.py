@@ -12,6 +12,19 @@ on the GPU by the library's point-insertion rounds (untimed set-up).
 --impl reference times the CPU oracle (sequential refinement) on the same
 workload, a bounded number of insertions per step, on the host cores.
 
+Two more workloads print their own line:
+* --workload batched64: 64 independent unit-cube PLCs (1k-50k interior points,
+  log-uniform; 1% segments and 1% triangles; B = 1.6) refined one after another
+  (create, refine, export each) and as one batch (add all, refine, export all):
+  meshes/s of both;
+* --workload served40: a Poisson stream of 40 requests (unit-cube PLCs with
+  2k-200k points, B drawn from {1.4, 1.6, 2.0}) served by continuous batching
+  under a 120 GB budget at 0.8x the throughput of a closed-loop warm-up: p50 /
+  p99 latency (arrival to export) and meshes/s.
+Their instance and request counts are bounded samples of the 256-instance and
+2,000-request streams, so that each run stays near a minute; the initial
+Delaunay meshes are built on the GPU before the timed region.
+
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -35,6 +48,10 @@ WORKLOADS = {
     "uniform100k": dict(kind="uniform", n=100_000, seed=1, B=1.4, n_seg=1000, n_tri=1000),
     "cube2k": dict(kind="cube", n=2000, seed=0, B=2.0, n_seg=0, n_tri=0),
     "clustered500k": dict(kind="clustered", n=500_000, seed=2, B=1.4, n_seg=5000, n_tri=5000),
+}
+MULTI = {
+    "batched64": dict(count=64, nmin=1000, nmax=50000, B=(1.6,), seed=1000),
+    "served40": dict(count=40, nmin=2000, nmax=200000, B=(1.4, 1.6, 2.0), seed=10 ** 6),
 }
 METRIC = "Steiner pts inserted/s on 1 GB300"
 UNIT = "Steiner points/s"
@@ -286,6 +303,144 @@ def gpu_arm(args, rank, world):
     return line
 
 
+# ------------------------------------------------- batched and served arms
+def multi_instances(spec, rank, cdr, stream):
+    """Seeded unit-cube PLCs with log-uniform sizes; initial meshes built on the GPU."""
+    from paper_1903_03406_gb300 import inputs, replicas
+    seed = replicas.instance_seed(spec["seed"], rank)
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(spec["count"]):
+        n = int(round(np.exp(rng.uniform(np.log(spec["nmin"]), np.log(spec["nmax"])))))
+        B = float(spec["B"][rng.integers(len(spec["B"]))])
+        pts, _, _ = inputs.box_points("cube", n, seed * 1000 + i)
+        dt = cdr.Handle.delaunay_box(pts, stream=stream)
+        ex = dt.export()
+        dt.close()
+        k = max(1, n // 100)
+        plc = inputs.plc_from_delaunay(pts, ex["tets"], k, k, seed * 1000 + i)
+        out.append(dict(B=B, n=n, mesh=dict(xyz=ex["xyz"], tets=ex["tets"], segs=plc["segs"],
+                                            seg_id=plc["seg_id"], tris=plc["tris"],
+                                            facet_id=plc["facet_id"], nfacets=plc["nfacets"])))
+    return out
+
+
+def _margs(m):
+    return (m["xyz"], m["tets"], m["segs"], m["seg_id"], m["tris"], m["facet_id"], m["nfacets"])
+
+
+def multi_arm(args, rank, world):
+    import torch
+    from paper_1903_03406_gb300 import cdr, replicas, serve
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    cdr.lib()
+    stream = torch.cuda.current_stream()
+    spec = MULTI[args.workload]
+    t0 = time.perf_counter()
+    insts = multi_instances(spec, rank, cdr, stream)
+    log("%d instances ready in %.1fs (%d points)" % (len(insts), time.perf_counter() - t0,
+                                                     sum(x["n"] for x in insts)))
+    al = cdr.TorchAllocator()
+    clocks = ClockSampler(dev)
+    if args.workload.startswith("batched"):
+        # warm-up: one small batch and one small instance alone
+        for _ in range(max(1, args.warmup)):
+            b = cdr.Batch(allocator=al, stream=stream)
+            b.add(insts[0]["B"], *_margs(insts[0]["mesh"]))
+            b.refine()
+            b.close()
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = time.perf_counter()
+        serial_ins = []
+        for x in insts:
+            h = cdr.Handle.create(*_margs(x["mesh"]), allocator=al, stream=stream)
+            st = h.refine(x["B"])
+            h.export()
+            serial_ins.append(st["steiner_inserted"])
+            h.close()
+        torch.cuda.synchronize()
+        t_serial = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        b = cdr.Batch(allocator=al, stream=stream)
+        slots = [b.add(x["B"], *_margs(x["mesh"])) for x in insts]
+        rounds = b.refine()
+        batch_ins = []
+        for k in slots:
+            batch_ins.append(b.stats(k)["steiner_inserted"])
+            b.export(k)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        b.close()
+        clk = clocks.stop()
+        (t_s, t_b), (ins_s, ins_b) = replicas.reduce_measurement(
+            [t_serial, t_batch], [sum(serial_ins), sum(batch_ins)], world, device="cuda")
+        if rank != 0:
+            return None
+        n_all = len(insts) * world
+        return {
+            "metric": "batched vs serial meshes/s", "value": n_all / t_b, "unit": "meshes/s",
+            "serial": {"value": n_all / t_s, "unit": "meshes/s", "steiner_per_s": ins_s / t_s},
+            "batched": {"value": n_all / t_b, "unit": "meshes/s", "steiner_per_s": ins_b / t_b,
+                        "rounds": rounds},
+            "same_counts": serial_ins == batch_ins, "n_gpus": world, "steps": 1,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "instances": len(insts),
+                       "points": [x["n"] for x in insts][:8] + ["..."],
+                       "points_total": sum(x["n"] for x in insts), "B": spec["B"],
+                       "constraints": "1% segments + 1% triangles",
+                       "timed": "create/add + refine + export of every instance",
+                       "sample": "64 of config 4's 256 instances"},
+            "clocks": clk,
+        }
+    # served: closed-loop warm-up on the first requests, then a Poisson stream
+    budget = 120 * 10 ** 9
+    reqs = [serve.Request(i, 0.0, x["B"], x["mesh"]) for i, x in enumerate(insts)]
+    nw = min(8, len(reqs))
+    b = cdr.Batch(allocator=al, stream=stream)
+    srv = serve.Server(b, budget_bytes=budget)
+    t0 = time.perf_counter()
+    for r in reqs[:nw]:
+        srv.submit(serve.Request(r.rid, t0, r.B, r.mesh))
+    srv.run()
+    torch.cuda.synchronize()
+    closed = nw / (time.perf_counter() - t0)
+    b.close()
+    rate = 0.8 * closed
+    b = cdr.Batch(allocator=al, stream=stream)
+    srv = serve.Server(b, budget_bytes=budget)
+    clocks.start()
+    t0 = time.perf_counter()
+    arr = serve.poisson_arrivals(len(reqs), rate, seed=spec["seed"] + rank, t0=t0)
+    for r, a in zip(reqs, arr):
+        srv.submit(serve.Request(r.rid, float(a), r.B, r.mesh))
+    res = srv.run()
+    torch.cuda.synchronize()
+    t_end = time.perf_counter()
+    clk = clocks.stop()
+    b.close()
+    lat = serve.latency_summary(res)
+    span = max(r.done for r in res) - t0
+    if rank != 0:
+        return None
+    return {
+        "metric": "served meshes/s; p50/p99 latency", "value": len(res) / span,
+        "unit": "meshes/s", "latency": lat, "arrival_rate": rate,
+        "closed_loop_warmup": {"value": closed, "unit": "meshes/s", "requests": nw},
+        "steiner_per_s": sum(r.stats["steiner_inserted"] for r in res) / span,
+        "rounds": srv.rounds, "n_gpus": world, "steps": 1, "warmup": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "requests": len(reqs),
+                   "points_total": sum(x["n"] for x in insts), "B": spec["B"],
+                   "hbm_budget_gb": budget / 1e9, "arrival": "Poisson, 0.8x closed-loop",
+                   "sample": "40 of config 5's 2,000 requests"},
+        "clocks": clk,
+    }
+
+
 def workload_config(args, world):
     """The workload named in both arms' JSON lines."""
     w = WORKLOADS[args.workload]
@@ -358,7 +513,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uniform100k", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="uniform100k", choices=sorted(WORKLOADS) + sorted(MULTI))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -378,6 +533,15 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
+    if args.workload in MULTI:
+        line = multi_arm(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     line = gpu_arm(args, rank, world)
     if line is not None and world == 1 and not args.no_cpu_baseline:
         log("cpu baseline: building the oracle's Delaunay mesh")

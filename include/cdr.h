@@ -194,6 +194,53 @@ int cdr_delaunay_box(const double* xyz, int32_t n, const cdr_options* opt,
                      const cdr_allocator* alloc, void* stream, cdr_handle** out,
                      int32_t* n_skipped, int32_t* n_rounds);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent refinements (instances) advance together, each round being
+ * one pass of every kernel over all instances' candidates (Sec. 2's round, with
+ * every instance serving its own first non-empty class: subsegments, then
+ * subfaces, then bad tetrahedra). The instances live as disconnected parts of
+ * one device-resident mesh. An element's priority depends only on its
+ * geometry and the relative order of its vertex ids, so an instance's result is
+ * the same whether it is refined alone (cdr_create + cdr_refine) or in a
+ * batch, whenever it joins. Instances can join (cdr_batch_add) and leave
+ * (cdr_batch_remove) between rounds.
+ *
+ * Create an empty batch. opt: walk_limit and guard2 apply to every instance
+ * (guard2 <= 0: each instance's own default); alloc, stream as for cdr_create.
+ * The batch is a cdr_handle: cdr_destroy releases it, cdr_export copies the
+ * whole multi-instance mesh, and cdr_refine / cdr_round / cdr_checkpoint /
+ * cdr_restore reject it (CDR_ERR_INVALID_INPUT). */
+int cdr_batch_create(const cdr_options* opt, const cdr_allocator* alloc, void* stream,
+                     cdr_handle** out);
+
+/* Admit an instance: a CDT with labels as for cdr_create (validated the same
+ * way) and its bound B. *slot receives its slot (slots of removed instances
+ * are reused). The input is copied; the call synchronises the batch's stream.
+ * CDR_ERR_OOM if the batch would exceed 2^28 vertices or the device memory. */
+int cdr_batch_add(cdr_handle* b, const cdr_mesh_in* in, double B, int32_t* slot);
+
+/* One round for every instance with work left. *n_active (nullable) receives
+ * the number of instances that had candidates this round (0: all done). */
+int cdr_batch_round(cdr_handle* b, int32_t* n_active);
+
+/* Rounds until no instance has work left or max_rounds rounds ran (then
+ * CDR_ROUND_LIMIT). *rounds (nullable) receives the rounds run. */
+int cdr_batch_refine(cdr_handle* b, int32_t max_rounds, int32_t* rounds);
+
+/* Statistics of one instance (accumulated over the rounds it took part in;
+ * the sizes and n_bad_left are those of its current mesh) and its state:
+ * 0 free slot, 1 refining, 2 done. */
+int cdr_batch_stats(cdr_handle* b, int32_t slot, cdr_stats* stats, int32_t* state);
+
+/* Sizes and copy of one instance's mesh, in the layout of cdr_export_sizes /
+ * cdr_export, with vertex ids, facet ids and segment ids local to the
+ * instance (vertices in the order the instance created them). */
+int cdr_batch_export_sizes(cdr_handle* b, int32_t slot, cdr_sizes* out);
+int cdr_batch_export(cdr_handle* b, int32_t slot, const cdr_mesh_out* out);
+
+/* Remove an instance: its elements are retired and its slot freed. */
+int cdr_batch_remove(cdr_handle* b, int32_t slot);
+
 /* Text for a status code. */
 const char* cdr_status_string(int status);
 
@@ -208,7 +255,8 @@ const char* cdr_status_string(int status);
  *            4 retried in tier 2, 5 invariant failures, 6 neighbour tetrahedra
  *            tested by growth, 7 cavity tetrahedra, 8 boundary faces, 9 new
  *            tetrahedra written, 10 refusals flagging a new candidate, 11 regions
- *            stopped on a higher-priority start, 15 kernels of this library launched (library
+ *            stopped on a higher-priority start, 12 tetrahedra retired by
+ *            insertion, 15 kernels of this library launched (library
  *            primitives such as sorts and scans excluded)
  * Any output pointer may be NULL. */
 int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_t* calls,

@@ -69,6 +69,8 @@ def lib():
             L.orc_tet_bad.argtypes = [dp] * 4 + [ctypes.c_double]
             L.orc_prio_hash.argtypes = [ctypes.c_int, ip, ctypes.c_int]
             L.orc_prio_hash.restype = ctypes.c_uint64
+            L.orc_prio_hash_xyz.argtypes = [ctypes.c_int, dp, ctypes.c_int]
+            L.orc_prio_hash_xyz.restype = ctypes.c_uint64
             L.orc_box_delaunay.argtypes = [dp, ctypes.c_int, ip]
             L.orc_box_delaunay.restype = P
             L.orc_create.argtypes = [dp, ctypes.c_int, ip, ctypes.c_int]
@@ -173,6 +175,13 @@ def tet_bad(a, b, c, d, B):
 def prio_hash(cls, ids):
     ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int32))
     return int(lib().orc_prio_hash(int(cls), _i(ids), len(ids)))
+
+
+def prio_hash_xyz(cls, xyz):
+    """Priority of an element from its vertices' coordinates, (n, 3), vertices in
+    ascending id order."""
+    xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+    return int(lib().orc_prio_hash_xyz(int(cls), _d(xyz), len(xyz)))
 
 
 # ---------------------------------------------------------------------- meshes

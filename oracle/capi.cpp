@@ -179,6 +179,9 @@ int orc_tet_bad(const double* a, const double* b, const double* c, const double*
   return tet_is_bad(a, b, c, d, B) ? 1 : 0;
 }
 uint64_t orc_prio_hash(int cls, const int* ids, int n) { return prio_hash(cls, ids, n); }
+uint64_t orc_prio_hash_xyz(int cls, const double* xyz, int nverts) {
+  return prio_hash_xyz(cls, xyz, nverts);
+}
 
 // ----------------------------------------------------------- meshes
 void* orc_box_delaunay(const double* pts, int n, int* skipped) {

@@ -20,6 +20,7 @@
 // circumcentre (Sec. 2); Delaunay region membership = "circumcircle or
 // circumsphere encloses p" (Sec. 2).
 #pragma once
+#include <cstring>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -314,8 +315,13 @@ inline bool tet_is_bad(const double* a, const double* b, const double* c, const 
   return (r2 / l2) > (B * B);
 }
 
-// Priority hash for candidate ordering: the SplitMix64 finaliser (Steele, Lea and
-// Flood 2014) chained over the sorted vertex ids of the element.
+// Priority hash for candidate ordering (the predetermined priorities of Sec. 2):
+// the SplitMix64 finaliser (Steele, Lea and Flood 2014) chained over 64-bit words
+// and seeded by the class. An element's words are the bit patterns of its
+// vertices' coordinates (x, y, z per vertex, vertices in ascending id order), so
+// its priority depends on its geometry and on the relative order of its vertex
+// ids only: an instance refined alone or beside others in one mesh orders its
+// candidates the same way. A plain point's word is its index.
 inline uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
@@ -324,6 +330,15 @@ inline uint64_t mix64(uint64_t z) {
 inline uint64_t prio_hash(int cls, const int* ids, int n) {
   uint64_t h = 0x9E3779B97F4A7C15ULL * (uint64_t)(cls + 1);
   for (int i = 0; i < n; ++i) h = mix64(h ^ (uint64_t)(uint32_t)ids[i]);
+  return h;
+}
+inline uint64_t prio_hash_xyz(int cls, const double* xyz, int nverts) {
+  uint64_t h = 0x9E3779B97F4A7C15ULL * (uint64_t)(cls + 1);
+  for (int i = 0; i < 3 * nverts; ++i) {
+    uint64_t w;
+    std::memcpy(&w, &xyz[i], 8);
+    h = mix64(h ^ w);
+  }
   return h;
 }
 

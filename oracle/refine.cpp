@@ -52,7 +52,14 @@ void cand_key(const Mesh& M, int cls, int elem, Cand& c) {
     c.key[0] = elem;
     c.nkey = 1;
   }
-  c.h = prio_hash(cls, c.key, c.nkey);
+  if (cls == CLS_POINT) {
+    c.h = prio_hash(cls, c.key, c.nkey);
+  } else {
+    double xyz[12];
+    for (int i = 0; i < c.nkey; ++i)
+      for (int k = 0; k < 3; ++k) xyz[3 * i + k] = M.X(c.key[i])[k];
+    c.h = prio_hash_xyz(cls, xyz, c.nkey);
+  }
 }
 
 static bool finite3(const double* p) {

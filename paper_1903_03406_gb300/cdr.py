@@ -121,6 +121,15 @@ def lib():
                                               ctypes.c_int32, i32p,
                                               ctypes.POINTER(ctypes.c_double), P]
             L.cdr_eval_predicates_noalloc.argtypes = L.cdr_eval_predicates.argtypes
+            L.cdr_batch_create.argtypes = [ctypes.POINTER(Options), ctypes.POINTER(Allocator), P,
+                                           pp]
+            L.cdr_batch_add.argtypes = [P, ctypes.POINTER(MeshIn), ctypes.c_double, i32p]
+            L.cdr_batch_round.argtypes = [P, i32p]
+            L.cdr_batch_refine.argtypes = [P, ctypes.c_int32, i32p]
+            L.cdr_batch_stats.argtypes = [P, ctypes.c_int32, ctypes.POINTER(Stats), i32p]
+            L.cdr_batch_export_sizes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(Sizes)]
+            L.cdr_batch_export.argtypes = [P, ctypes.c_int32, ctypes.POINTER(MeshOut)]
+            L.cdr_batch_remove.argtypes = [P, ctypes.c_int32]
             _lib = L
     return _lib
 
@@ -174,6 +183,42 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref=None):
+    """A cdr_mesh_in over contiguous copies (returned too, to keep them alive)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    segs = np.ascontiguousarray(segs, dtype=np.int32).reshape(-1, 2)
+    seg_id = np.ascontiguousarray(seg_id, dtype=np.int32).reshape(-1)
+    tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    facet_id = np.ascontiguousarray(facet_id, dtype=np.int32).reshape(-1)
+    fr = None
+    if facet_ref is not None:
+        fr = np.ascontiguousarray(facet_ref, dtype=np.float64).reshape(-1, 3)
+    mi = MeshIn(_p(xyz, ctypes.c_double), len(xyz), _p(tets, ctypes.c_int32), len(tets),
+                _p(segs, ctypes.c_int32), _p(seg_id, ctypes.c_int32), len(segs),
+                _p(tris, ctypes.c_int32), _p(facet_id, ctypes.c_int32), len(tris),
+                int(n_facets), _p(fr, ctypes.c_double))
+    return mi, (xyz, tets, segs, seg_id, tris, facet_id, fr)
+
+
+def _export(s, call, what):
+    """Buffers sized from s, filled by call(cdr_mesh_out)."""
+    xyz = np.zeros((s["nv"], 3))
+    tets = np.zeros((s["nt"], 4), dtype=np.int32)
+    tflag = np.zeros(s["nt"], dtype=np.uint8)
+    sf = np.zeros((s["ns"], 4), dtype=np.int32)
+    sfflag = np.zeros(s["ns"], dtype=np.uint8)
+    ss = np.zeros((s["ng"], 3), dtype=np.int32)
+    ssflag = np.zeros(s["ng"], dtype=np.uint8)
+    fq = np.zeros((max(s["nfacets"], 1), 3))
+    mo = MeshOut(_p(xyz, ctypes.c_double), _p(tets, ctypes.c_int32), _p(tflag, ctypes.c_uint8),
+                 _p(sf, ctypes.c_int32), _p(sfflag, ctypes.c_uint8), _p(ss, ctypes.c_int32),
+                 _p(ssflag, ctypes.c_uint8), _p(fq, ctypes.c_double))
+    _check(call(mo), what)
+    return dict(xyz=xyz, tets=tets, tflag=tflag, sf=sf, sfflag=sfflag, ss=ss, ssflag=ssflag,
+                facetq=fq[: s["nfacets"]])
+
+
 class Handle:
     """A refinement handle (cdr_handle) owning its device mesh."""
 
@@ -194,19 +239,7 @@ class Handle:
     @classmethod
     def create(cls, xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref=None,
                guard2=0.0, walk_limit=0, reserve_factor=0, allocator=None, stream=None):
-        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
-        tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
-        segs = np.ascontiguousarray(segs, dtype=np.int32).reshape(-1, 2)
-        seg_id = np.ascontiguousarray(seg_id, dtype=np.int32).reshape(-1)
-        tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
-        facet_id = np.ascontiguousarray(facet_id, dtype=np.int32).reshape(-1)
-        fr = None
-        if facet_ref is not None:
-            fr = np.ascontiguousarray(facet_ref, dtype=np.float64).reshape(-1, 3)
-        mi = MeshIn(_p(xyz, ctypes.c_double), len(xyz), _p(tets, ctypes.c_int32), len(tets),
-                    _p(segs, ctypes.c_int32), _p(seg_id, ctypes.c_int32), len(segs),
-                    _p(tris, ctypes.c_int32), _p(facet_id, ctypes.c_int32), len(tris),
-                    int(n_facets), _p(fr, ctypes.c_double))
+        mi, _arrays = _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref)
         opt = Options(float(guard2), int(walk_limit), int(reserve_factor))
         out = ctypes.c_void_p()
         al = ctypes.byref(allocator.struct) if allocator is not None else None
@@ -253,7 +286,7 @@ class Handle:
               "insert", "compact"]
     COUNTERS = ["refused", "unsplittable", "blasted", "inserted", "retried", "invariant",
                 "tested", "cavity", "boundary", "new_tets", "new_candidates", "blasted_early",
-                "c12", "c13", "c14", "launches"]
+                "dead_tets", "c13", "c14", "launches"]
 
     def profile(self, enable=-1, reset=False):
         ms = np.zeros(16)
@@ -280,21 +313,8 @@ class Handle:
                     nfacets=s.n_facets)
 
     def export(self):
-        s = self.sizes()
-        xyz = np.zeros((s["nv"], 3))
-        tets = np.zeros((s["nt"], 4), dtype=np.int32)
-        tflag = np.zeros(s["nt"], dtype=np.uint8)
-        sf = np.zeros((s["ns"], 4), dtype=np.int32)
-        sfflag = np.zeros(s["ns"], dtype=np.uint8)
-        ss = np.zeros((s["ng"], 3), dtype=np.int32)
-        ssflag = np.zeros(s["ng"], dtype=np.uint8)
-        fq = np.zeros((max(s["nfacets"], 1), 3))
-        mo = MeshOut(_p(xyz, ctypes.c_double), _p(tets, ctypes.c_int32), _p(tflag, ctypes.c_uint8),
-                     _p(sf, ctypes.c_int32), _p(sfflag, ctypes.c_uint8), _p(ss, ctypes.c_int32),
-                     _p(ssflag, ctypes.c_uint8), _p(fq, ctypes.c_double))
-        _check(lib().cdr_export(self.ptr, ctypes.byref(mo)), "cdr_export")
-        return dict(xyz=xyz, tets=tets, tflag=tflag, sf=sf, sfflag=sfflag, ss=ss, ssflag=ssflag,
-                    facetq=fq[: s["nfacets"]])
+        return _export(self.sizes(), lambda mo: lib().cdr_export(self.ptr, ctypes.byref(mo)),
+                       "cdr_export")
 
     def round_report(self):
         n = ctypes.c_int32(0)
@@ -316,6 +336,73 @@ class Handle:
                                   _p(cav, ctypes.c_int32)), "cdr_round_report")
         return dict(keys=keys, pts=pts, outcome=outcome, reason=reason, surv=surv, ncav=ncav,
                     nbnd=nbnd, nfcav=nfcav, cav=cav[: tot.value])
+
+
+class Batch:
+    """Many instances refined together in one device-resident mesh
+    (cdr_batch_*): every round runs each kernel once over all instances."""
+
+    STATE = {0: "free", 1: "refining", 2: "done"}
+
+    def __init__(self, guard2=0.0, walk_limit=0, allocator=None, stream=None):
+        opt = Options(float(guard2), int(walk_limit), 0)
+        out = ctypes.c_void_p()
+        al = ctypes.byref(allocator.struct) if allocator is not None else None
+        _check(lib().cdr_batch_create(ctypes.byref(opt), al, _stream_handle(stream),
+                                      ctypes.byref(out)), "cdr_batch_create")
+        self.ptr = out
+        self._keep = (allocator,)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        p = getattr(self, "ptr", None)
+        if p:
+            lib().cdr_destroy(p)
+            self.ptr = None
+
+    def add(self, B, xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref=None):
+        mi, _arrays = _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref)
+        slot = ctypes.c_int32(-1)
+        _check(lib().cdr_batch_add(self.ptr, ctypes.byref(mi), float(B), ctypes.byref(slot)),
+               "cdr_batch_add")
+        return slot.value
+
+    def round(self):
+        n = ctypes.c_int32(0)
+        _check(lib().cdr_batch_round(self.ptr, ctypes.byref(n)), "cdr_batch_round")
+        return n.value
+
+    def refine(self, max_rounds=1 << 30):
+        r = ctypes.c_int32(0)
+        st = lib().cdr_batch_refine(self.ptr, int(min(max_rounds, 2**31 - 1)), ctypes.byref(r))
+        _check(st, "cdr_batch_refine", ok=(CDR_OK, CDR_ROUND_LIMIT))
+        return r.value
+
+    def stats(self, slot):
+        s = Stats()
+        state = ctypes.c_int32(0)
+        _check(lib().cdr_batch_stats(self.ptr, int(slot), ctypes.byref(s), ctypes.byref(state)),
+               "cdr_batch_stats")
+        d = s.as_dict()
+        d["state"] = self.STATE.get(state.value, state.value)
+        return d
+
+    def sizes(self, slot):
+        s = Sizes()
+        _check(lib().cdr_batch_export_sizes(self.ptr, int(slot), ctypes.byref(s)),
+               "cdr_batch_export_sizes")
+        return dict(nv=s.n_verts, nt=s.n_tets, ns=s.n_subfaces, ng=s.n_subsegs,
+                    nfacets=s.n_facets)
+
+    def export(self, slot):
+        return _export(self.sizes(slot),
+                       lambda mo: lib().cdr_batch_export(self.ptr, int(slot), ctypes.byref(mo)),
+                       "cdr_batch_export")
+
+    def remove(self, slot):
+        _check(lib().cdr_batch_remove(self.ptr, int(slot)), "cdr_batch_remove")
 
 
 def device_arch():

@@ -42,14 +42,17 @@ struct cdr_handle {
   DevMesh m{};
   int capV = 0, capT = 0, capS = 0, capG = 0;
   int hcount = 0;
+  long long deadT = 0;     // retired tetrahedra not yet compacted away
+  bool deadKnown = true;   // false after removals: count them before deciding
   double lastB = -1.0;
   unsigned epoch = 0;
   bool dt_mode = false;
   // mesh arrays
   Buf bV, bT, bTS, bTflag, bTmark, bTseed, bTfwd, bSV, bSN, bSflag, bSmust, bSmark, bGV, bGflag, bGmust,
       bFQ, bHK, bHV;
-  // classification
-  Buf bCandS, bCandG, bCandT;
+  // classification: candidate flags and dirty marks, kept from round to round
+  Buf bCandS, bCandG, bCandT, bDirtyS, bDirtyG;
+  bool fullClassify = true;  // the next classification tests every element
   // round buffers
   int capR = 0, capR2 = 0, capWs2 = 0;
   Buf bCand, bCand2, bKeys, bKeys2, bSp, bLoc, bStatus, bSurv, bCounts, bOffs, bSlab1, bSlab2of,
@@ -66,10 +69,39 @@ struct cdr_handle {
   double prof_ms[16] = {};
   long long prof_calls[16] = {};
   long long prof_ctr[16] = {};
+  // instances: a plain handle holds one; a batch holds several as disconnected
+  // parts of this mesh (Vinst set)
+  int ninst = 1, capI = 0;
+  Buf bVinst, bInstB, bInstG2, bInstCls, bInstCnt, bInstSt, bCcls, bCinst, bRflags;
+  unsigned long long* pinCnt = nullptr;  // pinned: per-instance classification counts
+  int* pinCls = nullptr;                 // pinned: per-instance class of the round
+  unsigned long long* pinSt = nullptr;   // pinned: per-instance round counters
+  std::vector<int> instCls;              // host copy of the round's classes
+  // batch bookkeeping (host)
+  bool batch = false;
+  struct Inst {
+    int state = 0;  // 0 free slot, 1 refining, 2 done
+    int of = 0, nf = 0, oseg = 0, nseg = 0;
+    double B = 0;
+    cdr_stats st{};
+  };
+  std::vector<Inst> insts;
+  std::vector<int> freeSlots;
+  int segIds = 0;
+  cdr_options opts{};
+  // pinned host staging for the values a round reads back
+  struct Pinned {
+    unsigned long long c3[4];
+    unsigned long long st[ST_COUNT];
+    unsigned long long ctr[ST_COUNT];
+    int4 lastOff, lastCnt;
+    int cerr, n2, ovf;
+  }* pin = nullptr;
   // checkpoint
   std::vector<Buf> ck;
   DevMesh ckm{};
   int ck_hcount = 0;
+  long long ck_deadT = 0;
   bool has_ck = false;
 };
 
@@ -144,6 +176,12 @@ void bind(cdr_handle* h) {
   m.FQ = ptr<V4>(h->bFQ);
   m.HK = ptr<unsigned long long>(h->bHK);
   m.HV = ptr<int>(h->bHV);
+  m.Vinst = h->batch ? ptr<int>(h->bVinst) : nullptr;
+  m.candT = ptr<uint8_t>(h->bCandT);
+  m.candS = ptr<uint8_t>(h->bCandS);
+  m.candG = ptr<uint8_t>(h->bCandG);
+  m.dirtyS = ptr<uint8_t>(h->bDirtyS);
+  m.dirtyG = ptr<uint8_t>(h->bDirtyG);
   m.capV = h->capV;
   m.capT = h->capT;
   m.capS = h->capS;
@@ -155,6 +193,7 @@ bool grow_verts(cdr_handle* h, int need) {
   int cap = std::max(need, h->capV + h->capV / 2);
   if (cap > kMaxVerts) return false;
   if (!ensure(h, h->bV, (size_t)cap * sizeof(V4), (size_t)h->m.nV * sizeof(V4))) return false;
+  if (h->batch && !ensure(h, h->bVinst, (size_t)cap * 4, (size_t)h->m.nV * 4)) return false;
   h->capV = cap;
   bind(h);
   return true;
@@ -169,7 +208,7 @@ bool grow_tets(cdr_handle* h, int need) {
             ensure(h, h->bTflag, cap, n) &&
             ensure(h, h->bTmark, cap * sizeof(unsigned long long), n * 8) &&
             ensure(h, h->bTseed, cap * sizeof(unsigned long long), n * 8) &&
-            ensure(h, h->bTfwd, cap * sizeof(int), n * 4) && ensure(h, h->bCandT, cap, 0);
+            ensure(h, h->bTfwd, cap * sizeof(int), n * 4) && ensure(h, h->bCandT, cap, n);
   if (!ok) return false;
   h->capT = cap;
   bind(h);
@@ -182,7 +221,8 @@ bool grow_subfaces(cdr_handle* h, int need) {
   bool ok = ensure(h, h->bSV, cap * sizeof(int4), n * sizeof(int4)) &&
             ensure(h, h->bSN, cap * sizeof(int4), n * sizeof(int4)) &&
             ensure(h, h->bSflag, cap, n) && ensure(h, h->bSmust, cap, n) &&
-            ensure(h, h->bSmark, cap * 8, n * 8) && ensure(h, h->bCandS, cap, 0);
+            ensure(h, h->bSmark, cap * 8, n * 8) && ensure(h, h->bCandS, cap, n) &&
+            ensure(h, h->bDirtyS, cap, n);
   if (!ok) return false;
   h->capS = cap;
   bind(h);
@@ -194,7 +234,7 @@ bool grow_subsegs(cdr_handle* h, int need) {
   size_t n = h->m.nG;
   bool ok = ensure(h, h->bGV, cap * sizeof(int4), n * sizeof(int4)) &&
             ensure(h, h->bGflag, cap, n) && ensure(h, h->bGmust, cap, n) &&
-            ensure(h, h->bCandG, cap, 0);
+            ensure(h, h->bCandG, cap, n) && ensure(h, h->bDirtyG, cap, n);
   if (!ok) return false;
   h->capG = cap;
   bind(h);
@@ -254,9 +294,11 @@ struct Int4Sum {
     return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
   }
 };
-__global__ void k_cand_keys(DevMesh m, int cls, const int* cand, int n, int4* out) {
+__global__ void k_cand_keys(DevMesh m, int cls0, const uint8_t* ccls, const int* cand, int n,
+                            int4* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int e = cand[i];
+    const int cls = ccls ? (int)ccls[i] : cls0;
     int4 k = make_int4(-1, -1, -1, -1);
     if (cls == CLS_SUBSEG) {
       int4 G = m.GV[e];
@@ -401,6 +443,55 @@ inline void pcollect(cdr_handle* h, const bool* used) {
   }
 }
 
+bool ensure_pinned(cdr_handle* h) {
+  if (h->pin) return true;
+  void* p = nullptr;
+  if (cudaMallocHost(&p, sizeof(*h->pin)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  h->pin = static_cast<decltype(h->pin)>(p);
+  return true;
+}
+
+// per-instance device arrays and pinned staging for at least n instances
+bool ensure_instances(cdr_handle* h, int n) {
+  if (n <= h->capI && h->pinCnt) return true;
+  int c = std::max(n, std::max(16, 2 * h->capI));
+  if (!ensure(h, h->bInstB, (size_t)c * 8, (size_t)h->capI * 8) ||
+      !ensure(h, h->bInstG2, (size_t)c * 8, (size_t)h->capI * 8) ||
+      !ensure(h, h->bInstCls, (size_t)c * 4) || !ensure(h, h->bInstCnt, (size_t)c * 3 * 8) ||
+      !ensure(h, h->bInstSt, (size_t)c * IS_COUNT * 8))
+    return false;
+  void* a = nullptr;
+  void* b = nullptr;
+  void* q = nullptr;
+  if (cudaMallocHost(&a, (size_t)c * 3 * 8) != cudaSuccess ||
+      cudaMallocHost(&b, (size_t)c * 4) != cudaSuccess ||
+      cudaMallocHost(&q, (size_t)c * IS_COUNT * 8) != cudaSuccess) {
+    cudaGetLastError();
+    if (a) cudaFreeHost(a);
+    if (b) cudaFreeHost(b);
+    return false;
+  }
+  if (h->pinCnt) cudaFreeHost(h->pinCnt);
+  if (h->pinCls) cudaFreeHost(h->pinCls);
+  if (h->pinSt) cudaFreeHost(h->pinSt);
+  h->pinCnt = static_cast<unsigned long long*>(a);
+  h->pinCls = static_cast<int*>(b);
+  h->pinSt = static_cast<unsigned long long*>(q);
+  h->capI = c;
+  DevMesh& m = h->m;
+  m.instCls = ptr<int>(h->bInstCls);
+  m.instCnt = ptr<unsigned long long>(h->bInstCnt);
+  m.instSt = ptr<unsigned long long>(h->bInstSt);
+  if (h->batch) {
+    m.instB = ptr<double>(h->bInstB);
+    m.instG2 = ptr<double>(h->bInstG2);
+  }
+  return true;
+}
+
 bool ensure_round(cdr_handle* h, int n) {
   if (n <= h->capR && h->bCand.p) return true;
   int c = std::max(n, 1024);
@@ -412,7 +503,8 @@ bool ensure_round(cdr_handle* h, int n) {
             ensure(h, h->bSlab1, (size_t)c * SlabLayout<Tier1>::STRIDE * 4) &&
             ensure(h, h->bSlab2of, (size_t)c * 4) && ensure(h, h->bList2, (size_t)c * 4) &&
             ensure(h, h->bCkey, (size_t)c * 16) && ensure(h, h->bStats, 32 * 8) &&
-            ensure(h, h->bErr, 64) && ensure(h, h->bI32, (size_t)(c + 1) * 4);
+            ensure(h, h->bErr, 64) && ensure(h, h->bI32, (size_t)(c + 1) * 4) &&
+            ensure(h, h->bCcls, (size_t)c) && ensure(h, h->bCinst, (size_t)c * 4);
   if (ok) h->capR = c;
   return ok;
 }
@@ -437,8 +529,12 @@ DevRound make_round(cdr_handle* h, int cls, int n, double B) {
   r.offs = ptr<int4>(h->bOffs);
   r.point_state = ptr<int>(h->bPstate);
   r.stats = ptr<unsigned long long>(h->bStats);
-  r.candG = (cls == CLS_SUBSEG) ? ptr<uint8_t>(h->bCandG) : nullptr;
+  r.candG = (cls == CLS_SUBSEG || cls < 0) ? ptr<uint8_t>(h->bCandG) : nullptr;
   r.B = B;
+  if (cls < 0) {  // every instance serves its own class
+    r.ccls = ptr<uint8_t>(h->bCcls);
+    r.cinst = ptr<int>(h->bCinst);
+  }
   return r;
 }
 
@@ -451,6 +547,7 @@ struct RoundOut {
 int maybe_compact(cdr_handle* h, bool force) {
   DevMesh& m = h->m;
   if (!force && m.nT < (1 << 19)) return 0;
+  if (!force && h->deadKnown && h->deadT * 2 < m.nT) return 0;
   Buf alive, newid;
   if (!ensure(h, alive, (size_t)m.nT * 4 + 64) || !ensure(h, newid, (size_t)(m.nT + 1) * 4 + 64))
     return CDR_ERR_OOM;
@@ -465,6 +562,8 @@ int maybe_compact(cdr_handle* h, bool force) {
   cudaMemcpyAsync(&last[1], ptr<int>(alive) + m.nT - 1, 4, cudaMemcpyDeviceToHost, h->stream);
   cudaStreamSynchronize(h->stream);
   int live = last[0] + last[1];
+  h->deadT = m.nT - live;
+  h->deadKnown = true;
   if (!force && live * 2 > m.nT) {
     dfree(h, alive);
     dfree(h, newid);
@@ -486,6 +585,8 @@ int maybe_compact(cdr_handle* h, bool force) {
   dfree(h, TS2);
   dfree(h, F2);
   m.nT = live;
+  h->deadT = 0;
+  h->fullClassify = true;
   bind(h);
   cudaMemsetAsync(h->bTmark.p, 0xff, (size_t)h->capT * 8, h->stream);
   cudaMemsetAsync(h->bTseed.p, 0xff, (size_t)h->capT * 8, h->stream);
@@ -499,10 +600,12 @@ int maybe_compact(cdr_handle* h, bool force) {
 int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   DevMesh& m = h->m;
   cudaStream_t s = h->stream;
+  if (!ensure_pinned(h)) return CDR_ERR_OOM;
   DevRound r = make_round(h, cls, n, B);
   cudaMemsetAsync(h->bStats.p, 0, ST_COUNT * 8, s);
+  if (cls < 0) cudaMemsetAsync(h->bInstSt.p, 0, (size_t)h->ninst * IS_COUNT * 8, s);
   k_fill_int<<<gridn(n), 256, 0, s>>>(ptr<int>(h->bSlab2of), n, -1);
-  k_cand_keys<<<gridn(n), 256, 0, s>>>(m, cls, r.cand, n, ptr<int4>(h->bCkey));
+  k_cand_keys<<<gridn(n), 256, 0, s>>>(m, cls, r.ccls, r.cand, n, ptr<int4>(h->bCkey));
   h->prof_ctr[15] += 2;
   bool used[PG_N] = {};
   pmark(h, PG_SPLIT, 0);
@@ -543,9 +646,9 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
     tb = h->bTmp.bytes;
     cub::DeviceSelect::Flagged(h->bTmp.p, tb, thrust::counting_iterator<int>(0), flag,
                                ptr<int>(h->bList2), nsel, n, s);
-    int n2 = 0;
-    cudaMemcpyAsync(&n2, nsel, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&h->pin->n2, nsel, 4, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
+    int n2 = h->pin->n2;
     if (n2 > 0) {
       const size_t stride2 = SlabLayout<Tier2>::STRIDE;
       int warps = std::min(n2, 152 * 4);
@@ -572,6 +675,11 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   pmark(h, PG_SELECT, 1);
   h->prof_ctr[15] += cls == CLS_POINT ? 2 : 1;
   used[PG_SELECT] = true;
+  // stall rule for instances serving subsegments (decided on the device)
+  if (cls < 0 && std::find(h->instCls.begin(), h->instCls.end(), CLS_SUBSEG) != h->instCls.end()) {
+    launch_stall(m, r, s);
+    h->prof_ctr[15] += 1;
+  }
   // allocation: exclusive scan of (verts, tets, subfaces, subsegs)
   {
     size_t tb = 0;
@@ -582,21 +690,16 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
     cub::DeviceScan::ExclusiveScan(h->bTmp.p, tb, r.counts, ptr<int4>(h->bOffs), Int4Sum(),
                                    make_int4(0, 0, 0, 0), n, s);
   }
-  int4 lastOff, lastCnt;
-  unsigned long long st[ST_COUNT];
-  cudaMemcpyAsync(&lastOff, ptr<int4>(h->bOffs) + n - 1, 16, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(&lastCnt, r.counts + n - 1, 16, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(st, h->bStats.p, sizeof(st), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&h->pin->lastOff, ptr<int4>(h->bOffs) + n - 1, 16, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&h->pin->lastCnt, r.counts + n - 1, 16, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h->pin->st, h->bStats.p, sizeof(h->pin->st), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   if (cuda_status(h)) return h->err;
+  const int4 lastOff = h->pin->lastOff, lastCnt = h->pin->lastCnt;
+  unsigned long long st[ST_COUNT];
+  for (int k = 0; k < ST_COUNT; ++k) st[k] = h->pin->st[k];
   int4 tot = make_int4(lastOff.x + lastCnt.x, lastOff.y + lastCnt.y, lastOff.z + lastCnt.z,
                        lastOff.w + lastCnt.w);
-  if (cls == CLS_SUBSEG && st[ST_SURV] == 0 && st[ST_UNSPL] == 0 && st[ST_NEWCAND] == 0) {
-    launch_stall(m, r, s);
-    h->prof_ctr[15] += 1;
-    st[ST_UNSPL] += st[ST_REJECT];
-    st[ST_REJECT] = 0;
-  }
   if (!grow_verts(h, m.nV + tot.x) || !grow_tets(h, m.nT + tot.y) ||
       !grow_subfaces(h, m.nS + tot.z) || !grow_subsegs(h, m.nG + tot.w))
     return h->err ? h->err : CDR_ERR_OOM;
@@ -626,7 +729,19 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
     ro->unspl = (long long)st[ST_UNSPL];
     ro->blasted = (long long)st[ST_OK] + (long long)st[ST_BLAST];
   }
-  if (exact_overflow_flag(s, true)) return set_err(h, CDR_ERR_INTERNAL);
+  // one synchronisation for the round's error flags and counters
+  const unsigned long long* ctr = h->pin->ctr;
+  h->pin->ovf = 0;
+  exact_overflow_copy_async(&h->pin->ovf, s);
+  cudaMemcpyAsync(h->pin->ctr, h->bStats.p, sizeof(h->pin->ctr), cudaMemcpyDeviceToHost, s);
+  if (h->batch && cls < 0)
+    cudaMemcpyAsync(h->pinSt, h->bInstSt.p, (size_t)h->ninst * IS_COUNT * 8,
+                    cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (h->pin->ovf) {
+    exact_overflow_flag(s, true);  // clear it
+    return set_err(h, CDR_ERR_INTERNAL);
+  }
   {
     int info[4];
     if (checked_error(info, s)) {
@@ -635,14 +750,10 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
       return set_err(h, CDR_ERR_INTERNAL);
     }
   }
-  {
-    unsigned long long ctr[ST_COUNT];
-    cudaMemcpyAsync(ctr, h->bStats.p, sizeof(ctr), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    if (ctr[ST_ITER]) return set_err(h, CDR_ERR_INTERNAL);  // a device invariant check failed
-    pcollect(h, used);
-    for (int k = 0; k < ST_COUNT && k < 15; ++k) h->prof_ctr[k] += (long long)ctr[k];
-  }
+  if (ctr[ST_ITER]) return set_err(h, CDR_ERR_INTERNAL);  // a device invariant check failed
+  pcollect(h, used);
+  for (int k = 0; k < ST_COUNT && k < 15; ++k) h->prof_ctr[k] += (long long)ctr[k];
+  h->deadT += (long long)ctr[ST_DEADT];
   return cuda_status(h);
 }
 
@@ -664,64 +775,80 @@ int order_candidates(cdr_handle* h, int cls, int n) {
   return cuda_status(h);
 }
 
+// One round: every instance serves its own first non-empty class (subsegments,
+// subfaces, bad tetrahedra; Sec. 2). With one instance this is the plain
+// one-class round.
 int refine_round(cdr_handle* h, double B, RoundOut* ro) {
   DevMesh& m = h->m;
   cudaStream_t s = h->stream;
-  if (B != h->lastB) {
+  if (!h->batch && B != h->lastB) {  // (a batch's bounds are per instance, set on entry)
     launch_recompute_bad(m, B, s);
     h->prof_ctr[15] += 1;
     h->lastB = B;
+    h->fullClassify = true;
   }
   int st = maybe_compact(h, false);
   if (st) return st;
-  if (!ensure_round(h, 1024)) return CDR_ERR_OOM;
+  if (!ensure_round(h, 1024) || !ensure_pinned(h) || !ensure_instances(h, h->ninst))
+    return CDR_ERR_OOM;
+  const int ni = h->ninst;
   cudaMemsetAsync(h->bErr.p, 0, 64, s);
   pmark(h, PG_CLASSIFY, 0);
-  launch_classify(m, ptr<uint8_t>(h->bCandS), ptr<uint8_t>(h->bCandG), ptr<uint8_t>(h->bCandT),
-                  ptr<int>(h->bErr), s);
+  launch_classify(m, h->fullClassify, ptr<int>(h->bErr), s);
+  h->fullClassify = false;
   pmark(h, PG_CLASSIFY, 1);
   h->prof_ctr[15] += 2;  // classification + counts
-  unsigned long long* cnt = ptr<unsigned long long>(h->bStats);
-  cudaMemsetAsync(cnt, 0, 24, s);
-  k_count3<<<gridn((long)m.nG + m.nS + m.nT), 256, 0, s>>>(
-      ptr<uint8_t>(h->bCandG), m.nG, ptr<uint8_t>(h->bCandS), m.nS, ptr<uint8_t>(h->bCandT), m.nT,
-      cnt);
-  unsigned long long c3[3];
-  int cerr = 0;
-  cudaMemcpyAsync(c3, cnt, 24, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(&cerr, h->bErr.p, 4, cudaMemcpyDeviceToHost, s);
+  cudaMemsetAsync(h->bInstCnt.p, 0, (size_t)ni * 3 * 8, s);
+  launch_count_inst(m, ptr<uint8_t>(h->bCandG), ptr<uint8_t>(h->bCandS), ptr<uint8_t>(h->bCandT),
+                    s);
+  cudaMemcpyAsync(h->pinCnt, h->bInstCnt.p, (size_t)ni * 3 * 8, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&h->pin->cerr, h->bErr.p, 4, cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   if (cuda_status(h)) return h->err;
-  if (cerr) return set_err(h, CDR_ERR_INTERNAL);
+  if (h->pin->cerr) return set_err(h, CDR_ERR_INTERNAL);
   {
     bool used[PG_N] = {};
     used[PG_CLASSIFY] = true;
     pcollect(h, used);
   }
-  int cls = -1;
-  for (int c = 0; c < 3; ++c)
-    if (c3[c] > 0) {
-      cls = c;
-      break;
-    }
+  h->instCls.assign(ni, -1);
+  long long n = 0;
+  for (int k = 0; k < ni; ++k) {
+    for (int c = 0; c < 3; ++c)
+      if (h->pinCnt[3 * k + c] > 0) {
+        h->instCls[k] = c;
+        n += (long long)h->pinCnt[3 * k + c];
+        break;
+      }
+    h->pinCls[k] = h->instCls[k];
+  }
   if (ro) *ro = RoundOut();
-  if (cls < 0) return CDR_OK;
-  int n = (int)c3[cls];
-  if (!ensure_round(h, n)) return CDR_ERR_OOM;
-  const uint8_t* flags = cls == 0 ? ptr<uint8_t>(h->bCandG)
-                                  : (cls == 1 ? ptr<uint8_t>(h->bCandS) : ptr<uint8_t>(h->bCandT));
-  int nall = cls == 0 ? m.nG : (cls == 1 ? m.nS : m.nT);
+  if (n == 0) return CDR_OK;
+  if (n >= (1LL << 31) - 1) return set_err(h, CDR_ERR_OOM);
+  if (!ensure_round(h, (int)n)) return CDR_ERR_OOM;
+  const long nall = (long)m.nG + m.nS + m.nT;
+  if (!ensure(h, h->bRflags, (size_t)nall + 64)) return CDR_ERR_OOM;
+  cudaMemcpyAsync(h->bInstCls.p, h->pinCls, (size_t)ni * 4, cudaMemcpyHostToDevice, s);
+  launch_round_flags(m, ptr<uint8_t>(h->bCandG), ptr<uint8_t>(h->bCandS), ptr<uint8_t>(h->bCandT),
+                     ptr<uint8_t>(h->bRflags), s);
   size_t tb = 0;
   int* nsel = ptr<int>(h->bErr) + 4;
+  const uint8_t* flags = ptr<uint8_t>(h->bRflags);
   cub::DeviceSelect::Flagged(nullptr, tb, thrust::counting_iterator<int>(0), flags,
-                             ptr<int>(h->bCand), nsel, nall, s);
+                             ptr<int>(h->bCand), nsel, (int)nall, s);
   if (!tmp_ensure(h, tb)) return CDR_ERR_OOM;
   tb = h->bTmp.bytes;
   cub::DeviceSelect::Flagged(h->bTmp.p, tb, thrust::counting_iterator<int>(0), flags,
-                             ptr<int>(h->bCand), nsel, nall, s);
-  st = order_candidates(h, cls, n);
+                             ptr<int>(h->bCand), nsel, (int)nall, s);
+  h->prof_ctr[15] += 1;
+  st = order_candidates(h, -1, (int)n);
   if (st) return st;
-  return round_core(h, cls, n, B, ro);
+  launch_decode_cands(m, ptr<int>(h->bCand2), ptr<uint8_t>(h->bCcls), ptr<int>(h->bCinst), (int)n,
+                      s);
+  h->prof_ctr[15] += 1;
+  st = round_core(h, -1, (int)n, B, ro);
+  if (ro) ro->cls = ni == 1 ? h->instCls[0] : 3;  // 3: several classes
+  return st;
 }
 
 int count_bad(cdr_handle* h, long long* out) {
@@ -792,12 +919,18 @@ int cdr_device_arch(void) { return 103; }
 
 void cdr_destroy(cdr_handle* h) {
   if (!h) return;
+  if (h->pin) cudaFreeHost(h->pin);
+  if (h->pinCnt) cudaFreeHost(h->pinCnt);
+  if (h->pinCls) cudaFreeHost(h->pinCls);
+  if (h->pinSt) cudaFreeHost(h->pinSt);
   Buf* all[] = {&h->bV, &h->bT, &h->bTS, &h->bTflag, &h->bTmark, &h->bTseed, &h->bTfwd, &h->bSV, &h->bSN,
                 &h->bSflag, &h->bSmust, &h->bSmark, &h->bGV, &h->bGflag, &h->bGmust, &h->bFQ,
                 &h->bHK, &h->bHV, &h->bCandS, &h->bCandG, &h->bCandT, &h->bCand, &h->bCand2,
                 &h->bKeys, &h->bKeys2, &h->bSp, &h->bLoc, &h->bStatus, &h->bSurv, &h->bCounts,
                 &h->bOffs, &h->bSlab1, &h->bSlab2of, &h->bList2, &h->bSlab2, &h->bWs2, &h->bCkey,
-                &h->bTmp, &h->bStats, &h->bErr, &h->bI32, &h->bPts, &h->bHint, &h->bPstate};
+                &h->bTmp, &h->bStats, &h->bErr, &h->bI32, &h->bPts, &h->bHint, &h->bPstate,
+                &h->bVinst, &h->bInstB, &h->bInstG2, &h->bInstCls, &h->bInstCnt, &h->bInstSt,
+                &h->bCcls, &h->bCinst, &h->bRflags, &h->bDirtyS, &h->bDirtyG};
   for (Buf* b : all) dfree(h, *b);
   for (Buf& b : h->ck) dfree(h, b);
   for (auto& e : h->ev)
@@ -1057,6 +1190,7 @@ extern "C" {
 
 int cdr_round(cdr_handle* h, double B, int32_t* cls, cdr_stats* stats) {
   if (!h || !(B > 0)) return CDR_ERR_INVALID_INPUT;
+  if (h->batch) return CDR_ERR_INVALID_INPUT;
   if (h->err) return h->err;
   if (h->dt_mode) return CDR_ERR_INVALID_INPUT;
   RoundOut ro;
@@ -1065,7 +1199,7 @@ int cdr_round(cdr_handle* h, double B, int32_t* cls, cdr_stats* stats) {
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->rounds = ro.cls >= 0 ? 1 : 0;
-    if (ro.cls >= 0) stats->rounds_by_class[ro.cls] = 1;
+    if (ro.cls >= 0 && ro.cls < 3) stats->rounds_by_class[ro.cls] = 1;
     stats->candidates = ro.cand;
     stats->steiner_inserted = ro.ins;
     stats->rejected = ro.rej;
@@ -1078,6 +1212,7 @@ int cdr_round(cdr_handle* h, double B, int32_t* cls, cdr_stats* stats) {
 
 int cdr_refine(cdr_handle* h, double B, int32_t max_rounds, cdr_stats* stats) {
   if (!h || !(B > 0) || max_rounds < 0) return CDR_ERR_INVALID_INPUT;
+  if (h->batch) return CDR_ERR_INVALID_INPUT;
   if (h->err) return h->err;
   if (h->dt_mode) return CDR_ERR_INVALID_INPUT;
   cdr_stats acc;
@@ -1093,7 +1228,7 @@ int cdr_refine(cdr_handle* h, double B, int32_t max_rounds, cdr_stats* stats) {
       break;
     }
     acc.rounds++;
-    acc.rounds_by_class[ro.cls]++;
+    if (ro.cls < 3) acc.rounds_by_class[ro.cls]++;
     acc.candidates += ro.cand;
     acc.steiner_inserted += ro.ins;
     acc.rejected += ro.rej;
@@ -1279,6 +1414,7 @@ int cdr_round_report(cdr_handle* h, int32_t* n_cand, int64_t* n_cav_total, int32
 
 int cdr_checkpoint(cdr_handle* h) {
   if (!h) return CDR_ERR_INVALID_INPUT;
+  if (h->batch) return CDR_ERR_INVALID_INPUT;
   DevMesh& m = h->m;
   struct {
     Buf* b;
@@ -1308,6 +1444,7 @@ int cdr_checkpoint(cdr_handle* h) {
   }
   h->ckm = m;
   h->ck_hcount = h->hcount;
+  h->ck_deadT = h->deadT;
   h->has_ck = true;
   cudaStreamSynchronize(h->stream);
   return cuda_status(h);
@@ -1315,6 +1452,7 @@ int cdr_checkpoint(cdr_handle* h) {
 
 int cdr_restore(cdr_handle* h) {
   if (!h || !h->has_ck) return CDR_ERR_INVALID_INPUT;
+  if (h->batch) return CDR_ERR_INVALID_INPUT;
   DevMesh c = h->ckm;
   if (!grow_verts(h, c.nV) || !grow_tets(h, c.nT) || !grow_subfaces(h, c.nS) ||
       !grow_subsegs(h, c.nG))
@@ -1332,6 +1470,9 @@ int cdr_restore(cdr_handle* h) {
   m.nG = c.nG;
   m.hmask = c.hmask;
   h->hcount = h->ck_hcount;
+  h->deadT = h->ck_deadT;
+  h->deadKnown = true;
+  h->fullClassify = true;
   h->lastB = -1.0;
   h->lastN = 0;
   h->err = 0;
@@ -1467,6 +1608,339 @@ int cdr_delaunay_box(const double* xyz, int32_t n, const cdr_options* opt,
   }
   *out = h;
   return CDR_OK;
+}
+
+// ===================================================================== batches
+int cdr_batch_create(const cdr_options* opt, const cdr_allocator* alloc, void* stream,
+                     cdr_handle** out) {
+  if (!out) return CDR_ERR_INVALID_INPUT;
+  *out = nullptr;
+  cdr_handle* h = new (std::nothrow) cdr_handle();
+  if (!h) return CDR_ERR_OOM;
+  h->stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    h->alloc = *alloc;
+    h->has_alloc = true;
+  }
+  h->batch = true;
+  h->ninst = 0;
+  if (opt) h->opts = *opt;
+  h->opts.reserve_factor = 1;  // an instance is built at its own size, then appended
+  h->m.walk_limit = (opt && opt->walk_limit > 0) ? opt->walk_limit : 100000;
+  h->m.nV = h->m.nT = h->m.nS = h->m.nG = h->m.nF = 0;
+  if (!grow_verts(h, 4096) || !grow_tets(h, 16384) || !grow_subfaces(h, 4096) ||
+      !grow_subsegs(h, 1024) || !rebuild_hash(h, 1024) || !ensure(h, h->bFQ, 64 * sizeof(V4)) ||
+      !ensure_instances(h, 16) || !ensure_pinned(h)) {
+    int e = h->err ? h->err : CDR_ERR_OOM;
+    cdr_destroy(h);
+    return e;
+  }
+  bind(h);
+  int st = cuda_status(h);
+  if (st) {
+    cdr_destroy(h);
+    return st;
+  }
+  *out = h;
+  return CDR_OK;
+}
+
+int cdr_batch_add(cdr_handle* h, const cdr_mesh_in* in, double B, int32_t* slot) {
+  if (!h || !h->batch || !in || !(B > 0) || !slot) return CDR_ERR_INVALID_INPUT;
+  if (h->err) return h->err;
+  *slot = -1;
+  cdr_allocator al = h->alloc;
+  cdr_handle* t = nullptr;
+  int st = cdr_create(in, &h->opts, h->has_alloc ? &al : nullptr, h->stream, &t);
+  if (st) return st;
+  DevMesh& d = h->m;
+  const DevMesh& sm = t->m;
+  if ((long)d.nV + sm.nV >= kMaxVerts || (long)d.nT + sm.nT >= kMaxTets / 8) {
+    cdr_destroy(t);
+    return CDR_ERR_OOM;
+  }
+  int k;
+  if (!h->freeSlots.empty()) {
+    k = h->freeSlots.back();
+    h->freeSlots.pop_back();
+  } else {
+    k = h->ninst++;
+    h->insts.emplace_back();
+  }
+  if (!ensure_instances(h, h->ninst) || !grow_verts(h, d.nV + sm.nV) ||
+      !grow_tets(h, d.nT + sm.nT) || !grow_subfaces(h, d.nS + sm.nS) ||
+      !grow_subsegs(h, d.nG + sm.nG) ||
+      !ensure(h, h->bFQ, (size_t)(d.nF + sm.nF + 1) * sizeof(V4), (size_t)d.nF * sizeof(V4))) {
+    cdr_destroy(t);
+    return h->err ? h->err : CDR_ERR_OOM;
+  }
+  bind(h);
+  int nseg = 0;
+  for (int i = 0; i < in->n_segs; ++i) nseg = std::max(nseg, in->seg_id[i] + 1);
+  launch_append(d, sm, d.nV, d.nT, d.nS, d.nG, d.nF, h->segIds, k, h->stream);
+  const double b = B, g2 = sm.guard2;
+  cudaMemcpyAsync(ptr<double>(h->bInstB) + k, &b, 8, cudaMemcpyHostToDevice, h->stream);
+  cudaMemcpyAsync(ptr<double>(h->bInstG2) + k, &g2, 8, cudaMemcpyHostToDevice, h->stream);
+  const int g0 = d.nG;
+  cdr_handle::Inst& I = h->insts[k];
+  I = cdr_handle::Inst();
+  I.state = 1;
+  I.of = d.nF;
+  I.nf = sm.nF;
+  I.oseg = h->segIds;
+  I.nseg = nseg;
+  I.B = B;
+  d.nV += sm.nV;
+  d.nT += sm.nT;
+  d.nS += sm.nS;
+  d.nG += sm.nG;
+  d.nF += sm.nF;
+  h->segIds += nseg;
+  if ((size_t)(h->hcount + sm.nG) * 2 > (size_t)d.hmask + 1) {
+    if (!rebuild_hash(h, d.nG * 2)) {
+      cdr_destroy(t);
+      return CDR_ERR_OOM;
+    }
+  } else {
+    launch_hash_insert_subsegs(d, g0, d.nG, h->stream);
+    h->hcount += sm.nG;
+  }
+  launch_recompute_bad(d, 0.0, h->stream);  // per-instance bounds
+  h->fullClassify = true;
+  cudaStreamSynchronize(h->stream);
+  cdr_destroy(t);
+  st = cuda_status(h);
+  if (!st) *slot = k;
+  return st;
+}
+
+int cdr_batch_round(cdr_handle* h, int32_t* n_active) {
+  if (!h || !h->batch) return CDR_ERR_INVALID_INPUT;
+  if (h->err) return h->err;
+  if (n_active) *n_active = 0;
+  if (h->ninst == 0) return CDR_OK;
+  RoundOut ro;
+  int st = refine_round(h, 1.0, &ro);
+  if (st) return st;
+  int active = 0;
+  const bool ran = ro.cand > 0;
+  for (int k = 0; k < h->ninst; ++k) {
+    cdr_handle::Inst& I = h->insts[k];
+    if (I.state != 1) continue;
+    int c = k < (int)h->instCls.size() ? h->instCls[k] : -1;
+    if (c < 0) {
+      I.state = 2;
+      continue;
+    }
+    ++active;
+    I.st.rounds++;
+    I.st.rounds_by_class[c]++;
+    I.st.candidates += (long long)h->pinCnt[3 * k + c];
+    if (ran) {
+      const unsigned long long* q = h->pinSt + (size_t)k * IS_COUNT;
+      I.st.steiner_inserted += (long long)q[IS_SURV];
+      I.st.rejected += (long long)q[IS_REJECT] - (long long)q[IS_STALLED];
+      I.st.unsplittable += (long long)q[IS_UNSPL] + (long long)q[IS_STALLED];
+    }
+  }
+  if (n_active) *n_active = active;
+  return CDR_OK;
+}
+
+int cdr_batch_refine(cdr_handle* h, int32_t max_rounds, int32_t* rounds) {
+  if (!h || !h->batch || max_rounds < 0) return CDR_ERR_INVALID_INPUT;
+  int r = 0, st = CDR_OK, active = 1;
+  while (r < max_rounds) {
+    st = cdr_batch_round(h, &active);
+    if (st || active == 0) break;
+    ++r;
+  }
+  if (rounds) *rounds = r;
+  if (!st && active > 0) st = CDR_ROUND_LIMIT;
+  return st;
+}
+
+namespace {
+// live entries of instance k of one kind (0 vertices, 1 tets, 2 subfaces,
+// 3 subsegments, 4 bad tets left) and, if pos is given, their positions
+int inst_count(cdr_handle* h, int k, int kind, Buf* flag, Buf* pos, int* out) {
+  DevMesh& m = h->m;
+  int n = kind == 0 ? m.nV : (kind == 1 || kind == 4 ? m.nT : (kind == 2 ? m.nS : m.nG));
+  *out = 0;
+  if (n == 0) return CDR_OK;
+  Buf f;
+  if (!ensure(h, f, (size_t)n * 4 + 64) || !ensure(h, h->bErr, 64)) return CDR_ERR_OOM;
+  launch_inst_flags(m, k, kind == 4 ? 1 : kind, n, ptr<int>(f), h->stream);
+  if (kind == 4) launch_inst_bad(m, ptr<int>(f), n, h->stream);
+  int* sum = ptr<int>(h->bErr) + 8;
+  size_t tb = 0;
+  cub::DeviceReduce::Sum(nullptr, tb, ptr<int>(f), sum, n, h->stream);
+  if (!tmp_ensure(h, tb)) return CDR_ERR_OOM;
+  tb = h->bTmp.bytes;
+  cub::DeviceReduce::Sum(h->bTmp.p, tb, ptr<int>(f), sum, n, h->stream);
+  if (pos) {
+    if (!ensure(h, *pos, (size_t)n * 4 + 64)) return CDR_ERR_OOM;
+    size_t tb2 = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb2, ptr<int>(f), ptr<int>(*pos), n, h->stream);
+    if (!tmp_ensure(h, tb2)) return CDR_ERR_OOM;
+    tb2 = h->bTmp.bytes;
+    cub::DeviceScan::ExclusiveSum(h->bTmp.p, tb2, ptr<int>(f), ptr<int>(*pos), n, h->stream);
+  }
+  cudaMemcpyAsync(&h->pin->n2, sum, 4, cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  *out = h->pin->n2;
+  if (flag) {
+    dfree(h, *flag);
+    *flag = f;
+  } else {
+    dfree(h, f);
+  }
+  return cuda_status(h);
+}
+}  // namespace
+
+int cdr_batch_stats(cdr_handle* h, int32_t slot, cdr_stats* stats, int32_t* state) {
+  if (!h || !h->batch || slot < 0 || slot >= h->ninst) return CDR_ERR_INVALID_INPUT;
+  const cdr_handle::Inst& I = h->insts[slot];
+  if (state) *state = I.state;
+  if (stats) {
+    *stats = I.st;
+    if (I.state != 0 && ensure_pinned(h)) {
+      int nv = 0, nt = 0, ns = 0, ng = 0, nb = 0;
+      int st = inst_count(h, slot, 0, nullptr, nullptr, &nv);
+      if (!st) st = inst_count(h, slot, 1, nullptr, nullptr, &nt);
+      if (!st) st = inst_count(h, slot, 2, nullptr, nullptr, &ns);
+      if (!st) st = inst_count(h, slot, 3, nullptr, nullptr, &ng);
+      if (!st) st = inst_count(h, slot, 4, nullptr, nullptr, &nb);
+      if (st) return st;
+      stats->n_verts = nv;
+      stats->n_tets = nt;
+      stats->n_subfaces = ns;
+      stats->n_subsegs = ng;
+      stats->n_bad_left = nb;
+    }
+  }
+  return CDR_OK;
+}
+
+int cdr_batch_export_sizes(cdr_handle* h, int32_t slot, cdr_sizes* out) {
+  if (!h || !h->batch || !out || slot < 0 || slot >= h->ninst || h->insts[slot].state == 0)
+    return CDR_ERR_INVALID_INPUT;
+  if (!ensure_pinned(h)) return CDR_ERR_OOM;
+  int nv = 0, nt = 0, ns = 0, ng = 0;
+  int st = inst_count(h, slot, 0, nullptr, nullptr, &nv);
+  if (!st) st = inst_count(h, slot, 1, nullptr, nullptr, &nt);
+  if (!st) st = inst_count(h, slot, 2, nullptr, nullptr, &ns);
+  if (!st) st = inst_count(h, slot, 3, nullptr, nullptr, &ng);
+  if (st) return st;
+  out->n_verts = nv;
+  out->n_tets = nt;
+  out->n_subfaces = ns;
+  out->n_subsegs = ng;
+  out->n_facets = h->insts[slot].nf;
+  return CDR_OK;
+}
+
+int cdr_batch_export(cdr_handle* h, int32_t slot, const cdr_mesh_out* out) {
+  if (!h || !h->batch || !out || slot < 0 || slot >= h->ninst || h->insts[slot].state == 0)
+    return CDR_ERR_INVALID_INPUT;
+  if (!ensure_pinned(h)) return CDR_ERR_OOM;
+  DevMesh& m = h->m;
+  cudaStream_t s = h->stream;
+  const cdr_handle::Inst& I = h->insts[slot];
+  Buf vflag, vpos;
+  int nv = 0;
+  int st = inst_count(h, slot, 0, &vflag, &vpos, &nv);
+  if (st) return st;
+  Buf dense;
+  if (!ensure(h, dense, (size_t)std::max(nv, 1) * sizeof(V4))) return CDR_ERR_OOM;
+  launch_inst_gather(m, 0, m.nV, ptr<int>(vflag), ptr<int>(vpos), ptr<int>(vpos), 0, 0, nullptr,
+                     nullptr, ptr<V4>(dense), s);
+  if (out->xyz && nv > 0) {
+    std::vector<V4> v(nv);
+    cudaMemcpyAsync(v.data(), dense.p, (size_t)nv * sizeof(V4), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (int i = 0; i < nv; ++i) {
+      out->xyz[3 * i] = v[i].x;
+      out->xyz[3 * i + 1] = v[i].y;
+      out->xyz[3 * i + 2] = v[i].z;
+    }
+  }
+  dfree(h, dense);
+  dfree(h, vflag);
+  for (int kind = 1; kind <= 3; ++kind) {
+    Buf f, pos;
+    int live = 0;
+    st = inst_count(h, slot, kind, &f, &pos, &live);
+    if (st) return st;
+    int n = kind == 1 ? m.nT : (kind == 2 ? m.nS : m.nG);
+    Buf d4, d1;
+    if (!ensure(h, d4, (size_t)std::max(live, 1) * 16) || !ensure(h, d1, (size_t)std::max(live, 1)))
+      return CDR_ERR_OOM;
+    launch_inst_gather(m, kind, n, ptr<int>(f), ptr<int>(pos), ptr<int>(vpos), I.of, I.oseg,
+                       ptr<int4>(d4), ptr<uint8_t>(d1), nullptr, s);
+    std::vector<int4> d(live);
+    std::vector<uint8_t> fl(live);
+    if (live) {
+      cudaMemcpyAsync(d.data(), d4.p, (size_t)live * 16, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(fl.data(), d1.p, (size_t)live, cudaMemcpyDeviceToHost, s);
+    }
+    cudaStreamSynchronize(s);
+    dfree(h, f);
+    dfree(h, pos);
+    dfree(h, d4);
+    dfree(h, d1);
+    for (int i = 0; i < live; ++i) {
+      if (kind == 1) {
+        if (out->tets) {
+          out->tets[4 * i] = d[i].x;
+          out->tets[4 * i + 1] = d[i].y;
+          out->tets[4 * i + 2] = d[i].z;
+          out->tets[4 * i + 3] = d[i].w;
+        }
+        if (out->tet_flag) out->tet_flag[i] = fl[i];
+      } else if (kind == 2) {
+        if (out->subfaces) {
+          out->subfaces[4 * i] = d[i].x;
+          out->subfaces[4 * i + 1] = d[i].y;
+          out->subfaces[4 * i + 2] = d[i].z;
+          out->subfaces[4 * i + 3] = d[i].w;
+        }
+        if (out->subface_flag) out->subface_flag[i] = fl[i];
+      } else {
+        if (out->subsegs) {
+          out->subsegs[3 * i] = d[i].x;
+          out->subsegs[3 * i + 1] = d[i].y;
+          out->subsegs[3 * i + 2] = d[i].z;
+        }
+        if (out->subseg_flag) out->subseg_flag[i] = fl[i];
+      }
+    }
+  }
+  dfree(h, vpos);
+  if (out->facet_ref && I.nf > 0) {
+    std::vector<V4> q(I.nf);
+    cudaMemcpyAsync(q.data(), m.FQ + I.of, (size_t)I.nf * sizeof(V4), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (int f = 0; f < I.nf; ++f) {
+      out->facet_ref[3 * f] = q[f].x;
+      out->facet_ref[3 * f + 1] = q[f].y;
+      out->facet_ref[3 * f + 2] = q[f].z;
+    }
+  }
+  return cuda_status(h);
+}
+
+int cdr_batch_remove(cdr_handle* h, int32_t slot) {
+  if (!h || !h->batch || slot < 0 || slot >= h->ninst || h->insts[slot].state == 0)
+    return CDR_ERR_INVALID_INPUT;
+  launch_kill_instance(h->m, slot, h->stream);
+  cudaStreamSynchronize(h->stream);
+  h->deadKnown = false;
+  h->fullClassify = true;
+  h->insts[slot] = cdr_handle::Inst();
+  h->freeSlots.push_back(slot);
+  return cuda_status(h);
 }
 
 int cdr_eval_predicates(int32_t kind, const double* in, int32_t n, int32_t* sign, double* out,

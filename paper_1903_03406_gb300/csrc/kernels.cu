@@ -20,6 +20,15 @@ namespace cdr {
 
 #define FULLMASK 0xffffffffu
 
+// grid for n items of `block` threads, at most 32 blocks per SM (152 SMs);
+// kernels stride over the rest
+static inline int grid_for(long n, int block) {
+  long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)g;
+}
+
 // Checked build (CDR_CHECKED): every mesh-array index is bounds-checked; a bad
 // index is recorded (site = source line, index, bound) and replaced by 0 so
 // that nothing is read or written out of bounds.
@@ -157,6 +166,21 @@ __device__ __forceinline__ bool sf_incircle(const DevMesh& m, int4 S, D3 p) {
 
 __device__ __forceinline__ void set_status(const DevRound& r, int i, int outcome, int reason) {
   r.status[i] = outcome | (reason << 8);
+}
+// class and instance of candidate i; instance of vertex v; per-instance bound
+// and shortest-edge guard
+__device__ __forceinline__ int cls_of(const DevRound& r, int i) {
+  return r.ccls ? (int)r.ccls[i] : r.cls;
+}
+__device__ __forceinline__ int inst_of(const DevRound& r, int i) {
+  return r.cinst ? r.cinst[i] : 0;
+}
+__device__ __forceinline__ int vinst(const DevMesh& m, int v) { return m.Vinst ? m.Vinst[v] : 0; }
+__device__ __forceinline__ double bound_of(const DevMesh& m, double B, int inst) {
+  return m.instB ? m.instB[inst] : B;
+}
+__device__ __forceinline__ double guard2_of(const DevMesh& m, int inst) {
+  return m.instG2 ? m.instG2[inst] : m.guard2;
 }
 
 // ================================================================= create
@@ -325,8 +349,10 @@ __global__ void k_recompute_bad(DevMesh m, double B) {
     int4 v = m.T[CKI(t, m.capT)].v;
     int s[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
     sort4(s);
-    bool bad = tet_bad_fixed(vtx(m, s[0]), vtx(m, s[1]), vtx(m, s[2]), vtx(m, s[3]), B);
+    const double Bt = bound_of(m, B, vinst(m, s[0]));
+    bool bad = tet_bad_fixed(vtx(m, s[0]), vtx(m, s[1]), vtx(m, s[2]), vtx(m, s[3]), Bt);
     m.Tflag[CKI(t, m.capT)] = bad ? (f | F_BAD) : (f & ~F_BAD);
+    m.candT[CKI(t, m.capT)] = (bad && !(f & F_UNSPL)) ? 1 : 0;
   }
 }
 
@@ -376,12 +402,22 @@ __device__ bool edge_ring(const DevMesh& m, int t0, int a, int b, F visit) {
   return true;
 }
 
-__global__ void k_classify(DevMesh m, unsigned char* candS, unsigned char* candG,
-                           unsigned char* candT, int* err) {
-  int n = m.nG + m.nS + m.nT;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+// Classification (Sec. 2's split order: encroached subsegments, encroached
+// subfaces, bad tetrahedra). Incremental: only subsegments and subfaces marked
+// dirty (created or touched by the last round, or flagged since) are tested;
+// tetrahedra get their flag when they are created or retired. full: test all.
+__global__ void k_classify(DevMesh m, int full, int* err) {
+  unsigned char* candS = m.candS;
+  unsigned char* candG = m.candG;
+  unsigned char* candT = m.candT;
+  long n = (long)m.nG + m.nS + (full ? m.nT : 0);
+  for (long ii = (long)blockIdx.x * blockDim.x + threadIdx.x; ii < n;
+       ii += (long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
     if (i < m.nG) {
       int g = i;
+      if (!full && !m.dirtyG[g]) continue;
+      m.dirtyG[g] = 0;
       uint8_t f = m.Gflag[CKI(g, m.capG)];
       if (f & (F_DEAD | F_UNSPL)) {
         candG[g] = 0;
@@ -405,6 +441,8 @@ __global__ void k_classify(DevMesh m, unsigned char* candS, unsigned char* candG
       candG[g] = enc ? 1 : 0;
     } else if (i < m.nG + m.nS) {
       int s = i - m.nG;
+      if (!full && !m.dirtyS[s]) continue;
+      m.dirtyS[s] = 0;
       uint8_t f = m.Sflag[CKI(s, m.capS)];
       if (f & (F_DEAD | F_UNSPL)) {
         candS[s] = 0;
@@ -466,15 +504,44 @@ __device__ int elem_key(const DevMesh& m, int cls, int e, int* ids) {
   return 1;
 }
 
+// Candidates of a round in which each instance serves its own class are listed
+// by their index in the concatenation (subsegments | subfaces | tetrahedra).
+__device__ __forceinline__ int decode_cand(const DevMesh& m, int idx, int& cls) {
+  if (idx < m.nG) {
+    cls = CLS_SUBSEG;
+    return idx;
+  }
+  if (idx < m.nG + m.nS) {
+    cls = CLS_SUBFACE;
+    return idx - m.nG;
+  }
+  cls = CLS_TET;
+  return idx - m.nG - m.nS;
+}
+
+// Priorities. cls >= 0: elems are element ids of that class; cls < 0: they are
+// concatenated indices.
 __global__ void k_prio(DevMesh m, int cls, const int* elems, int n, unsigned long long* keys) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c = cls;
+    int e = cls >= 0 ? elems[i] : decode_cand(m, elems[i], c);
     int ids[4];
-    int k = elem_key(m, cls, elems[i], ids);
-    keys[i] = prio_hash(cls, ids, k);
+    int k = elem_key(m, c, e, ids);
+    if (c == CLS_POINT) {
+      keys[i] = prio_hash(c, ids, k);
+    } else {
+      uint64_t h = 0x9E3779B97F4A7C15ULL * (uint64_t)(c + 1);
+      for (int q = 0; q < k; ++q) {
+        V4 v = m.V[CKI(ids[q], m.capV)];
+        h = prio_hash_step(prio_hash_step(prio_hash_step(h, v.x), v.y), v.z);
+      }
+      keys[i] = h;
+    }
   }
 }
 
-// Equal priority hashes (practically never): order the run by the sorted ids.
+// Equal priority hashes (practically never): order the run by class, then by
+// the sorted vertex ids.
 __global__ void k_tiefix(DevMesh m, int cls, const unsigned long long* keys, int* elems, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     bool start = (i == 0 || keys[i - 1] != keys[i]) && (i + 1 < n && keys[i + 1] == keys[i]);
@@ -483,15 +550,23 @@ __global__ void k_tiefix(DevMesh m, int cls, const unsigned long long* keys, int
     while (j < n && keys[j] == keys[i]) ++j;
     for (int a = i + 1; a < j; ++a)
       for (int b = a; b > i; --b) {
-        int x[4], y[4];
-        int nk = elem_key(m, cls, elems[b - 1], x);
-        elem_key(m, cls, elems[b], y);
-        bool lt = false, eq = true;
-        for (int q = 0; q < nk && eq; ++q)
-          if (y[q] != x[q]) {
-            lt = y[q] < x[q];
-            eq = false;
-          }
+        int cx = cls, cy = cls;
+        int ex = cls >= 0 ? elems[b - 1] : decode_cand(m, elems[b - 1], cx);
+        int ey = cls >= 0 ? elems[b] : decode_cand(m, elems[b], cy);
+        bool lt = false;
+        if (cx != cy) {
+          lt = cy < cx;
+        } else {
+          int x[4], y[4];
+          int nk = elem_key(m, cx, ex, x);
+          elem_key(m, cy, ey, y);
+          bool eq = true;
+          for (int q = 0; q < nk && eq; ++q)
+            if (y[q] != x[q]) {
+              lt = y[q] < x[q];
+              eq = false;
+            }
+        }
         if (!lt) break;
         int t = elems[b];
         elems[b] = elems[b - 1];
@@ -500,21 +575,92 @@ __global__ void k_tiefix(DevMesh m, int cls, const unsigned long long* keys, int
   }
 }
 
+// concatenated indices (in priority order) -> element ids, classes, instances
+__global__ void k_decode_cands(DevMesh m, int* cand, uint8_t* ccls, int* cinst, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c;
+    int e = decode_cand(m, cand[i], c);
+    int v0 = c == CLS_SUBSEG ? m.GV[CKI(e, m.capG)].x
+                             : (c == CLS_SUBFACE ? m.SV[CKI(e, m.capS)].x : vid(m.T[CKI(e, m.capT)].v.x));
+    cand[i] = e;
+    ccls[i] = (uint8_t)c;
+    cinst[i] = vinst(m, v0);
+  }
+}
+
+// Per-instance classification counts over the concatenated index space (lanes
+// with the same instance and class add together).
+__global__ void k_count_inst(DevMesh m, const uint8_t* candG, const uint8_t* candS,
+                             const uint8_t* candT) {
+  const long tot = (long)m.nG + m.nS + m.nT;
+  const long stride = (long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (long base = (long)blockIdx.x * blockDim.x; base < tot; base += stride) {
+    long i = base + threadIdx.x;
+    int key = -1;
+    if (i < tot) {
+      int c;
+      int e = decode_cand(m, (int)i, c);
+      bool f;
+      int v0;
+      if (c == CLS_SUBSEG) {
+        f = candG[e] != 0;
+        v0 = f ? m.GV[CKI(e, m.capG)].x : 0;
+      } else if (c == CLS_SUBFACE) {
+        f = candS[e] != 0;
+        v0 = f ? m.SV[CKI(e, m.capS)].x : 0;
+      } else {
+        f = candT[e] != 0;
+        v0 = f ? vid(m.T[CKI(e, m.capT)].v.x) : 0;
+      }
+      if (f) key = vinst(m, v0) * 3 + c;
+    }
+    unsigned grp = __match_any_sync(FULLMASK, key);
+    if (key >= 0 && (__ffs(grp) - 1) == lane)
+      atomicAdd(&m.instCnt[key], (unsigned long long)__popc(grp));
+  }
+}
+
+// This round's candidates: flagged elements of the class their instance serves.
+__global__ void k_round_flags(DevMesh m, const uint8_t* candG, const uint8_t* candS,
+                              const uint8_t* candT, uint8_t* out) {
+  const long tot = (long)m.nG + m.nS + m.nT;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+       i += (long)gridDim.x * blockDim.x) {
+    int c;
+    int e = decode_cand(m, (int)i, c);
+    bool f;
+    int v0 = 0;
+    if (c == CLS_SUBSEG) {
+      f = candG[e] != 0;
+      if (f) v0 = m.GV[CKI(e, m.capG)].x;
+    } else if (c == CLS_SUBFACE) {
+      f = candS[e] != 0;
+      if (f) v0 = m.SV[CKI(e, m.capS)].x;
+    } else {
+      f = candT[e] != 0;
+      if (f) v0 = vid(m.T[CKI(e, m.capT)].v.x);
+    }
+    out[i] = (f && m.instCls[vinst(m, v0)] == c) ? 1 : 0;
+  }
+}
+
 // ============================================================ split + locate
 __global__ void k_split(DevMesh m, DevRound r) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
     int e = r.cand[i];
+    const int cls = cls_of(r, i);
     D3 p{0, 0, 0};
     bool ok = true;
-    if (r.cls == CLS_SUBSEG) {
+    if (cls == CLS_SUBSEG) {
       int4 G = m.GV[CKI(e, m.capG)];
       p = midpoint_fixed(vtx(m, min(G.x, G.y)), vtx(m, max(G.x, G.y)));
       ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
-    } else if (r.cls == CLS_SUBFACE) {
+    } else if (cls == CLS_SUBFACE) {
       int ids[4];
       elem_key(m, CLS_SUBFACE, e, ids);
       ok = tri_circumcenter_fixed(vtx(m, ids[0]), vtx(m, ids[1]), vtx(m, ids[2]), p);
-    } else if (r.cls == CLS_TET) {
+    } else if (cls == CLS_TET) {
       int ids[4];
       elem_key(m, CLS_TET, e, ids);
       D3 off;
@@ -536,10 +682,11 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
     if (r.status[i] != OUT_OK) continue;
     int e = r.cand[i];
+    const int cls = cls_of(r, i);
     V4 q = r.sp[i];
     D3 p{q.x, q.y, q.z};
-    if (r.cls == CLS_TET || r.cls == CLS_POINT) {
-      int t = r.cls == CLS_TET ? e : hint[e];
+    if (cls == CLS_TET || cls == CLS_POINT) {
+      int t = cls == CLS_TET ? e : hint[e];
       bool done = false;
       for (int it = 0; it < m.walk_limit && !done; ++it) {
         TetRec rec = ld_tet(m, t);
@@ -591,7 +738,7 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
         t = n >> 2;
       }
       if (!done) set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
-    } else if (r.cls == CLS_SUBFACE) {
+    } else if (cls == CLS_SUBFACE) {
       int s = e;
       bool done = false;
       for (int it = 0; it < m.walk_limit && !done; ++it) {
@@ -644,9 +791,10 @@ __global__ void k_seed(DevMesh m, DevRound r) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
     if (r.status[i] != OUT_OK) continue;
     const unsigned long long mk = (r.seed_epoch << 32) | (unsigned long long)(unsigned)i;
-    if (r.cls == CLS_TET || r.cls == CLS_POINT) {
+    const int cls = cls_of(r, i);
+    if (cls == CLS_TET || cls == CLS_POINT) {
       atomicMin(&m.Tseed[CKI(r.loc[i], m.capT)], mk);
-    } else if (r.cls == CLS_SUBFACE) {
+    } else if (cls == CLS_SUBFACE) {
       int tf = m.SN[CKI(r.loc[i], m.capS)].w;
       if (tf < 0) continue;
       atomicMin(&m.Tseed[CKI(tf >> 2, m.capT)], mk);
@@ -728,11 +876,23 @@ __device__ __forceinline__ void wappend(int* list, int& n, int cap, bool pred, i
   n += __popc(b);
 }
 
+// work counters of one warp's regions, added to the round totals once per warp
+struct GrowAcc {
+  unsigned long long tested = 0, cav = 0, bnd = 0;
+};
+__device__ __forceinline__ void flush_acc(const DevRound& r, const GrowAcc& a, int lane) {
+  if (lane == 0) {
+    if (a.tested) atomicAdd(&r.stats[ST_TESTED], a.tested);
+    if (a.cav) atomicAdd(&r.stats[ST_CAV], a.cav);
+    if (a.bnd) atomicAdd(&r.stats[ST_BND], a.bnd);
+  }
+}
+
 template <class C>
 __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w, int* slab,
-                         int lane) {
+                         int lane, GrowAcc& acc) {
   using L = SlabLayout<C>;
-  const int cls = r.cls;
+  const int cls = cls_of(r, i);
   int st = r.status[i];
   if (st != OUT_OK && st != OUT_RETRY) {
     if (lane == 0) {
@@ -1219,6 +1379,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   }
   // ------------------------------------------------ shortest-edge guard
   {
+    const double g2 = guard2_of(m, inst_of(r, i));
     bool g = false;
     int items = ncav * 4;
     for (int base = 0; base < items; base += 32) {
@@ -1226,7 +1387,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       bool near = false;
       if (it < items) {
         int v = vid(geti(m.T[CKI(w.cav[it >> 2], m.capT)].v, it & 3));
-        near = dist2_fixed(p, vtx(m, v)) <= m.guard2;
+        near = dist2_fixed(p, vtx(m, v)) <= g2;
       }
       g |= __any_sync(FULLMASK, near);
     }
@@ -1254,6 +1415,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
               if (s >= 0 && s < m.nS) {
                 un = (m.Sflag[CKI(s, m.capS)] & F_UNSPL) != 0;
                 m.Smust[CKI(s, m.capS)] = 1;
+                m.dirtyS[CKI(s, m.capS)] = 1;
               } else {
                 atomicAdd(&r.stats[ST_ITER], 1ULL);
               }
@@ -1292,7 +1454,11 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
                 flag = true;
                 un = (m.Gflag[CKI(g, m.capG)] & F_UNSPL) != 0;
                 m.Gmust[CKI(g, m.capG)] = 1;
-                if (r.candG && !r.candG[g]) atomicAdd(&r.stats[ST_NEWCAND], 1ULL);
+                m.dirtyG[CKI(g, m.capG)] = 1;
+                if (r.candG && cls == CLS_SUBSEG && !r.candG[g]) {
+                  atomicAdd(&r.stats[ST_NEWCAND], 1ULL);
+                  if (m.instSt) atomicAdd(&m.instSt[inst_of(r, i) * IS_COUNT + IS_NEWCAND], 1ULL);
+                }
               }
             }
           }
@@ -1324,12 +1490,10 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
 done:
   __syncwarp();
   for (int o = 16; o > 0; o >>= 1) ntested += __shfl_xor_sync(FULLMASK, ntested, o);
-  if (lane == 0) {
-    atomicAdd(&r.stats[ST_TESTED], (unsigned long long)ntested);
-    if (!retry) {
-      atomicAdd(&r.stats[ST_CAV], (unsigned long long)ncav);
-      atomicAdd(&r.stats[ST_BND], (unsigned long long)nbnd);
-    }
+  acc.tested += (unsigned long long)ntested;
+  if (!retry) {
+    acc.cav += (unsigned long long)ncav;
+    acc.bnd += (unsigned long long)nbnd;
   }
   if (blast) {
     if (lane == 0) {
@@ -1393,11 +1557,13 @@ __global__ void __launch_bounds__(32 * kWarps1) k_grow1(DevMesh m, DevRound r) {
   Ws w{sm->cav, sm->hset, sm->bin, sm->bout, sm->bv, sm->fcav, sm->fbnd, sm->fbv};
   int warp = blockIdx.x * kWarps1 + (threadIdx.x >> 5);
   int nw = gridDim.x * kWarps1;
+  GrowAcc acc;
   for (int i = warp; i < r.n; i += nw) {
     int* slab = r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
-    grow_one<Tier1>(m, r, i, w, slab, lane);
+    grow_one<Tier1>(m, r, i, w, slab, lane, acc);
     __syncwarp();
   }
+  flush_acc(r, acc, lane);
 }
 
 // tier 2: global-memory workspaces; the slab doubles as the list storage
@@ -1410,15 +1576,17 @@ __global__ void k_grow2(DevMesh m, DevRound r) {
   if (warp >= r.nws2) return;  // no workspace for this warp
   nw = min(nw, r.nws2);
   int* extra = r.ws2 + (size_t)warp * kWs2Extra;
+  GrowAcc acc;
   for (int j = warp; j < r.n2; j += nw) {
     int i = r.list2[j];
     int* slab = r.slab2 + (size_t)j * L::STRIDE;
     Ws w{slab + L::OFF_CAV, extra, slab + L::OFF_BIN, slab + L::OFF_BOUT,
          slab + L::OFF_BV, slab + L::OFF_FCAV, slab + L::OFF_FBND, slab + L::OFF_FBV};
-    grow_one<Tier2>(m, r, i, w, slab, lane);
+    grow_one<Tier2>(m, r, i, w, slab, lane, acc);
     __syncwarp();
     if (lane == 0 && r.status[i] == OUT_RETRY) set_status(r, i, OUT_UNSPL, RS_OVERFLOW);
   }
+  flush_acc(r, acc, lane);
 }
 
 // ============================================================== selection
@@ -1429,54 +1597,113 @@ __device__ __forceinline__ const int* slab_of(const DevRound& r, int i, bool& ti
   return r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
 }
 
+// Selection: a region is kept if it holds every mark it placed. One lane per
+// candidate; the warp checks the marks of each eligible candidate together.
+__device__ bool holds_marks(const DevMesh& m, const DevRound& r, int i, int lane) {
+  bool t2;
+  const int* slab = slab_of(r, i, t2);
+  int ncav = slab[0], nbnd = slab[1], nf = slab[2], nfb = slab[3];
+  int offC = t2 ? SlabLayout<Tier2>::OFF_CAV : SlabLayout<Tier1>::OFF_CAV;
+  int offBO = t2 ? SlabLayout<Tier2>::OFF_BOUT : SlabLayout<Tier1>::OFF_BOUT;
+  int offF = t2 ? SlabLayout<Tier2>::OFF_FCAV : SlabLayout<Tier1>::OFF_FCAV;
+  int offFB = t2 ? SlabLayout<Tier2>::OFF_FBND : SlabLayout<Tier1>::OFF_FBND;
+  const unsigned long long mk = (r.epoch << 32) | (unsigned long long)(unsigned)i;
+  bool lost = false;
+  for (int k = lane; k < ncav; k += 32) lost |= m.Tmark[CKI(slab[offC + k], m.capT)] != mk;
+  for (int k = lane; k < nbnd; k += 32) {
+    int b = slab[offBO + k];
+    if (b >= 0) lost |= m.Tmark[CKI(b >> 2, m.capT)] != mk;
+  }
+  for (int k = lane; k < nf; k += 32) lost |= m.Smark[CKI(slab[offF + k], m.capS)] != mk;
+  for (int k = lane; k < nfb; k += 32) {
+    int sk = slab[offFB + k];
+    int nb = sn_ptr(m, sk >> 2)[sk & 3];
+    if (nb >= 0) lost |= m.Smark[CKI(nb, m.capS)] != mk;
+  }
+  return !__any_sync(FULLMASK, lost);
+}
+
 __global__ void k_select(DevMesh m, DevRound r) {
   int lane = threadIdx.x & 31;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int i = warp; i < r.n; i += nw) {
-    int st = r.status[i];
-    int outcome = st & 0xff;
-    bool t2;
-    const int* slab = slab_of(r, i, t2);
-    int ncav = slab[0], nbnd = slab[1], nf = slab[2], nfb = slab[3];
-    int offC = t2 ? SlabLayout<Tier2>::OFF_CAV : SlabLayout<Tier1>::OFF_CAV;
-    int offBO = t2 ? SlabLayout<Tier2>::OFF_BOUT : SlabLayout<Tier1>::OFF_BOUT;
-    int offF = t2 ? SlabLayout<Tier2>::OFF_FCAV : SlabLayout<Tier1>::OFF_FCAV;
-    int offFB = t2 ? SlabLayout<Tier2>::OFF_FBND : SlabLayout<Tier1>::OFF_FBND;
+  // per-lane outcome counts: kept, eligible but lost, refused, blasted, unsplittable
+  unsigned c_surv = 0, c_ok = 0, c_rej = 0, c_blast = 0, c_unspl = 0;
+  for (int base = warp * 32; base < r.n; base += nw * 32) {
+    int i = base + lane;
+    int outcome = i < r.n ? (r.status[i] & 0xff) : -1;
     bool surv = false;
+    unsigned okm = __ballot_sync(FULLMASK, outcome == OUT_OK);
+    while (okm) {
+      int src = __ffs(okm) - 1;
+      okm &= okm - 1;
+      bool kept = holds_marks(m, r, base + src, lane);
+      if (lane == src) surv = kept;
+    }
+    // per-instance counts (lanes of one instance add together)
+    if (m.instSt) {
+      int key = i < r.n ? inst_of(r, i) : -1;
+      unsigned grp = __match_any_sync(FULLMASK, key);
+      bool leader = key >= 0 && (__ffs(grp) - 1) == lane;
+      unsigned sv = __ballot_sync(FULLMASK, surv) & grp;
+      unsigned un = __ballot_sync(FULLMASK, outcome == OUT_UNSPL) & grp;
+      unsigned rj = __ballot_sync(FULLMASK, outcome == OUT_REJECT) & grp;
+      if (leader) {
+        unsigned long long* q = m.instSt + (size_t)key * IS_COUNT;
+        if (sv) atomicAdd(&q[IS_SURV], (unsigned long long)__popc(sv));
+        if (un) atomicAdd(&q[IS_UNSPL], (unsigned long long)__popc(un));
+        if (rj) atomicAdd(&q[IS_REJECT], (unsigned long long)__popc(rj));
+      }
+    }
+    if (i >= r.n) continue;
+    const int cls = cls_of(r, i);
+    r.survived[i] = surv ? 1 : 0;
+    int4 c = make_int4(0, 0, 0, 0);
+    if (surv) {
+      bool t2;
+      const int* slab = slab_of(r, i, t2);
+      c = make_int4(cls == CLS_POINT ? 0 : 1, slab[1], slab[3], cls == CLS_SUBSEG ? 1 : 0);
+    }
+    r.counts[i] = c;
+    int e = r.cand[i];
+    if (outcome == OUT_UNSPL) {
+      if (cls == CLS_SUBSEG) {
+        m.Gflag[CKI(e, m.capG)] |= F_UNSPL;
+        m.dirtyG[CKI(e, m.capG)] = 1;
+      } else if (cls == CLS_SUBFACE) {
+        m.Sflag[CKI(e, m.capS)] |= F_UNSPL;
+        m.dirtyS[CKI(e, m.capS)] = 1;
+      } else if (cls == CLS_TET) {
+        m.Tflag[CKI(e, m.capT)] |= F_UNSPL;
+        m.candT[CKI(e, m.capT)] = 0;
+      } else {
+        r.point_state[e] = 2;
+      }
+    }
     if (outcome == OUT_OK) {
-      const unsigned long long mk = (r.epoch << 32) | (unsigned long long)(unsigned)i;
-      bool lost = false;
-      for (int k = lane; k < ncav; k += 32) lost |= m.Tmark[CKI(slab[offC + k], m.capT)] != mk;
-      for (int k = lane; k < nbnd; k += 32) {
-        int b = slab[offBO + k];
-        if (b >= 0) lost |= m.Tmark[CKI(b >> 2, m.capT)] != mk;
-      }
-      for (int k = lane; k < nf; k += 32) lost |= m.Smark[CKI(slab[offF + k], m.capS)] != mk;
-      for (int k = lane; k < nfb; k += 32) {
-        int sk = slab[offFB + k];
-        int nb = sn_ptr(m, sk >> 2)[sk & 3];
-        if (nb >= 0) lost |= m.Smark[CKI(nb, m.capS)] != mk;
-      }
-      surv = !__any_sync(FULLMASK, lost);
+      if (surv) ++c_surv;
+      else ++c_ok;
+    } else if (outcome == OUT_REJECT) {
+      ++c_rej;
+    } else if (outcome == OUT_BLASTED) {
+      ++c_blast;
+    } else {
+      ++c_unspl;
     }
-    if (lane == 0) {
-      r.survived[i] = surv ? 1 : 0;
-      int4 c = make_int4(0, 0, 0, 0);
-      if (surv) c = make_int4(r.cls == CLS_POINT ? 0 : 1, nbnd, nfb, r.cls == CLS_SUBSEG ? 1 : 0);
-      r.counts[i] = c;
-      int e = r.cand[i];
-      if (outcome == OUT_UNSPL) {
-        if (r.cls == CLS_SUBSEG) m.Gflag[CKI(e, m.capG)] |= F_UNSPL;
-        else if (r.cls == CLS_SUBFACE) m.Sflag[CKI(e, m.capS)] |= F_UNSPL;
-        else if (r.cls == CLS_TET) m.Tflag[CKI(e, m.capT)] |= F_UNSPL;
-        else r.point_state[e] = 2;
-      }
-      if (outcome == OUT_OK) atomicAdd(&r.stats[surv ? ST_SURV : ST_OK], 1ULL);
-      else if (outcome == OUT_REJECT) atomicAdd(&r.stats[ST_REJECT], 1ULL);
-      else if (outcome == OUT_BLASTED) atomicAdd(&r.stats[ST_BLAST], 1ULL);
-      else atomicAdd(&r.stats[ST_UNSPL], 1ULL);
-    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    c_surv += __shfl_xor_sync(FULLMASK, c_surv, o);
+    c_ok += __shfl_xor_sync(FULLMASK, c_ok, o);
+    c_rej += __shfl_xor_sync(FULLMASK, c_rej, o);
+    c_blast += __shfl_xor_sync(FULLMASK, c_blast, o);
+    c_unspl += __shfl_xor_sync(FULLMASK, c_unspl, o);
+  }
+  if (lane == 0) {
+    if (c_surv) atomicAdd(&r.stats[ST_SURV], (unsigned long long)c_surv);
+    if (c_ok) atomicAdd(&r.stats[ST_OK], (unsigned long long)c_ok);
+    if (c_rej) atomicAdd(&r.stats[ST_REJECT], (unsigned long long)c_rej);
+    if (c_blast) atomicAdd(&r.stats[ST_BLAST], (unsigned long long)c_blast);
+    if (c_unspl) atomicAdd(&r.stats[ST_UNSPL], (unsigned long long)c_unspl);
   }
 }
 
@@ -1503,17 +1730,25 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
 #undef SLAB_OFF
     const int4 off = r.offs[i];
     const int e = r.cand[i];
-    const int vp = r.cls == CLS_POINT ? e : m.nV + off.x;
+    const int cls = cls_of(r, i);
+    const int inst = inst_of(r, i);
+    const int vp = cls == CLS_POINT ? e : m.nV + off.x;
     const int t0 = m.nT + off.y;
     const int s0 = m.nS + off.z;
     int sa = -1, sb = -1;
-    if (r.cls == CLS_SUBSEG) {
+    if (cls == CLS_SUBSEG) {
       int4 G = m.GV[CKI(e, m.capG)];
       sa = G.x;
       sb = G.y;
     }
-    if (lane == 0 && r.cls != CLS_POINT) m.V[CKI(vp, m.capV)] = r.sp[i];
-    if (lane == 0) atomicAdd(&r.stats[ST_NEWT], (unsigned long long)nbnd);
+    if (lane == 0 && cls != CLS_POINT) {
+      m.V[CKI(vp, m.capV)] = r.sp[i];
+      if (m.Vinst) m.Vinst[CKI(vp, m.capV)] = inst;
+    }
+    if (lane == 0) {
+      atomicAdd(&r.stats[ST_NEWT], (unsigned long long)nbnd);
+      atomicAdd(&r.stats[ST_DEADT], (unsigned long long)ncav);
+    }
     // step 1: new tetrahedra (p replaces the vertex opposite each boundary face)
     for (int j = lane; j < nbnd; j += 32) {
       int t = bin[j] >> 2, f = bin[j] & 3;
@@ -1529,7 +1764,7 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
           mark = edge_bit(R.v, ed);
         } else {
           int other = vid(geti(R.v, a == f ? b : a));
-          mark = r.cls == CLS_SUBSEG && (other == sa || other == sb);
+          mark = cls == CLS_SUBSEG && (other == sa || other == sb);
         }
         if (mark) seti(nv, ed >> 1, geti(nv, ed >> 1) | (1 << (29 + (ed & 1))));
       }
@@ -1544,8 +1779,12 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       if (face_sub(R.v, f)) {
         int s = ts_ptr(m, t)[f];
         seti(ts, f, s);
-        if (s >= 0 && s < m.nS) m.SN[CKI(s, m.capS)].w = (nid << 2) | f;
-        else atomicAdd(&r.stats[ST_ITER], 1ULL);
+        if (s >= 0 && s < m.nS) {
+          m.SN[CKI(s, m.capS)].w = (nid << 2) | f;
+          m.dirtyS[CKI(s, m.capS)] = 1;  // one of its tetrahedra is new
+        } else {
+          atomicAdd(&r.stats[ST_ITER], 1ULL);
+        }
       }
       m.TS[CKI(nid, m.capT)] = ts;
       m.Tmark[CKI(nid, m.capT)] = ~0ULL;
@@ -1636,6 +1875,7 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       m.SN[CKI(ns, m.capS)] = sn;
       m.Sflag[CKI(ns, m.capS)] = 0;
       m.Smust[CKI(ns, m.capS)] = 0;
+      m.dirtyS[CKI(ns, m.capS)] = 1;
       m.Smark[CKI(ns, m.capS)] = ~0ULL;
     }
     __syncwarp();
@@ -1644,10 +1884,14 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       int t = cav[k];
       m.Tflag[CKI(t, m.capT)] |= F_DEAD;
       m.Tfwd[CKI(t, m.capT)] = t0;
+      if (m.candT) m.candT[CKI(t, m.capT)] = 0;
     }
-    for (int k = lane; k < nf; k += 32) m.Sflag[CKI(fcav[k], m.capS)] |= F_DEAD;
+    for (int k = lane; k < nf; k += 32) {
+      m.Sflag[CKI(fcav[k], m.capS)] |= F_DEAD;
+      if (m.candS) m.candS[CKI(fcav[k], m.capS)] = 0;
+    }
     // step 5: the split subsegment becomes (a, p) and (p, b)
-    if (r.cls == CLS_SUBSEG) {
+    if (cls == CLS_SUBSEG) {
       int ta = -1, tb = -1;
       for (int j = lane; j < nbnd; j += 32) {
         const int* F = bv + 3 * j;
@@ -1667,6 +1911,8 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
         m.Gmust[CKI(e, m.capG)] = 0;
         m.Gflag[CKI(g2, m.capG)] = 0;
         m.Gmust[CKI(g2, m.capG)] = 0;
+        m.dirtyG[CKI(e, m.capG)] = 1;
+        m.dirtyG[CKI(g2, m.capG)] = 1;
         hash_insert(m, ekey(G.x, vp), e);
         hash_insert(m, ekey(vp, G.y), g2);
       }
@@ -1681,18 +1927,168 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
         int a = vid(geti(v, edge_i(ed))), b = vid(geti(v, edge_j(ed)));
         if (a == vp || b == vp) continue;
         int g = hash_lookup(m, ekey(a, b));
-        if (g >= 0) m.GV[CKI(g, m.capG)].w = nid;
+        if (g >= 0) {
+          m.GV[CKI(g, m.capG)].w = nid;
+          if (m.dirtyG) m.dirtyG[CKI(g, m.capG)] = 1;  // its edge ring changed
+        }
       }
       int s4[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
       sort4(s4);
-      bool bad = tet_bad_fixed(vtx(m, s4[0]), vtx(m, s4[1]), vtx(m, s4[2]), vtx(m, s4[3]), r.B);
+      bool bad = tet_bad_fixed(vtx(m, s4[0]), vtx(m, s4[1]), vtx(m, s4[2]), vtx(m, s4[3]),
+                               bound_of(m, r.B, inst));
       m.Tflag[CKI(nid, m.capT)] = bad ? F_BAD : 0;
+      if (m.candT) m.candT[CKI(nid, m.capT)] = bad ? 1 : 0;
     }
-    if (lane == 0 && r.cls == CLS_POINT) {
+    if (lane == 0 && cls == CLS_POINT) {
       r.point_state[e] = 1;
       hint[e] = t0;
     }
   }
+}
+
+// ================================================================ batches
+// Append an instance built on its own (src) to the batch mesh d. Its ids move
+// by the batch's current sizes (vertices ov, tets ot, subfaces os, subsegments
+// og, facets of) and its segment ids by oseg; its vertices record the slot.
+__global__ void k_append(DevMesh d, DevMesh src, int ov, int ot, int os, int og, int of, int oseg,
+                         int slot) {
+  const long tot = max(max((long)src.nV, (long)src.nT), max(max((long)src.nS, (long)src.nG), (long)src.nF));
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+       i += (long)gridDim.x * blockDim.x) {
+    if (i < src.nV) {
+      d.V[CKI(ov + i, d.capV)] = src.V[i];
+      d.Vinst[CKI(ov + i, d.capV)] = slot;
+    }
+    if (i < src.nT) {
+      TetRec R = src.T[i];
+      for (int k = 0; k < 4; ++k) {
+        int v = geti(R.v, k);
+        seti(R.v, k, ((v & kVidMask) + ov) | (v & ~kVidMask));
+        int nb = geti(R.n, k);
+        if (nb >= 0) seti(R.n, k, (((nb >> 2) + ot) << 2) | (nb & 3));
+      }
+      const long t = ot + i;
+      d.T[CKI(t, d.capT)] = R;
+      int4 ts = src.TS[i];
+      for (int k = 0; k < 4; ++k)
+        if (geti(ts, k) >= 0) seti(ts, k, geti(ts, k) + os);
+      d.TS[CKI(t, d.capT)] = ts;
+      d.Tflag[CKI(t, d.capT)] = src.Tflag[i];
+      d.Tmark[CKI(t, d.capT)] = ~0ULL;
+      d.Tseed[CKI(t, d.capT)] = ~0ULL;
+      d.Tfwd[CKI(t, d.capT)] = -1;
+    }
+    if (i < src.nS) {
+      int4 sv = src.SV[i];
+      d.SV[CKI(os + i, d.capS)] = make_int4(sv.x + ov, sv.y + ov, sv.z + ov, sv.w + of);
+      int4 sn = src.SN[i];
+      for (int k = 0; k < 3; ++k)
+        if (geti(sn, k) >= 0) seti(sn, k, geti(sn, k) + os);
+      if (sn.w >= 0) sn.w = (((sn.w >> 2) + ot) << 2) | (sn.w & 3);
+      d.SN[CKI(os + i, d.capS)] = sn;
+      d.Sflag[CKI(os + i, d.capS)] = src.Sflag[i];
+      d.Smust[CKI(os + i, d.capS)] = src.Smust[i];
+      d.Smark[CKI(os + i, d.capS)] = ~0ULL;
+    }
+    if (i < src.nG) {
+      int4 g = src.GV[i];
+      d.GV[CKI(og + i, d.capG)] = make_int4(g.x + ov, g.y + ov, g.z + oseg, g.w >= 0 ? g.w + ot : -1);
+      d.Gflag[CKI(og + i, d.capG)] = src.Gflag[i];
+      d.Gmust[CKI(og + i, d.capG)] = src.Gmust[i];
+    }
+    if (i < src.nF) d.FQ[of + i] = src.FQ[i];
+  }
+}
+void launch_append(const DevMesh& d, const DevMesh& src, int ov, int ot, int os, int og, int of,
+                   int oseg, int slot, cudaStream_t s) {
+  long tot = max(max((long)src.nV, (long)src.nT), max(max((long)src.nS, (long)src.nG), (long)src.nF));
+  if (tot > 0) k_append<<<grid_for(tot, 256), 256, 0, s>>>(d, src, ov, ot, os, og, of, oseg, slot);
+}
+
+__device__ __forceinline__ int tet_inst(const DevMesh& m, int t) {
+  return vinst(m, vid(m.T[CKI(t, m.capT)].v.x));
+}
+// Remove an instance: its elements die; its vertices leave the slot (which can
+// then be reused).
+__global__ void k_kill_instance(DevMesh m, int slot) {
+  const long tot = (long)m.nT + m.nS + m.nG;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+       i += (long)gridDim.x * blockDim.x) {
+    if (i < m.nT) {
+      if (tet_inst(m, (int)i) == slot) m.Tflag[CKI(i, m.capT)] |= F_DEAD;
+    } else if (i < (long)m.nT + m.nS) {
+      int s = (int)(i - m.nT);
+      if (vinst(m, m.SV[CKI(s, m.capS)].x) == slot) m.Sflag[CKI(s, m.capS)] |= F_DEAD;
+    } else {
+      int g = (int)(i - m.nT - m.nS);
+      if (vinst(m, m.GV[CKI(g, m.capG)].x) == slot) m.Gflag[CKI(g, m.capG)] |= F_DEAD;
+    }
+  }
+}
+__global__ void k_release_vertices(DevMesh m, int slot) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m.nV; v += gridDim.x * blockDim.x)
+    if (m.Vinst[CKI(v, m.capV)] == slot) m.Vinst[CKI(v, m.capV)] = -1;
+}
+void launch_kill_instance(const DevMesh& m, int slot, cudaStream_t s) {
+  long tot = (long)m.nT + m.nS + m.nG;
+  if (tot > 0) k_kill_instance<<<grid_for(tot, 256), 256, 0, s>>>(m, slot);
+  if (m.nV > 0) k_release_vertices<<<grid_for(m.nV, 256), 256, 0, s>>>(m, slot);
+}
+
+// Export of one instance: flags of its vertices (kind 0), live tets (1),
+// subfaces (2) and subsegments (3) as 0/1 ints.
+__global__ void k_inst_flags(DevMesh m, int slot, int kind, int n, int* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    bool f;
+    if (kind == 0) f = m.Vinst[CKI(i, m.capV)] == slot;
+    else if (kind == 1) f = !(m.Tflag[CKI(i, m.capT)] & F_DEAD) && tet_inst(m, i) == slot;
+    else if (kind == 2) f = !(m.Sflag[CKI(i, m.capS)] & F_DEAD) && vinst(m, m.SV[CKI(i, m.capS)].x) == slot;
+    else f = !(m.Gflag[CKI(i, m.capG)] & F_DEAD) && vinst(m, m.GV[CKI(i, m.capG)].x) == slot;
+    out[i] = f ? 1 : 0;
+  }
+}
+// Gather the flagged entries (positions pos from an exclusive scan of the
+// flags) with vertex ids renumbered by vpos and facet / segment ids shifted back.
+__global__ void k_inst_gather(DevMesh m, int kind, int n, const int* flag, const int* pos,
+                              const int* vpos, int of, int oseg, int4* out, uint8_t* oflag,
+                              V4* oxyz) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (!flag[i]) continue;
+    int d = pos[i];
+    if (kind == 0) {
+      oxyz[d] = m.V[CKI(i, m.capV)];
+    } else if (kind == 1) {
+      int4 v = m.T[CKI(i, m.capT)].v;
+      out[d] = make_int4(vpos[vid(v.x)], vpos[vid(v.y)], vpos[vid(v.z)], vpos[vid(v.w)]);
+      oflag[d] = m.Tflag[CKI(i, m.capT)] & F_UNSPL ? 2 : 0;
+    } else if (kind == 2) {
+      int4 S = m.SV[CKI(i, m.capS)];
+      out[d] = make_int4(vpos[S.x], vpos[S.y], vpos[S.z], S.w - of);
+      oflag[d] = (m.Smust[CKI(i, m.capS)] ? 1 : 0) | (m.Sflag[CKI(i, m.capS)] & F_UNSPL ? 2 : 0);
+    } else {
+      int4 G = m.GV[CKI(i, m.capG)];
+      out[d] = make_int4(vpos[G.x], vpos[G.y], G.z - oseg, 0);
+      oflag[d] = (m.Gmust[CKI(i, m.capG)] ? 1 : 0) | (m.Gflag[CKI(i, m.capG)] & F_UNSPL ? 2 : 0);
+    }
+  }
+}
+// keep the flags of bad tetrahedra (bad, not unsplittable)
+__global__ void k_inst_bad(DevMesh m, int* flag, int n) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    if (flag[t] && !(m.Tflag[CKI(t, m.capT)] & F_BAD)) flag[t] = 0;
+}
+void launch_inst_bad(const DevMesh& m, int* flag, int n, cudaStream_t s) {
+  if (n > 0) k_inst_bad<<<grid_for(n, 256), 256, 0, s>>>(m, flag, n);
+}
+void launch_inst_flags(const DevMesh& m, int slot, int kind, int n, int* out, cudaStream_t s) {
+  if (n > 0) k_inst_flags<<<grid_for(n, 256), 256, 0, s>>>(m, slot, kind, n, out);
+}
+void launch_inst_gather(const DevMesh& m, int kind, int n, const int* flag, const int* pos,
+                        const int* vpos, int of, int oseg, int4* out, uint8_t* oflag, V4* oxyz,
+                        cudaStream_t s) {
+  if (n > 0)
+    k_inst_gather<<<grid_for(n, 256), 256, 0, s>>>(m, kind, n, flag, pos, vpos, of, oseg, out,
+                                                   oflag, oxyz);
 }
 
 // ============================================================ maintenance
@@ -1794,12 +2190,6 @@ __global__ void k_report_cav(DevMesh m, DevRound r, const int* offs, int4* out) 
 }
 
 // ================================================================ wrappers
-static inline int grid_for(long n, int block) {
-  long g = (n + block - 1) / block;
-  if (g < 1) g = 1;
-  if (g > 152 * 32) g = 152 * 32;
-  return (int)g;
-}
 
 void launch_init_tets(const DevMesh& m, const int4* tets, int n, cudaStream_t s) {
   k_init_tets<<<grid_for(n, 256), 256, 0, s>>>(m, tets, n);
@@ -1841,9 +2231,9 @@ void launch_check_create(const DevMesh& m, int* err, cudaStream_t s) {
 void launch_recompute_bad(const DevMesh& m, double B, cudaStream_t s) {
   k_recompute_bad<<<grid_for(m.nT, 256), 256, 0, s>>>(m, B);
 }
-void launch_classify(const DevMesh& m, unsigned char* candS, unsigned char* candG,
-                     unsigned char* candT, int* err, cudaStream_t s) {
-  k_classify<<<grid_for((long)m.nG + m.nS + m.nT, 256), 256, 0, s>>>(m, candS, candG, candT, err);
+void launch_classify(const DevMesh& m, bool full, int* err, cudaStream_t s) {
+  long n = (long)m.nG + m.nS + (full ? m.nT : 0);
+  if (n > 0) k_classify<<<grid_for(n, 256), 256, 0, s>>>(m, full ? 1 : 0, err);
 }
 void launch_prio(const DevMesh& m, int cls, const int* elems, int n, unsigned long long* keys,
                  cudaStream_t s) {
@@ -1880,7 +2270,7 @@ void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t 
   k_grow2<<<blocks, 64, 0, s>>>(m, r);
 }
 void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s) {
-  if (r.n > 0) k_select<<<grid_for(32L * r.n, 256), 256, 0, s>>>(m, r);
+  if (r.n > 0) k_select<<<grid_for(r.n, 256), 256, 0, s>>>(m, r);
 }
 void launch_insert(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s) {
   if (r.n > 0) k_insert<<<grid_for(32L * r.n, 256), 256, 0, s>>>(m, r, hint);
@@ -1963,12 +2353,37 @@ void launch_eval_pred(int kind, const double* in, int n, int* sign, double* outp
 
 // A subsegment round that inserted nothing, gave up nothing and flagged no new
 // candidate would repeat itself: its refused candidates become unsplittable.
+// Decided per instance from its round counters (run after selection).
 __global__ void k_stall(DevMesh m, DevRound r) {
+  unsigned moved = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
-    if ((r.status[i] & 0xff) != OUT_REJECT) continue;
+    if (cls_of(r, i) != CLS_SUBSEG || (r.status[i] & 0xff) != OUT_REJECT) continue;
+    const unsigned long long* q = m.instSt + (size_t)inst_of(r, i) * IS_COUNT;
+    if (q[IS_SURV] || q[IS_UNSPL] || q[IS_NEWCAND]) continue;
     r.status[i] = OUT_UNSPL | (RS_STRUCT << 8);
     m.Gflag[CKI(r.cand[i], m.capG)] |= F_UNSPL;
+    m.dirtyG[CKI(r.cand[i], m.capG)] = 1;
+    atomicAdd(&m.instSt[(size_t)inst_of(r, i) * IS_COUNT + IS_STALLED], 1ULL);
+    ++moved;
   }
+  if (moved) {
+    atomicAdd(&r.stats[ST_UNSPL], (unsigned long long)moved);
+    atomicAdd(&r.stats[ST_REJECT], (unsigned long long)(-(long long)moved));
+  }
+}
+void launch_count_inst(const DevMesh& m, const uint8_t* candG, const uint8_t* candS,
+                       const uint8_t* candT, cudaStream_t s) {
+  long tot = (long)m.nG + m.nS + m.nT;
+  if (tot > 0) k_count_inst<<<grid_for(tot, 256), 256, 0, s>>>(m, candG, candS, candT);
+}
+void launch_round_flags(const DevMesh& m, const uint8_t* candG, const uint8_t* candS,
+                        const uint8_t* candT, uint8_t* out, cudaStream_t s) {
+  long tot = (long)m.nG + m.nS + m.nT;
+  if (tot > 0) k_round_flags<<<grid_for(tot, 256), 256, 0, s>>>(m, candG, candS, candT, out);
+}
+void launch_decode_cands(const DevMesh& m, int* cand, uint8_t* ccls, int* cinst, int n,
+                         cudaStream_t s) {
+  if (n > 0) k_decode_cands<<<grid_for(n, 256), 256, 0, s>>>(m, cand, ccls, cinst, n);
 }
 void launch_stall(const DevMesh& m, const DevRound& r, cudaStream_t s) {
   if (r.n > 0) k_stall<<<grid_for(r.n, 256), 256, 0, s>>>(m, r);
@@ -1987,6 +2402,11 @@ int checked_error(int* info, cudaStream_t s) {
   info[0] = info[1] = info[2] = info[3] = 0;
   return 0;
 #endif
+}
+
+// enqueue a copy of the exact-arithmetic overflow flag (no synchronisation)
+void exact_overflow_copy_async(int* dst, cudaStream_t s) {
+  cudaMemcpyFromSymbolAsync(dst, g_exact_overflow, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
 }
 
 int exact_overflow_flag(cudaStream_t s, bool reset) {

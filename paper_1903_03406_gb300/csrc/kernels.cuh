@@ -27,12 +27,17 @@ void launch_check_create(const DevMesh& m, int* err, cudaStream_t s);
 void launch_recompute_bad(const DevMesh& m, double B, cudaStream_t s);
 
 // classification and queues
-void launch_classify(const DevMesh& m, unsigned char* candS, unsigned char* candG,
-                     unsigned char* candT, int* err, cudaStream_t s);
+void launch_classify(const DevMesh& m, bool full, int* err, cudaStream_t s);
 void launch_prio(const DevMesh& m, int cls, const int* elems, int n, unsigned long long* keys,
                  cudaStream_t s);
 void launch_tiefix(const DevMesh& m, int cls, const unsigned long long* keys, int* elems, int n,
                    cudaStream_t s);
+void launch_count_inst(const DevMesh& m, const uint8_t* candG, const uint8_t* candS,
+                       const uint8_t* candT, cudaStream_t s);
+void launch_round_flags(const DevMesh& m, const uint8_t* candG, const uint8_t* candS,
+                        const uint8_t* candT, uint8_t* out, cudaStream_t s);
+void launch_decode_cands(const DevMesh& m, int* cand, uint8_t* ccls, int* cinst, int n,
+                         cudaStream_t s);
 
 // one round
 void launch_split(const DevMesh& m, const DevRound& r, cudaStream_t s);
@@ -62,8 +67,19 @@ void launch_gather_subsegs(const DevMesh& m, const int* pos, int4* out, unsigned
 void launch_report_cav(const DevMesh& m, const DevRound& r, const int* offs, int4* out,
                        cudaStream_t s);
 
+// batches
+void launch_append(const DevMesh& d, const DevMesh& src, int ov, int ot, int os, int og, int of,
+                   int oseg, int slot, cudaStream_t s);
+void launch_kill_instance(const DevMesh& m, int slot, cudaStream_t s);
+void launch_inst_flags(const DevMesh& m, int slot, int kind, int n, int* out, cudaStream_t s);
+void launch_inst_bad(const DevMesh& m, int* flag, int n, cudaStream_t s);
+void launch_inst_gather(const DevMesh& m, int kind, int n, const int* flag, const int* pos,
+                        const int* vpos, int of, int oseg, int4* out, uint8_t* oflag, V4* oxyz,
+                        cudaStream_t s);
+
 void launch_eval_pred(int kind, const double* in, int n, int* sign, double* outp, cudaStream_t s);
 int exact_overflow_flag(cudaStream_t s, bool reset);
+void exact_overflow_copy_async(int* dst, cudaStream_t s);
 int checked_error(int* info, cudaStream_t s);
 
 }  // namespace cdr

@@ -93,7 +93,28 @@ struct DevMesh {
   int capV, capT, capS, capG;  // allocated sizes (bounds of the checked build)
   double guard2;
   int walk_limit;
+  // Candidate flags kept from round to round, and the subfaces / subsegments
+  // whose flag must be recomputed (created or touched by the last round).
+  uint8_t* candT;
+  uint8_t* candS;
+  uint8_t* candG;
+  uint8_t* dirtyS;
+  uint8_t* dirtyG;
+  // Instances: independent meshes held as disconnected parts of this mesh
+  // (batched refinement). Each vertex records its instance; an element belongs
+  // to the instance of its vertices. Vinst == nullptr means one instance (0)
+  // whose bound is the round's B and whose guard is guard2.
+  int* Vinst;
+  const double* instB;          // per instance: quality bound B
+  const double* instG2;         // per instance: squared shortest-edge guard
+  const int* instCls;           // per instance: class served this round (-1: none)
+  unsigned long long* instCnt;  // per instance: classification counts [3]
+  unsigned long long* instSt;   // per instance: round counters [IS_COUNT]
+  int ninst;
 };
+
+// per-instance round counters
+enum { IS_SURV = 0, IS_UNSPL, IS_NEWCAND, IS_REJECT, IS_STALLED, IS_COUNT };
 
 // Tier capacities of the region-growth workspace. Tier 1 lives in shared
 // memory (one workspace per warp); candidates whose region does not fit are
@@ -145,6 +166,11 @@ struct DevRound {
   unsigned long long* stats;   // device counters
   const uint8_t* candG;        // this round's subsegment candidates (classification)
   double B;
+  // Per-candidate class and instance (rounds in which every instance serves
+  // its own first non-empty class); nullptr: every candidate has class cls
+  // and instance 0.
+  const uint8_t* ccls;
+  const int* cinst;
 };
 
 // device counters
@@ -161,6 +187,7 @@ enum {
   ST_NEWT,    // tetrahedra written by insertion
   ST_NEWCAND,  // refusals that flagged a subsegment not yet a candidate
   ST_BLAST,    // regions stopped on a higher-priority start tetrahedron
+  ST_DEADT,    // tetrahedra retired by insertion
   ST_COUNT
 };
 

@@ -281,6 +281,35 @@ __device__ inline int ex_len2(const Ex2* r, double* out, ExScratch& w) {
 struct D3 {
   double x, y, z;
 };
+
+// ------------------------------------------------------ FP32 first stage
+// GB300 runs FP32 far faster than FP64, so orient3d and insphere first decide
+// in FP32. The coordinate differences are formed in FP64 and rounded once to
+// FP32, so each equals the exact difference times (1 + eta) with
+// |eta| <= 2^-24 + 2^-53; a degree-k monomial then moves by at most
+// ((1+eta)^k - 1) of its magnitude. The determinant and its permanent (the
+// same polynomial over absolute values) are evaluated in FP32 along the same
+// straight-line program as the FP64 filter below, adding at most gamma_m(2^-24)
+// times the permanent (m roundings on a path; Higham ch. 3). The bound is the
+// sum of both terms with a factor-of-two margin:
+//   orient3d  (k = 3, m = 8):  32 * 2^-24 * permanent
+//   insphere  (k = 5, m = 17): 64 * 2^-24 * permanent
+// The stage runs only when every nonzero difference lies in [2^-20, 2^24]: then
+// no product overflows and a product can leave the normal range only after an
+// exact (Sterbenz) cancellation; the absolute error such an underflow can
+// carry, at most 2^-150 per operation times the remaining factors (< 2^100 in
+// all), stays below the added absolute term 2^-40. Undecided cases fall
+// through to the FP64 filter and then to exact arithmetic.
+constexpr float kF32Unit = 5.9604644775390625e-08f;  // 2^-24
+constexpr float kOrientBoundF = 32.0f * kF32Unit;
+constexpr float kInsphereBoundF = 64.0f * kF32Unit;
+constexpr float kF32Abs = 9.094947017729282e-13f;    // 2^-40
+constexpr float kF32Lo = 9.5367431640625e-07f;       // 2^-20
+constexpr float kF32Hi = 16777216.0f;                // 2^24
+__device__ __forceinline__ bool f32_range(float v) {
+  float a = fabsf(v);
+  return a == 0.0f || (a >= kF32Lo && a <= kF32Hi);
+}
 CDR_HD D3 d3(double x, double y, double z) { return D3{x, y, z}; }
 
 // ------------------------------------------------------------------ orient
@@ -300,6 +329,25 @@ __device__ __forceinline__ int orient3d(D3 a, D3 b, D3 c, D3 d) {
   double ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
   double vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
   double wx = d.x - a.x, wy = d.y - a.y, wz = d.z - a.z;
+  {
+    const float fux = __double2float_rn(ux), fuy = __double2float_rn(uy),
+                fuz = __double2float_rn(uz), fvx = __double2float_rn(vx),
+                fvy = __double2float_rn(vy), fvz = __double2float_rn(vz),
+                fwx = __double2float_rn(wx), fwy = __double2float_rn(wy),
+                fwz = __double2float_rn(wz);
+    if (f32_range(fux) && f32_range(fuy) && f32_range(fuz) && f32_range(fvx) &&
+        f32_range(fvy) && f32_range(fvz) && f32_range(fwx) && f32_range(fwy) &&
+        f32_range(fwz)) {
+      float m1 = fvy * fwz - fvz * fwy, m2 = fvz * fwx - fvx * fwz, m3 = fvx * fwy - fvy * fwx;
+      float det = fux * m1 + fuy * m2 + fuz * m3;
+      float perm = fabsf(fux) * (fabsf(fvy * fwz) + fabsf(fvz * fwy)) +
+                   fabsf(fuy) * (fabsf(fvz * fwx) + fabsf(fvx * fwz)) +
+                   fabsf(fuz) * (fabsf(fvx * fwy) + fabsf(fvy * fwx));
+      float bound = kOrientBoundF * perm + kF32Abs;
+      if (det > bound) return 1;
+      if (-det > bound) return -1;
+    }
+  }
   double m1 = vy * wz - vz * wy, m2 = vz * wx - vx * wz, m3 = vx * wy - vy * wx;
   double det = ux * m1 + uy * m2 + uz * m3;
   double perm = fabs(ux) * (fabs(vy * wz) + fabs(vz * wy)) +
@@ -352,11 +400,46 @@ __device__ __forceinline__ double det3f(double ax, double ay, double az, double 
   return ax * m1 + ay * m2 + az * m3;
 }
 
+__device__ __forceinline__ float det3f32(float ax, float ay, float az, float bx, float by,
+                                         float bz, float cx, float cy, float cz, float& perm) {
+  float m1 = by * cz - bz * cy, m2 = bz * cx - bx * cz, m3 = bx * cy - by * cx;
+  perm = fabsf(ax) * (fabsf(by * cz) + fabsf(bz * cy)) +
+         fabsf(ay) * (fabsf(bz * cx) + fabsf(bx * cz)) +
+         fabsf(az) * (fabsf(bx * cy) + fabsf(by * cx));
+  return ax * m1 + ay * m2 + az * m3;
+}
+
 __device__ __forceinline__ int insphere(D3 a, D3 b, D3 c, D3 d, D3 e) {
   double ax = a.x - e.x, ay = a.y - e.y, az = a.z - e.z;
   double bx = b.x - e.x, by = b.y - e.y, bz = b.z - e.z;
   double cx = c.x - e.x, cy = c.y - e.y, cz = c.z - e.z;
   double dx = d.x - e.x, dy = d.y - e.y, dz = d.z - e.z;
+  {
+    const float fax = __double2float_rn(ax), fay = __double2float_rn(ay),
+                faz = __double2float_rn(az), fbx = __double2float_rn(bx),
+                fby = __double2float_rn(by), fbz = __double2float_rn(bz),
+                fcx = __double2float_rn(cx), fcy = __double2float_rn(cy),
+                fcz = __double2float_rn(cz), fdx = __double2float_rn(dx),
+                fdy = __double2float_rn(dy), fdz = __double2float_rn(dz);
+    if (f32_range(fax) && f32_range(fay) && f32_range(faz) && f32_range(fbx) &&
+        f32_range(fby) && f32_range(fbz) && f32_range(fcx) && f32_range(fcy) &&
+        f32_range(fcz) && f32_range(fdx) && f32_range(fdy) && f32_range(fdz)) {
+      float al = fax * fax + fay * fay + faz * faz;
+      float bl = fbx * fbx + fby * fby + fbz * fbz;
+      float cl = fcx * fcx + fcy * fcy + fcz * fcz;
+      float dl = fdx * fdx + fdy * fdy + fdz * fdz;
+      float p1, p2, p3, p4;
+      float m1 = det3f32(fax, fay, faz, fbx, fby, fbz, fcx, fcy, fcz, p1);
+      float m2 = det3f32(fax, fay, faz, fbx, fby, fbz, fdx, fdy, fdz, p2);
+      float m3 = det3f32(fax, fay, faz, fcx, fcy, fcz, fdx, fdy, fdz, p3);
+      float m4 = det3f32(fbx, fby, fbz, fcx, fcy, fcz, fdx, fdy, fdz, p4);
+      float det = -(dl * m1 - cl * m2 + bl * m3 - al * m4);
+      float perm = dl * p1 + cl * p2 + bl * p3 + al * p4;
+      float bound = kInsphereBoundF * perm + kF32Abs;
+      if (det > bound) return 1;
+      if (-det > bound) return -1;
+    }
+  }
   double al = ax * ax + ay * ay + az * az;
   double bl = bx * bx + by * by + bz * bz;
   double cl = cx * cx + cy * cy + cz * cz;
@@ -589,6 +672,13 @@ CDR_HD uint64_t prio_hash(int cls, const int* ids, int n) {
   uint64_t h = 0x9E3779B97F4A7C15ULL * (uint64_t)(cls + 1);
   for (int i = 0; i < n; ++i) h = mix64(h ^ (uint64_t)(uint32_t)ids[i]);
   return h;
+}
+// An element's priority: the same chain over the bit patterns of its vertices'
+// coordinates (x, y, z per vertex, ascending vertex id), so that it does not
+// depend on the absolute ids (an instance orders its candidates alike whether
+// it is refined alone or beside other instances in one mesh).
+__device__ __forceinline__ uint64_t prio_hash_step(uint64_t h, double c) {
+  return mix64(h ^ (uint64_t)__double_as_longlong(c));
 }
 
 }  // namespace cdr

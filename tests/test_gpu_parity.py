@@ -35,7 +35,7 @@ def gpu_handle(cdr, e, plc, **kw):
 def _families(rng, n):
     out = []
     for i in range(n):
-        k = i % 4
+        k = i % 6
         if k == 0:
             P = rng.uniform(-1, 1, size=(5, 3))
         elif k == 1:
@@ -45,10 +45,21 @@ def _families(rng, n):
                           [1, -2, 2], [3, 0, 0], [0, 3, 0], [0, 0, 3], [0, 0, -3], [-2, -2, 1]],
                          dtype=np.float64)
             P = S[rng.choice(len(S), size=5, replace=False)] * 0.37 + 1000.0
-        else:
+        elif k == 3:
             P = rng.integers(-2, 3, size=(5, 3)).astype(np.float64) * 0.1 + 0.3
             j, c = rng.integers(0, 5), rng.integers(0, 3)
             P[j, c] = np.nextafter(P[j, c], np.inf if rng.random() < 0.5 else -np.inf)
+        elif k == 4:
+            # nearly cospherical, relative noise 1e-9..1e-5: the FP32 stage's bound
+            # must make it defer, never decide wrongly
+            d = rng.normal(size=(5, 3))
+            P = 500.0 + 37.0 * d / np.linalg.norm(d, axis=1, keepdims=True)
+            P *= 1.0 + 10.0 ** rng.uniform(-9, -5) * rng.normal(size=(5, 3))
+        else:
+            # nearly coplanar (for orient3d), same noise
+            u, v = rng.normal(size=3), rng.normal(size=3)
+            P = 250.0 + rng.normal(size=(5, 1)) * u * 40 + rng.normal(size=(5, 1)) * v * 40
+            P *= 1.0 + 10.0 ** rng.uniform(-9, -5) * rng.normal(size=(5, 3))
         out.append(P)
     return out
 

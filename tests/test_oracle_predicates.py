@@ -281,3 +281,16 @@ def test_priority_hash_is_splitmix64():
         for i in ids:
             h = mix(h ^ i)
         assert oracle.prio_hash(cls, ids) == h
+    # an element's priority chains the same finaliser over the bit patterns of
+    # its vertex coordinates (x, y, z per vertex, ascending vertex id)
+    P = np.array([[0.0, 1.5, -2.25], [1e-300, 3.0, 7.0], [5.0, -0.0, 1.0]])
+    for cls in (0, 1, 2):
+        h = (0x9E3779B97F4A7C15 * (cls + 1)) & ((1 << 64) - 1)
+        for w in P.reshape(-1).view(np.uint64):
+            h = mix(h ^ int(w))
+        assert oracle.prio_hash_xyz(cls, P) == h
+    # it depends on the geometry only, and -0.0 differs from 0.0 bitwise
+    assert oracle.prio_hash_xyz(2, P) != oracle.prio_hash_xyz(2, P[::-1])
+    Q = P.copy()
+    Q[2, 1] = 0.0
+    assert oracle.prio_hash_xyz(2, P) != oracle.prio_hash_xyz(2, Q)

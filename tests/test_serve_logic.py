@@ -1,0 +1,113 @@
+"""Host logic of the serving loop (admission by memory budget, continuous
+batching, retirement, latency), run against a stand-in batch on the CPU."""
+import numpy as np
+import pytest
+
+from paper_1903_03406_gb300 import serve
+
+
+class FakeBatch:
+    """Instances finish after a number of rounds fixed by their size; slots of
+    removed instances are reused, as in the library."""
+
+    def __init__(self):
+        self.left, self.free, self.log = {}, [], []
+        self.n = 0
+
+    def add(self, B, xyz, *rest):
+        slot = self.free.pop() if self.free else self.n
+        if slot == self.n:
+            self.n += 1
+        self.left[slot] = max(1, len(xyz) // 100)
+        self.log.append(("add", slot, len(xyz)))
+        return slot
+
+    def round(self):
+        active = 0
+        for k in self.left:
+            if self.left[k] > 0:
+                self.left[k] -= 1
+                active += 1
+        return active
+
+    def stats(self, slot):
+        return {"state": "done" if self.left[slot] == 0 else "refining", "steiner_inserted": 1}
+
+    def export(self, slot):
+        return {"slot": slot}
+
+    def sizes(self, slot):
+        return {}
+
+    def remove(self, slot):
+        del self.left[slot]
+        self.free.append(slot)
+        self.log.append(("remove", slot))
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 0.001
+        return self.t
+
+
+def _mesh(n):
+    return dict(xyz=np.zeros((n, 3)), tets=None, segs=None, seg_id=None, tris=None, facet_id=None,
+                nfacets=6)
+
+
+def test_estimate_grows_with_size_and_quality():
+    assert serve.growth(1.4) > serve.growth(1.6) > serve.growth(2.0) > 1.0
+    assert serve.estimate_bytes(2000, 1.4) > serve.estimate_bytes(1000, 1.4)
+    assert abs(serve.growth(1.5) - np.interp(1 / 1.5, [1 / 1.6, 1 / 1.4],
+                                             [serve.growth(1.6), serve.growth(1.4)])) < 1e-12
+
+
+def test_admission_respects_the_budget_and_arrival_order():
+    b = FakeBatch()
+    per = serve.estimate_bytes(1000, 1.6)
+    srv = serve.Server(b, budget_bytes=int(2.5 * per), clock=Clock())
+    for i in range(6):
+        srv.submit(serve.Request(i, arrival=0.0, B=1.6, mesh=_mesh(1000)))
+    srv.admit(1.0)
+    assert len(srv.running) == 2 and srv.used_bytes == 2 * per
+    res = srv.run()
+    assert [r.rid for r in sorted(res, key=lambda r: r.rid)] == list(range(6))
+    assert srv.used_bytes == 0 and not srv.running
+    # never more than two instances on the device at once
+    live, peak = 0, 0
+    for ev in b.log:
+        live += 1 if ev[0] == "add" else -1
+        peak = max(peak, live)
+    assert peak == 2
+    # admission in arrival order: request i is admitted no later than i+1
+    adm = {r.rid: r.admitted for r in res}
+    assert all(adm[i] <= adm[i + 1] for i in range(5))
+
+
+def test_continuous_batching_overlaps_requests():
+    b = FakeBatch()
+    srv = serve.Server(b, budget_bytes=10 ** 12, clock=Clock())
+    srv.submit(serve.Request(0, 0.0, 1.4, _mesh(3000)))  # 30 rounds
+    srv.submit(serve.Request(1, 0.0, 1.4, _mesh(500)))   # 5 rounds
+    res = srv.run()
+    by = {r.rid: r for r in res}
+    assert by[1].done < by[0].done          # the short one leaves first
+    assert srv.rounds == 30                 # they shared rounds
+    s = serve.latency_summary(res)
+    assert s["n"] == 2 and s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_oversized_request_is_refused():
+    srv = serve.Server(FakeBatch(), budget_bytes=1000)
+    with pytest.raises(ValueError):
+        srv.submit(serve.Request(0, 0.0, 1.4, _mesh(10 ** 6)))
+
+
+def test_poisson_arrivals():
+    t = serve.poisson_arrivals(20000, rate=50.0, seed=3)
+    assert np.all(np.diff(t) > 0)
+    assert abs(len(t) / t[-1] - 50.0) < 2.0
