@@ -246,7 +246,8 @@ const char* cdr_status_string(int status);
 
 /* Timing of the kernel groups of each round with CUDA events recorded on the
  * handle's stream, and device work counters (always accumulated).
- *   enable   1 on, 0 off, -1 unchanged;  reset  nonzero clears the totals first
+ *   enable   1 on, 2 on for the region-growth groups (4, 5) only, 0 off,
+ *            -1 unchanged;  reset  nonzero clears the totals first
  *   ms[16]   accumulated milliseconds per group: 0 classify, 1 order, 2 split,
  *            3 locate, 4 grow (tier 1), 5 grow (tier 2), 6 select, 7 scan,
  *            8 insert, 9 compact

@@ -65,6 +65,7 @@ struct cdr_handle {
   int lastN = 0, lastCls = -1, lastN2 = 0;
   // profiling: events around each kernel group, accumulated per round
   bool prof = false;
+  bool profGrowOnly = false;  // time the region-growth groups only
   cudaEvent_t ev[2 * 16] = {};
   double prof_ms[16] = {};
   long long prof_calls[16] = {};
@@ -266,9 +267,6 @@ __global__ void k_gather_u32(const unsigned* src, const int* perm, int n, unsign
 __global__ void k_iota(int* a, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
 }
-__global__ void k_fill_int(int* a, int n, int v) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
-}
 __global__ void k_xyz_to_v4(const double* xyz, int n, V4* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     out[i] = make_v4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.0);
@@ -281,10 +279,6 @@ __global__ void k_init_subsegs(int4* GV, uint8_t* Gf, uint8_t* Gm, const int* se
     Gm[i] = 0;
   }
 }
-__global__ void k_retry_flags(const int* status, int n, int* flag) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    flag[i] = status[i] == OUT_RETRY ? 1 : 0;
-}
 __global__ void k_scatter_slab2(const int* list2, int n2, int* slab2_of) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n2; j += gridDim.x * blockDim.x)
     slab2_of[list2[j]] = j;
@@ -294,39 +288,6 @@ struct Int4Sum {
     return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
   }
 };
-__global__ void k_cand_keys(DevMesh m, int cls0, const uint8_t* ccls, const int* cand, int n,
-                            int4* out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int e = cand[i];
-    const int cls = ccls ? (int)ccls[i] : cls0;
-    int4 k = make_int4(-1, -1, -1, -1);
-    if (cls == CLS_SUBSEG) {
-      int4 G = m.GV[e];
-      k.x = min(G.x, G.y);
-      k.y = max(G.x, G.y);
-    } else if (cls == CLS_SUBFACE) {
-      int4 S = m.SV[e];
-      int a = S.x, b = S.y, c = S.z, t;
-      if (a > b) { t = a; a = b; b = t; }
-      if (b > c) { t = b; b = c; c = t; }
-      if (a > b) { t = a; a = b; b = t; }
-      k = make_int4(a, b, c, -1);
-    } else if (cls == CLS_TET) {
-      int4 v = m.T[e].v;
-      int s[4] = {v.x & kVidMask, v.y & kVidMask, v.z & kVidMask, v.w & kVidMask};
-      for (int a = 1; a < 4; ++a)
-        for (int b = a; b > 0 && s[b - 1] > s[b]; --b) {
-          int t = s[b];
-          s[b] = s[b - 1];
-          s[b - 1] = t;
-        }
-      k = make_int4(s[0], s[1], s[2], s[3]);
-    } else {
-      k.x = e;
-    }
-    out[i] = k;
-  }
-}
 // points: one candidate per located tetrahedron (the smallest rank) this round
 __global__ void k_point_prefilter(DevMesh m, int* status, const int* loc, int n,
                                   unsigned long long epoch, int pass) {
@@ -382,24 +343,6 @@ bool sort2(cdr_handle* h, const unsigned long long* hi, const unsigned* lo, int 
   return cuda_status(h) == 0;
 }
 
-// warp-aggregated counts of nonzero bytes in up to three arrays
-__global__ void k_count3(const unsigned char* a, int na, const unsigned char* b, int nb,
-                         const unsigned char* c, int nc, unsigned long long* out) {
-  int tot = na + nb + nc;
-  int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < tot; base += stride) {
-    int i = base + threadIdx.x;
-    int w = -1;
-    if (i < na) w = a[i] ? 0 : -1;
-    else if (i < na + nb) w = b[i - na] ? 1 : -1;
-    else if (i < tot) w = c[i - na - nb] ? 2 : -1;
-    for (int k = 0; k < 3; ++k) {
-      unsigned bal = __ballot_sync(0xffffffffu, w == k);
-      if (bal && (int)(threadIdx.x & 31) == __ffs(bal) - 1)
-        atomicAdd(&out[k], (unsigned long long)__popc(bal));
-    }
-  }
-}
 __global__ void k_count_bad(DevMesh m, unsigned long long* out) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.nT; t += gridDim.x * blockDim.x)
     if ((m.Tflag[t] & (F_DEAD | F_BAD)) == F_BAD) atomicAdd(out, 1ULL);
@@ -427,6 +370,7 @@ enum { PG_CLASSIFY = 0, PG_ORDER, PG_SPLIT, PG_LOCATE, PG_GROW1, PG_GROW2, PG_SE
        PG_INSERT, PG_COMPACT, PG_N };
 inline void pmark(cdr_handle* h, int g, int which) {
   if (!h->prof) return;
+  if (h->profGrowOnly && g != PG_GROW1 && g != PG_GROW2) return;
   if (!h->ev[2 * g + which]) cudaEventCreate(&h->ev[2 * g + which]);
   cudaEventRecord(h->ev[2 * g + which], h->stream);
 }
@@ -435,6 +379,7 @@ inline void pcollect(cdr_handle* h, const bool* used) {
   if (!h->prof) return;
   for (int g = 0; g < PG_N; ++g) {
     if (!used[g]) continue;
+    if (h->profGrowOnly && g != PG_GROW1 && g != PG_GROW2) continue;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev[2 * g], h->ev[2 * g + 1]) == cudaSuccess) {
       h->prof_ms[g] += ms;
@@ -604,9 +549,9 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   DevRound r = make_round(h, cls, n, B);
   cudaMemsetAsync(h->bStats.p, 0, ST_COUNT * 8, s);
   if (cls < 0) cudaMemsetAsync(h->bInstSt.p, 0, (size_t)h->ninst * IS_COUNT * 8, s);
-  k_fill_int<<<gridn(n), 256, 0, s>>>(ptr<int>(h->bSlab2of), n, -1);
-  k_cand_keys<<<gridn(n), 256, 0, s>>>(m, cls, r.ccls, r.cand, n, ptr<int4>(h->bCkey));
-  h->prof_ctr[15] += 2;
+  r.ckey = ptr<int4>(h->bCkey);
+  r.rflag = ptr<int>(h->bSurv);  // scratch until selection
+  if (cls != CLS_POINT) r.seed_epoch = next_epoch(h);  // claims are made while locating
   bool used[PG_N] = {};
   pmark(h, PG_SPLIT, 0);
   launch_split(m, r, s);
@@ -625,19 +570,20 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
     k_point_prefilter<<<gridn(n), 256, 0, s>>>(m, r.status, r.loc, n, e0, 0);
     k_point_prefilter<<<gridn(n), 256, 0, s>>>(m, r.status, r.loc, n, e0, 1);
   }
-  r.seed_epoch = next_epoch(h);
-  launch_seed(m, r, s);
-  h->prof_ctr[15] += 1;
+  if (cls == CLS_POINT) {
+    r.seed_epoch = next_epoch(h);
+    launch_seed(m, r, s);
+    h->prof_ctr[15] += 1;
+  }
   r.epoch = next_epoch(h);
   pmark(h, PG_GROW1, 0);
   launch_grow1(m, r, s);
   pmark(h, PG_GROW1, 1);
-  h->prof_ctr[15] += 2;  // growth + retry flags
+  h->prof_ctr[15] += 1;
   used[PG_GROW1] = true;
-  // tier 2 for regions that did not fit
+  // tier 2 for regions that did not fit (flagged by the growth kernel)
   {
-    int* flag = ptr<int>(h->bSurv);  // scratch before selection
-    k_retry_flags<<<gridn(n), 256, 0, s>>>(r.status, n, flag);
+    int* flag = r.rflag;
     size_t tb = 0;
     int* nsel = ptr<int>(h->bErr) + 4;
     cub::DeviceSelect::Flagged(nullptr, tb, thrust::counting_iterator<int>(0), flag,
@@ -1988,7 +1934,10 @@ int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_
     for (int g = 0; g < 16; ++g) calls[g] = h->prof_calls[g];
   if (counters)
     for (int g = 0; g < 16; ++g) counters[g] = h->prof_ctr[g];
-  if (enable >= 0) h->prof = enable != 0;
+  if (enable >= 0) {
+    h->prof = enable != 0;
+    h->profGrowOnly = enable == 2;
+  }
   return CDR_OK;
 }
 

@@ -673,11 +673,19 @@ __global__ void k_split(DevMesh m, DevRound r) {
     r.sp[i] = make_v4(p.x, p.y, p.z, 0.0);
     r.loc[i] = -1;
     set_status(r, i, ok ? OUT_OK : OUT_UNSPL, ok ? RS_NONE : RS_BADPOINT);
+    r.slab2_of[i] = -1;
+    if (r.ckey) {
+      int ids[4] = {-1, -1, -1, -1};
+      elem_key(m, cls, e, ids);
+      r.ckey[i] = make_int4(ids[0], ids[1], ids[2], ids[3]);
+    }
   }
 }
 
 // Visibility walk (exit through the face with the smallest sorted vertex triple
 // among those p lies strictly beyond) and the facet walk (same rule on edges).
+__device__ __forceinline__ void seed_claim(const DevMesh& m, const DevRound& r, int i);
+
 __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
     if (r.status[i] != OUT_OK) continue;
@@ -726,6 +734,7 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
             set_status(r, i, OUT_REJECT, RS_WALK_SUBFACE);
           }
           m.Smust[CKI(s, m.capS)] = 1;
+          m.dirtyS[CKI(s, m.capS)] = 1;
           done = true;
           break;
         }
@@ -770,6 +779,7 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
             if (m.Gflag[CKI(g, m.capG)] & F_UNSPL) set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
             else set_status(r, i, OUT_REJECT, RS_WALK_SUBSEG);
             m.Gmust[CKI(g, m.capG)] = 1;
+            m.dirtyG[CKI(g, m.capG)] = 1;
           }
           done = true;
           break;
@@ -780,6 +790,9 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
     } else {
       r.loc[i] = e;
     }
+    // refinement rounds claim their start tetrahedra here (points do it in
+    // k_seed, after their one-per-tetrahedron filter)
+    if (r.cls != CLS_POINT && r.status[i] == OUT_OK) seed_claim(m, r, i);
   }
 }
 
@@ -787,24 +800,25 @@ __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
 // Start claims: every candidate whose point was located claims the tetrahedra
 // its region starts from (the located tetrahedron; both sides of the located
 // subface; the ring of the subsegment) with its priority rank.
-__global__ void k_seed(DevMesh m, DevRound r) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
-    if (r.status[i] != OUT_OK) continue;
-    const unsigned long long mk = (r.seed_epoch << 32) | (unsigned long long)(unsigned)i;
-    const int cls = cls_of(r, i);
-    if (cls == CLS_TET || cls == CLS_POINT) {
-      atomicMin(&m.Tseed[CKI(r.loc[i], m.capT)], mk);
-    } else if (cls == CLS_SUBFACE) {
-      int tf = m.SN[CKI(r.loc[i], m.capS)].w;
-      if (tf < 0) continue;
-      atomicMin(&m.Tseed[CKI(tf >> 2, m.capT)], mk);
-      int nb = tet_n_ptr(m, tf >> 2)[tf & 3];
-      if (nb >= 0) atomicMin(&m.Tseed[CKI(nb >> 2, m.capT)], mk);
-    } else {
-      int4 G = m.GV[CKI(r.cand[i], m.capG)];
-      edge_ring(m, G.w, G.x, G.y, [&](int t, const TetRec&) { atomicMin(&m.Tseed[CKI(t, m.capT)], mk); });
-    }
+__device__ __forceinline__ void seed_claim(const DevMesh& m, const DevRound& r, int i) {
+  const unsigned long long mk = (r.seed_epoch << 32) | (unsigned long long)(unsigned)i;
+  const int cls = cls_of(r, i);
+  if (cls == CLS_TET || cls == CLS_POINT) {
+    atomicMin(&m.Tseed[CKI(r.loc[i], m.capT)], mk);
+  } else if (cls == CLS_SUBFACE) {
+    int tf = m.SN[CKI(r.loc[i], m.capS)].w;
+    if (tf < 0) return;
+    atomicMin(&m.Tseed[CKI(tf >> 2, m.capT)], mk);
+    int nb = tet_n_ptr(m, tf >> 2)[tf & 3];
+    if (nb >= 0) atomicMin(&m.Tseed[CKI(nb >> 2, m.capT)], mk);
+  } else {
+    int4 G = m.GV[CKI(r.cand[i], m.capG)];
+    edge_ring(m, G.w, G.x, G.y, [&](int t, const TetRec&) { atomicMin(&m.Tseed[CKI(t, m.capT)], mk); });
   }
+}
+__global__ void k_seed(DevMesh m, DevRound r) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x)
+    if (r.status[i] == OUT_OK) seed_claim(m, r, i);
 }
 #ifdef CDR_CHECKED
 #define seed_blasts(m, r, t, i) seed_blasts_at(m, r, t, i, __LINE__)
@@ -1139,7 +1153,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
             TetRec rec = ld_tet(m, t);
             int nb = geti(rec.n, f);
             CKL(nb, m.nT);
-            CKI(t, m.nT);
+            (void)CKI(t, m.nT);
             if (nb >= 0 && !face_sub(rec.v, f)) {
               int nt = nb >> 2;
               if (hs_find(w.hset, C::HCAP, nt) == 0 && orient_rep(m, rec, f, p) > 0) cand = nt;
@@ -1562,6 +1576,7 @@ __global__ void __launch_bounds__(32 * kWarps1) k_grow1(DevMesh m, DevRound r) {
     int* slab = r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
     grow_one<Tier1>(m, r, i, w, slab, lane, acc);
     __syncwarp();
+    if (lane == 0 && r.rflag) r.rflag[i] = r.status[i] == OUT_RETRY ? 1 : 0;
   }
   flush_acc(r, acc, lane);
 }
@@ -1597,8 +1612,8 @@ __device__ __forceinline__ const int* slab_of(const DevRound& r, int i, bool& ti
   return r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
 }
 
-// Selection: a region is kept if it holds every mark it placed. One lane per
-// candidate; the warp checks the marks of each eligible candidate together.
+// Selection (the "blast" step of Sec. 2): a region is kept if it holds every
+// mark it placed. One warp per candidate; its lanes check the marks together.
 __device__ bool holds_marks(const DevMesh& m, const DevRound& r, int i, int lane) {
   bool t2;
   const int* slab = slab_of(r, i, t2);
@@ -1627,35 +1642,13 @@ __global__ void k_select(DevMesh m, DevRound r) {
   int lane = threadIdx.x & 31;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int nw = (gridDim.x * blockDim.x) >> 5;
-  // per-lane outcome counts: kept, eligible but lost, refused, blasted, unsplittable
+  // this warp's outcome counts: kept, eligible but lost, refused, blasted,
+  // unsplittable (added to the round totals once, at the end)
   unsigned c_surv = 0, c_ok = 0, c_rej = 0, c_blast = 0, c_unspl = 0;
-  for (int base = warp * 32; base < r.n; base += nw * 32) {
-    int i = base + lane;
-    int outcome = i < r.n ? (r.status[i] & 0xff) : -1;
-    bool surv = false;
-    unsigned okm = __ballot_sync(FULLMASK, outcome == OUT_OK);
-    while (okm) {
-      int src = __ffs(okm) - 1;
-      okm &= okm - 1;
-      bool kept = holds_marks(m, r, base + src, lane);
-      if (lane == src) surv = kept;
-    }
-    // per-instance counts (lanes of one instance add together)
-    if (m.instSt) {
-      int key = i < r.n ? inst_of(r, i) : -1;
-      unsigned grp = __match_any_sync(FULLMASK, key);
-      bool leader = key >= 0 && (__ffs(grp) - 1) == lane;
-      unsigned sv = __ballot_sync(FULLMASK, surv) & grp;
-      unsigned un = __ballot_sync(FULLMASK, outcome == OUT_UNSPL) & grp;
-      unsigned rj = __ballot_sync(FULLMASK, outcome == OUT_REJECT) & grp;
-      if (leader) {
-        unsigned long long* q = m.instSt + (size_t)key * IS_COUNT;
-        if (sv) atomicAdd(&q[IS_SURV], (unsigned long long)__popc(sv));
-        if (un) atomicAdd(&q[IS_UNSPL], (unsigned long long)__popc(un));
-        if (rj) atomicAdd(&q[IS_REJECT], (unsigned long long)__popc(rj));
-      }
-    }
-    if (i >= r.n) continue;
+  for (int i = warp; i < r.n; i += nw) {
+    const int outcome = r.status[i] & 0xff;
+    const bool surv = outcome == OUT_OK && holds_marks(m, r, i, lane);
+    if (lane != 0) continue;
     const int cls = cls_of(r, i);
     r.survived[i] = surv ? 1 : 0;
     int4 c = make_int4(0, 0, 0, 0);
@@ -1690,13 +1683,12 @@ __global__ void k_select(DevMesh m, DevRound r) {
     } else {
       ++c_unspl;
     }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    c_surv += __shfl_xor_sync(FULLMASK, c_surv, o);
-    c_ok += __shfl_xor_sync(FULLMASK, c_ok, o);
-    c_rej += __shfl_xor_sync(FULLMASK, c_rej, o);
-    c_blast += __shfl_xor_sync(FULLMASK, c_blast, o);
-    c_unspl += __shfl_xor_sync(FULLMASK, c_unspl, o);
+    // per-instance counts for the stall rule and batch statistics (blasted
+    // regions, the bulk of a large round, need none)
+    if (m.instSt && (surv || outcome == OUT_UNSPL || outcome == OUT_REJECT)) {
+      unsigned long long* q = m.instSt + (size_t)inst_of(r, i) * IS_COUNT;
+      atomicAdd(&q[surv ? IS_SURV : (outcome == OUT_UNSPL ? IS_UNSPL : IS_REJECT)], 1ULL);
+    }
   }
   if (lane == 0) {
     if (c_surv) atomicAdd(&r.stats[ST_SURV], (unsigned long long)c_surv);
@@ -1772,7 +1764,7 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       N.v = nv;
       N.n = make_int4(-1, -1, -1, -1);
       CKL(bout[j], m.nT);
-      CKI(t, m.nT);
+      (void)CKI(t, m.nT);
       seti(N.n, f, bout[j]);
       m.T[CKI(nid, m.capT)] = N;
       int4 ts = make_int4(-1, -1, -1, -1);
@@ -2270,7 +2262,7 @@ void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t 
   k_grow2<<<blocks, 64, 0, s>>>(m, r);
 }
 void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s) {
-  if (r.n > 0) k_select<<<grid_for(r.n, 256), 256, 0, s>>>(m, r);
+  if (r.n > 0) k_select<<<grid_for(32L * r.n, 256), 256, 0, s>>>(m, r);
 }
 void launch_insert(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s) {
   if (r.n > 0) k_insert<<<grid_for(32L * r.n, 256), 256, 0, s>>>(m, r, hint);

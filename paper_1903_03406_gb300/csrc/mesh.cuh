@@ -171,6 +171,8 @@ struct DevRound {
   // and instance 0.
   const uint8_t* ccls;
   const int* cinst;
+  int4* ckey;                  // per candidate: sorted vertex ids (round report)
+  int* rflag;                  // per candidate: 1 if its region needs tier 2
 };
 
 // device counters
