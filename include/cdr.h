@@ -238,6 +238,11 @@ int cdr_batch_stats(cdr_handle* b, int32_t slot, cdr_stats* stats, int32_t* stat
 int cdr_batch_export_sizes(cdr_handle* b, int32_t slot, cdr_sizes* out);
 int cdr_batch_export(cdr_handle* b, int32_t slot, const cdr_mesh_out* out);
 
+/* Slots of the instances that have finished (state 2), in slot order: up to
+ * cap of them into slots[], their total count into *n. Host-side, no device
+ * work. */
+int cdr_batch_finished(cdr_handle* b, int32_t* slots, int32_t cap, int32_t* n);
+
 /* Remove an instance: its elements are retired and its slot freed. */
 int cdr_batch_remove(cdr_handle* b, int32_t slot);
 

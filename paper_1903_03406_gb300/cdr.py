@@ -130,6 +130,7 @@ def lib():
             L.cdr_batch_export_sizes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(Sizes)]
             L.cdr_batch_export.argtypes = [P, ctypes.c_int32, ctypes.POINTER(MeshOut)]
             L.cdr_batch_remove.argtypes = [P, ctypes.c_int32]
+            L.cdr_batch_finished.argtypes = [P, i32p, ctypes.c_int32, i32p]
             _lib = L
     return _lib
 
@@ -403,6 +404,15 @@ class Batch:
 
     def remove(self, slot):
         _check(lib().cdr_batch_remove(self.ptr, int(slot)), "cdr_batch_remove")
+
+    def finished(self):
+        """Slots whose instance has finished refining."""
+        n = ctypes.c_int32(0)
+        _check(lib().cdr_batch_finished(self.ptr, None, 0, ctypes.byref(n)), "cdr_batch_finished")
+        out = np.zeros(max(n.value, 1), dtype=np.int32)
+        _check(lib().cdr_batch_finished(self.ptr, _p(out, ctypes.c_int32), len(out),
+                                        ctypes.byref(n)), "cdr_batch_finished")
+        return [int(x) for x in out[: n.value]]
 
 
 def device_arch():

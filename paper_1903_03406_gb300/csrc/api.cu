@@ -209,7 +209,7 @@ bool grow_tets(cdr_handle* h, int need) {
             ensure(h, h->bTflag, cap, n) &&
             ensure(h, h->bTmark, cap * sizeof(unsigned long long), n * 8) &&
             ensure(h, h->bTseed, cap * sizeof(unsigned long long), n * 8) &&
-            ensure(h, h->bTfwd, cap * sizeof(int), n * 4) && ensure(h, h->bCandT, cap, n);
+            ensure(h, h->bTfwd, cap * sizeof(int), n * 4) && ensure(h, h->bCandT, cap + 16, n);
   if (!ok) return false;
   h->capT = cap;
   bind(h);
@@ -222,7 +222,7 @@ bool grow_subfaces(cdr_handle* h, int need) {
   bool ok = ensure(h, h->bSV, cap * sizeof(int4), n * sizeof(int4)) &&
             ensure(h, h->bSN, cap * sizeof(int4), n * sizeof(int4)) &&
             ensure(h, h->bSflag, cap, n) && ensure(h, h->bSmust, cap, n) &&
-            ensure(h, h->bSmark, cap * 8, n * 8) && ensure(h, h->bCandS, cap, n) &&
+            ensure(h, h->bSmark, cap * 8, n * 8) && ensure(h, h->bCandS, cap + 16, n) &&
             ensure(h, h->bDirtyS, cap, n);
   if (!ok) return false;
   h->capS = cap;
@@ -235,7 +235,7 @@ bool grow_subsegs(cdr_handle* h, int need) {
   size_t n = h->m.nG;
   bool ok = ensure(h, h->bGV, cap * sizeof(int4), n * sizeof(int4)) &&
             ensure(h, h->bGflag, cap, n) && ensure(h, h->bGmust, cap, n) &&
-            ensure(h, h->bCandG, cap, n) && ensure(h, h->bDirtyG, cap, n);
+            ensure(h, h->bCandG, cap + 16, n) && ensure(h, h->bDirtyG, cap, n);
   if (!ok) return false;
   h->capG = cap;
   bind(h);
@@ -548,7 +548,7 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   if (!ensure_pinned(h)) return CDR_ERR_OOM;
   DevRound r = make_round(h, cls, n, B);
   cudaMemsetAsync(h->bStats.p, 0, ST_COUNT * 8, s);
-  if (cls < 0) cudaMemsetAsync(h->bInstSt.p, 0, (size_t)h->ninst * IS_COUNT * 8, s);
+  if (cls != CLS_POINT) cudaMemsetAsync(h->bInstSt.p, 0, (size_t)h->ninst * IS_COUNT * 8, s);
   r.ckey = ptr<int4>(h->bCkey);
   r.rflag = ptr<int>(h->bSurv);  // scratch until selection
   if (cls != CLS_POINT) r.seed_epoch = next_epoch(h);  // claims are made while locating
@@ -622,7 +622,8 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   h->prof_ctr[15] += cls == CLS_POINT ? 2 : 1;
   used[PG_SELECT] = true;
   // stall rule for instances serving subsegments (decided on the device)
-  if (cls < 0 && std::find(h->instCls.begin(), h->instCls.end(), CLS_SUBSEG) != h->instCls.end()) {
+  if (cls == CLS_SUBSEG ||
+      (cls < 0 && std::find(h->instCls.begin(), h->instCls.end(), CLS_SUBSEG) != h->instCls.end())) {
     launch_stall(m, r, s);
     h->prof_ctr[15] += 1;
   }
@@ -745,8 +746,11 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
   pmark(h, PG_CLASSIFY, 1);
   h->prof_ctr[15] += 2;  // classification + counts
   cudaMemsetAsync(h->bInstCnt.p, 0, (size_t)ni * 3 * 8, s);
-  launch_count_inst(m, ptr<uint8_t>(h->bCandG), ptr<uint8_t>(h->bCandS), ptr<uint8_t>(h->bCandT),
-                    s);
+  if (h->batch)
+    launch_count_inst(m, ptr<uint8_t>(h->bCandG), ptr<uint8_t>(h->bCandS),
+                      ptr<uint8_t>(h->bCandT), s);
+  else
+    launch_count_single(m, ptr<unsigned long long>(h->bInstCnt), s);
   cudaMemcpyAsync(h->pinCnt, h->bInstCnt.p, (size_t)ni * 3 * 8, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&h->pin->cerr, h->bErr.p, 4, cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
@@ -772,6 +776,25 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
   if (n == 0) return CDR_OK;
   if (n >= (1LL << 31) - 1) return set_err(h, CDR_ERR_OOM);
   if (!ensure_round(h, (int)n)) return CDR_ERR_OOM;
+  if (!h->batch) {  // one instance, one class: its flagged elements in id order
+    const int cls = h->instCls[0];
+    const uint8_t* flags = cls == 0 ? ptr<uint8_t>(h->bCandG)
+                                    : (cls == 1 ? ptr<uint8_t>(h->bCandS) : ptr<uint8_t>(h->bCandT));
+    const int nall = cls == 0 ? m.nG : (cls == 1 ? m.nS : m.nT);
+    size_t tb = 0;
+    int* nsel = ptr<int>(h->bErr) + 4;
+    cub::DeviceSelect::Flagged(nullptr, tb, thrust::counting_iterator<int>(0), flags,
+                               ptr<int>(h->bCand), nsel, nall, s);
+    if (!tmp_ensure(h, tb)) return CDR_ERR_OOM;
+    tb = h->bTmp.bytes;
+    cub::DeviceSelect::Flagged(h->bTmp.p, tb, thrust::counting_iterator<int>(0), flags,
+                               ptr<int>(h->bCand), nsel, nall, s);
+    st = order_candidates(h, cls, (int)n);
+    if (st) return st;
+    st = round_core(h, cls, (int)n, B, ro);
+    if (ro) ro->cls = cls;
+    return st;
+  }
   const long nall = (long)m.nG + m.nS + m.nT;
   if (!ensure(h, h->bRflags, (size_t)nall + 64)) return CDR_ERR_OOM;
   cudaMemcpyAsync(h->bInstCls.p, h->pinCls, (size_t)ni * 4, cudaMemcpyHostToDevice, s);
@@ -1875,6 +1898,18 @@ int cdr_batch_export(cdr_handle* h, int32_t slot, const cdr_mesh_out* out) {
     }
   }
   return cuda_status(h);
+}
+
+int cdr_batch_finished(cdr_handle* h, int32_t* slots, int32_t cap, int32_t* n) {
+  if (!h || !h->batch || !n || cap < 0 || (cap > 0 && !slots)) return CDR_ERR_INVALID_INPUT;
+  int c = 0;
+  for (int k = 0; k < h->ninst; ++k)
+    if (h->insts[k].state == 2) {
+      if (c < cap) slots[c] = k;
+      ++c;
+    }
+  *n = c;
+  return CDR_OK;
 }
 
 int cdr_batch_remove(cdr_handle* h, int32_t slot) {

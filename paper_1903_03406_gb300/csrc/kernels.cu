@@ -10,6 +10,7 @@
 // re-linking the new stars to the rest of the mesh (k_insert).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -619,6 +620,35 @@ __global__ void k_count_inst(DevMesh m, const uint8_t* candG, const uint8_t* can
     if (key >= 0 && (__ffs(grp) - 1) == lane)
       atomicAdd(&m.instCnt[key], (unsigned long long)__popc(grp));
   }
+}
+
+// One instance: the candidates of each class are just the set flags. Sixteen
+// flags per thread (uint4 loads; flag arrays are allocated in whole 16-byte
+// units), one atomic per warp and class.
+__global__ void k_count_single(const uint8_t* candG, int nG, const uint8_t* candS, int nS,
+                               const uint8_t* candT, int nT, unsigned long long* cnt) {
+  const int lane = threadIdx.x & 31;
+  const uint8_t* arr[3] = {candG, candS, candT};
+  const int len[3] = {nG, nS, nT};
+  for (int c = 0; c < 3; ++c) {
+    const int nv = (len[c] + 15) / 16;
+    unsigned tot = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+      uint4 q = reinterpret_cast<const uint4*>(arr[c])[v];
+      unsigned w[4] = {q.x, q.y, q.z, q.w};
+      const int base = v * 16;
+      for (int k = 0; k < 4; ++k)
+        for (int b = 0; b < 4; ++b)
+          if (base + 4 * k + b < len[c] && ((w[k] >> (8 * b)) & 0xff)) ++tot;
+    }
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULLMASK, tot, o);
+    if (lane == 0 && tot) atomicAdd(&cnt[c], (unsigned long long)tot);
+  }
+}
+void launch_count_single(const DevMesh& m, unsigned long long* cnt, cudaStream_t s) {
+  long nv = ((long)std::max(m.nG, std::max(m.nS, m.nT)) + 15) / 16;
+  k_count_single<<<grid_for(nv, 256), 256, 0, s>>>(m.candG, m.nG, m.candS, m.nS, m.candT, m.nT,
+                                                      cnt);
 }
 
 // This round's candidates: flagged elements of the class their instance serves.

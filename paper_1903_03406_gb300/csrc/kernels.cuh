@@ -34,6 +34,7 @@ void launch_tiefix(const DevMesh& m, int cls, const unsigned long long* keys, in
                    cudaStream_t s);
 void launch_count_inst(const DevMesh& m, const uint8_t* candG, const uint8_t* candS,
                        const uint8_t* candT, cudaStream_t s);
+void launch_count_single(const DevMesh& m, unsigned long long* cnt, cudaStream_t s);
 void launch_round_flags(const DevMesh& m, const uint8_t* candG, const uint8_t* candS,
                         const uint8_t* candT, uint8_t* out, cudaStream_t s);
 void launch_decode_cands(const DevMesh& m, int* cand, uint8_t* ccls, int* cinst, int n,

@@ -18,8 +18,9 @@ throughput only.
 
 The memory estimate of a request is its final size predicted from its input
 size and B: final vertices = V0 * growth(B), at `bytes_per_vertex` device
-bytes each. The growth table is calibrated by refining sample meshes
-(`calibrate`); the defaults come from such a calibration.
+bytes each. `calibrate` fits the growth table from refined samples (input
+vertices, B, final vertices); the defaults are a conservative table for
+unit-cube inputs with 1% constraints.
 """
 from __future__ import annotations
 
@@ -72,10 +73,19 @@ def estimate_bytes(n_verts, B, table=None, bytes_per_vertex=DEFAULT_BYTES_PER_VE
     return int(n_verts * growth(B, table) * bytes_per_vertex)
 
 
+def calibrate(samples, margin=1.1):
+    """Growth table {B: ratio} from (input vertices, B, final vertices) samples:
+    the largest observed ratio per B, times a safety margin."""
+    table = {}
+    for n0, B, n1 in samples:
+        table[float(B)] = max(table.get(float(B), 0.0), n1 / float(n0))
+    return {B: g * margin for B, g in table.items()}
+
+
 @dataclass
 class Server:
     """Continuous-batching server over a batch object with the cdr.Batch API
-    (add, round, stats, export, remove)."""
+    (add, round, finished, stats, export, remove)."""
 
     batch: object
     budget_bytes: int
@@ -116,17 +126,17 @@ class Server:
     def retire(self):
         """Export and remove every finished instance."""
         done = []
-        for slot, (req, t_adm) in list(self.running.items()):
-            st = self.batch.stats(slot)
-            if st["state"] != "done":
+        for slot in self.batch.finished():
+            if slot not in self.running:
                 continue
-            mesh = self.batch.export(slot) if self.keep_meshes else None
-            if not self.keep_meshes:
-                self.batch.sizes(slot)  # the result is complete on the host side too
+            req, t_adm = self.running[slot]
+            st = self.batch.stats(slot)
+            mesh = self.batch.export(slot)  # the result reaches the host
             self.batch.remove(slot)
             self.used_bytes -= req.est_bytes
             del self.running[slot]
-            r = Result(req.rid, req.arrival, t_adm, self.clock(), st, mesh)
+            r = Result(req.rid, req.arrival, t_adm, self.clock(), st,
+                       mesh if self.keep_meshes else None)
             self.results.append(r)
             done.append(r)
         return done

@@ -30,6 +30,9 @@ class FakeBatch:
                 active += 1
         return active
 
+    def finished(self):
+        return [k for k, v in self.left.items() if v == 0]
+
     def stats(self, slot):
         return {"state": "done" if self.left[slot] == 0 else "refining", "steiner_inserted": 1}
 
@@ -105,6 +108,12 @@ def test_oversized_request_is_refused():
     srv = serve.Server(FakeBatch(), budget_bytes=1000)
     with pytest.raises(ValueError):
         srv.submit(serve.Request(0, 0.0, 1.4, _mesh(10 ** 6)))
+
+
+def test_calibrate_takes_the_largest_ratio_with_margin():
+    t = serve.calibrate([(1000, 1.4, 4000), (2000, 1.4, 9000), (1000, 2.0, 1500)], margin=1.0)
+    assert t == {1.4: 4.5, 2.0: 1.5}
+    assert serve.calibrate([(10, 1.6, 30)])[1.6] == pytest.approx(3.3)
 
 
 def test_poisson_arrivals():
