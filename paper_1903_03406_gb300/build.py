@@ -32,6 +32,8 @@ def _flags():
          "-diag-suppress", "1444"]
     if os.environ.get("CDR_CHECKED"):
         f.append("-DCDR_CHECKED")  # bounds-checked diagnostic build
+    if os.environ.get("CDR_PHASES"):
+        f.append("-DCDR_PHASES")  # per-phase timing of region growth (diagnostic build)
     return f
 
 

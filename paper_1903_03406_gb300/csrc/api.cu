@@ -1580,6 +1580,13 @@ int cdr_delaunay_box(const double* xyz, int32_t n, const cdr_options* opt,
 }
 
 // ===================================================================== batches
+// Diagnostic builds only (CDR_PHASES): cycles and region counts per phase of
+// region growth since the last call. Not part of the declared interface.
+int cdr_debug_phases(cdr_handle* h, unsigned long long* out32) {
+  if (!h || !out32) return CDR_ERR_INVALID_INPUT;
+  return phase_counters(out32, h->stream) ? CDR_OK : CDR_ERR_INVALID_INPUT;
+}
+
 int cdr_batch_create(const cdr_options* opt, const cdr_allocator* alloc, void* stream,
                      cdr_handle** out) {
   if (!out) return CDR_ERR_INVALID_INPUT;

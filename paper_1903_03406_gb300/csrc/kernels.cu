@@ -868,6 +868,25 @@ __device__ __forceinline__ bool seed_blasts(const DevMesh& m, const DevRound& r,
 }
 #endif
 
+// Diagnostic build (CDR_PHASES): cycles spent per phase of region growth,
+// summed over regions (lane 0's clock), and the regions that reached each phase.
+#ifdef CDR_PHASES
+static __device__ unsigned long long g_phase[2][16];
+#define PHASE(k)                                              \
+  do {                                                        \
+    if (lane == 0) {                                          \
+      long long t_ = clock64();                               \
+      atomicAdd(&g_phase[0][k], (unsigned long long)(t_ - ph_t)); \
+      atomicAdd(&g_phase[1][k], 1ULL);                        \
+      ph_t = t_;                                              \
+    }                                                         \
+  } while (0)
+#else
+#define PHASE(k) \
+  do {           \
+  } while (0)
+#endif
+
 // =============================================================== growth
 struct Ws {
   int* cav;   // cavity tets
@@ -920,6 +939,65 @@ __device__ __forceinline__ void wappend(int* list, int& n, int cap, bool pred, i
   n += __popc(b);
 }
 
+// Table of a region's boundary edges and vertices (open addressing in the
+// storage of the tet hash set, which growth no longer needs). An entry e <
+// 3 CAPB is the edge of boundary face e/3 opposite its vertex e%3 (each edge is
+// entered once per face: twice on a closed boundary); e >= 3 CAPB is the
+// vertex bv[e - 3 CAPB], entered once. Keys are (min, max) vertex pairs, (v, v)
+// for a vertex.
+__device__ __forceinline__ void bt_key(const int* bv, int e, int cap3, int& a, int& b) {
+  if (e < cap3) {
+    const int j = e / 3, q = e - 3 * j;
+    const int u = bv[3 * j + (q + 1) % 3], x = bv[3 * j + (q + 2) % 3];
+    a = min(u, x);
+    b = max(u, x);
+  } else {
+    a = b = bv[e - cap3];
+  }
+}
+__device__ __forceinline__ unsigned bt_slot(int a, int b, int cap) {
+  return (unsigned)mix64(((unsigned long long)(unsigned)a << 32) | (unsigned)b) & (unsigned)(cap - 1);
+}
+// enter e (vertices: only if their key is absent); false if the table is full
+__device__ bool bt_put(int* t, int cap, const int* bv, int cap3, int e, bool unique) {
+  int a, b;
+  bt_key(bv, e, cap3, a, b);
+  unsigned h = bt_slot(a, b, cap);
+  for (int it = 0; it < cap; ++it) {
+    int old = atomicCAS(&t[h], -1, e);
+    if (old == -1) return true;
+    if (unique) {
+      int c, d;
+      bt_key(bv, old, cap3, c, d);
+      if (c == a && d == b) return true;
+    }
+    h = (h + 1) & (unsigned)(cap - 1);
+  }
+  return false;
+}
+// is key (a, b) in the table; with self >= 0: how many edge entries other
+// than self have it (*other = one of them)
+__device__ int bt_find(const int* t, int cap, const int* bv, int cap3, int a, int b, int self,
+                       int* other) {
+  unsigned h = bt_slot(a, b, cap);
+  int cnt = 0;
+  for (int it = 0; it < cap; ++it) {
+    const int e = t[h];
+    if (e == -1) break;
+    if (e != self) {
+      int c, d;
+      bt_key(bv, e, cap3, c, d);
+      if (c == a && d == b) {
+        if (self < 0) return 1;
+        ++cnt;
+        *other = e;
+      }
+    }
+    h = (h + 1) & (unsigned)(cap - 1);
+  }
+  return cnt;
+}
+
 // work counters of one warp's regions, added to the round totals once per warp
 struct GrowAcc {
   unsigned long long tested = 0, cav = 0, bnd = 0;
@@ -960,8 +1038,12 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   bool blast = false;  // the region met a higher-priority start (warp-uniform)
   bool cfail = false;  // a closure failure was met (the growth goes on)
 
+#ifdef CDR_PHASES
+  long long ph_t = clock64();
+#endif
   for (int k = lane; k < C::HCAP; k += 32) w.hset[k] = -1;
   __syncwarp();
+  PHASE(0);
 
   // ---------------------------------------------------------- start sets
   if (cls == CLS_TET || cls == CLS_POINT) {
@@ -1023,6 +1105,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   }
   __syncwarp();
 
+  PHASE(1);  // start sets
   // ---------------------------------------------------------- facet part
   if (nf > 0) {
     int head = 0;
@@ -1168,6 +1251,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
     }
   }
 
+  PHASE(2);  // facet part
   // ----------------------------------------------------------- tet part
   {
     int head = 0;
@@ -1312,6 +1396,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
     }
     if (blast) goto done;
   }
+  PHASE(3);  // tet part: growth, closure, boundary, shell
   if (ncav > kCavLimit) {
     outcome = OUT_UNSPL;
     reason = RS_OVERFLOW;
@@ -1324,6 +1409,22 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   }
   __syncwarp();
 
+  // ------------------------------------------------ boundary table
+  // (the tet set's storage: growth is done)
+  {
+    for (int k = lane; k < C::HCAP; k += 32) w.hset[k] = -1;
+    __syncwarp();
+    bool full = false;
+    for (int it = lane; it < 3 * nbnd; it += 32) {
+      full |= !bt_put(w.hset, C::HCAP, w.bv, C::CAP3, it, false);
+      full |= !bt_put(w.hset, C::HCAP, w.bv, C::CAP3, C::CAP3 + it, true);
+    }
+    if (__any_sync(FULLMASK, full)) {  // cannot happen within the caps; be safe
+      retry = true;
+      goto done;
+    }
+    __syncwarp();
+  }
   // ------------------------------------------------ preservation checks
   {
     // every cavity vertex lies on a boundary face
@@ -1334,7 +1435,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       bool miss = false;
       if (it < items) {
         int v = vid(geti(m.T[CKI(w.cav[it >> 2], m.capT)].v, it & 3));
-        miss = !in_list(w.bv, 3 * nbnd, v);
+        miss = !bt_find(w.hset, C::HCAP, w.bv, C::CAP3, v, v, -1, nullptr);
       }
       lost = __any_sync(FULLMASK, miss);
     }
@@ -1344,12 +1445,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       bool miss = false;
       if (it < nfb) {
         int u = w.fbv[3 * it], x = w.fbv[3 * it + 1];
-        bool found = false;
-        for (int j = 0; j < nbnd && !found; ++j) {
-          const int* F = w.bv + 3 * j;
-          found = (F[0] == u || F[1] == u || F[2] == u) && (F[0] == x || F[1] == x || F[2] == x);
-        }
-        miss = !found;
+        miss = !bt_find(w.hset, C::HCAP, w.bv, C::CAP3, min(u, x), max(u, x), -1, nullptr);
       }
       lost = __any_sync(FULLMASK, miss);
     }
@@ -1359,41 +1455,40 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       goto done;
     }
   }
+  PHASE(4);  // preservation
   // ------------------------------------------------ star check
   {
-    // topology first: every star edge is shared by at most two boundary faces
+    // topology first: every star edge is shared by at most two boundary faces;
+    // each edge's partner (the other face's entry) is kept in the slab for
+    // insertion
     bool topo = false, nondel = false;
-    int items = nbnd * 3;
-    for (int pass = 0; pass < 2; ++pass) {
+    const int items = nbnd * 3;
+    for (int it = lane; it < items; it += 32) {
+      int a, b, other = -1;
+      bt_key(w.bv, it, C::CAP3, a, b);
+      int cnt = bt_find(w.hset, C::HCAP, w.bv, C::CAP3, a, b, it, &other);
+      topo |= cnt > 1;
+      slab[L::OFF_PART + it] = cnt == 1 ? other : -1;
+    }
+    topo = __any_sync(FULLMASK, topo);
+    if (!topo) {
       for (int base = 0; base < items; base += 32) {
         int it = base + lane;
         bool bad = false;
         if (it < items) {
-          int j = it / 3, q = it % 3;
-          const int* F = w.bv + 3 * j;
-          int u = F[(q + 1) % 3], x = F[(q + 2) % 3];  // edge opposite face vertex q
-          int partner = -1, cnt = 0;
-          for (int k = 0; k < nbnd; ++k) {
-            if (k == j) continue;
-            const int* G = w.bv + 3 * k;
-            bool hu = G[0] == u || G[1] == u || G[2] == u;
-            bool hx = G[0] == x || G[1] == x || G[2] == x;
-            if (hu && hx) {
-              ++cnt;
-              partner = k;
-            }
-          }
-          if (pass == 0) {
-            bad = cnt > 1;
-          } else if (cnt == 1 && j < partner) {
+          const int j = it / 3, q = it - 3 * j;
+          const int pe = slab[L::OFF_PART + it];  // written by this lane above
+          const int partner = pe >= 0 ? pe / 3 : -1;
+          if (partner >= 0 && j < partner) {
+            const int* F = w.bv + 3 * j;
+            const int u = F[(q + 1) % 3], x = F[(q + 2) % 3];  // edge opposite face vertex q
             bool isnew = false;
             for (int z = 0; z < nfb && !isnew; ++z) {
               int a = w.fbv[3 * z], b = w.fbv[3 * z + 1];
               isnew = (a == u && b == x) || (a == x && b == u);
             }
             if (!isnew) {
-              const int* G = w.bv + 3 * partner;
-              int apex = (G[0] != u && G[0] != x) ? G[0] : ((G[1] != u && G[1] != x) ? G[1] : G[2]);
+              const int apex = w.bv[pe];  // the partner face's vertex off the shared edge
               int bij = w.bin[j];
               TetRec rec = ld_tet(m, bij >> 2);
               int f = bij & 3;
@@ -1405,10 +1500,8 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
             }
           }
         }
-        if (pass == 0) topo |= __any_sync(FULLMASK, bad);
-        else nondel |= __any_sync(FULLMASK, bad);
+        nondel |= __any_sync(FULLMASK, bad);
       }
-      if (pass == 0 && topo) break;
     }
     if (topo) {
       outcome = OUT_UNSPL;
@@ -1421,6 +1514,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       goto done;
     }
   }
+  PHASE(5);  // star check
   // ------------------------------------------------ shortest-edge guard
   {
     const double g2 = guard2_of(m, inst_of(r, i));
@@ -1441,6 +1535,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       goto done;
     }
   }
+  PHASE(6);  // guard
   // ------------------------------------------------ encroachment
   {
     bool rej = false, runspl = false;
@@ -1484,14 +1579,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           if (!split) {
             bool enc = false;
             if (cls == CLS_TET || cls == CLS_SUBFACE) enc = diametral(vtx(m, u), vtx(m, x), p) < 0;
-            if (!enc) {
-              bool on = false;
-              for (int j = 0; j < nbnd && !on; ++j) {
-                const int* F = w.bv + 3 * j;
-                on = (F[0] == u || F[1] == u || F[2] == u) && (F[0] == x || F[1] == x || F[2] == x);
-              }
-              enc = !on;
-            }
+            if (!enc) enc = !bt_find(w.hset, C::HCAP, w.bv, C::CAP3, min(u, x), max(u, x), -1, nullptr);
             if (enc) {
               int g = hash_lookup(m, ekey(u, x));
               if (g >= 0) {
@@ -1517,6 +1605,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       goto done;
     }
   }
+  PHASE(7);  // encroachment
   // ------------------------------------------------ priority marks
   {
     const unsigned long long mk = (r.epoch << 32) | (unsigned long long)(unsigned)i;
@@ -1531,6 +1620,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
     }
   }
 
+  PHASE(8);  // marks
 done:
   __syncwarp();
   for (int o = 16; o > 0; o >>= 1) ntested += __shfl_xor_sync(FULLMASK, ntested, o);
@@ -1749,6 +1839,7 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
     const int* fbnd = slab + SLAB_OFF(OFF_FBND);
     const int* bv = slab + SLAB_OFF(OFF_BV);
     const int* fbv = slab + SLAB_OFF(OFF_FBV);
+    const int* part = slab + SLAB_OFF(OFF_PART);
 #undef SLAB_OFF
     const int4 off = r.offs[i];
     const int e = r.cand[i];
@@ -1815,11 +1906,11 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       if (bout[j] >= 0) tet_n_ptr(m, bout[j] >> 2)[bout[j] & 3] = (nid << 2) | f;
     }
     __syncwarp();
-    // step 2: links inside the star, matched by the boundary faces' shared edges
+    // step 2: links inside the star, through the boundary faces' shared edges
+    // (each edge's partner entry was recorded by growth's star check)
     for (int it = lane; it < nbnd * 3; it += 32) {
       int j = it / 3, q = it % 3;
       const int* F = bv + 3 * j;
-      int u = F[(q + 1) % 3], x = F[(q + 2) % 3];
       int t = bin[j] >> 2, f = bin[j] & 3;
       // position in tet j of the face vertex q (the apex across the new face)
       TetRec R = ld_tet(m, t);
@@ -1827,21 +1918,16 @@ __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
       for (int k = 0; k < 4; ++k)
         if (k != f && vid(geti(R.v, k)) == F[q]) g = k;
       int link = -1;
-      for (int k2 = 0; k2 < nbnd; ++k2) {
-        if (k2 == j) continue;
-        const int* G = bv + 3 * k2;
-        int pu = G[0] == u ? 0 : (G[1] == u ? 1 : (G[2] == u ? 2 : -1));
-        int px = G[0] == x ? 0 : (G[1] == x ? 1 : (G[2] == x ? 2 : -1));
-        if (pu >= 0 && px >= 0) {
-          int apexv = G[3 - pu - px];
-          int t2_ = bin[k2] >> 2, f2 = bin[k2] & 3;
-          TetRec R2 = ld_tet(m, t2_);
-          int h = -1;
-          for (int k = 0; k < 4; ++k)
-            if (k != f2 && vid(geti(R2.v, k)) == apexv) h = k;
-          link = h >= 0 ? (((t0 + k2) << 2) | h) : -1;
-          break;
-        }
+      const int pe = part[it];
+      if (pe >= 0) {
+        const int k2 = pe / 3;
+        const int apexv = bv[pe];  // vertex of face k2 off the shared edge
+        int t2_ = bin[k2] >> 2, f2 = bin[k2] & 3;
+        TetRec R2 = ld_tet(m, t2_);
+        int h = -1;
+        for (int k = 0; k < 4; ++k)
+          if (k != f2 && vid(geti(R2.v, k)) == apexv) h = k;
+        link = h >= 0 ? (((t0 + k2) << 2) | h) : -1;
       }
       CKL(link, m.nT + 0x7fffffff / 8);
       if (link >= 0 && (link >> 2) < t0) CKL(link, 0);  // must point into this star
@@ -2429,6 +2515,22 @@ int checked_error(int* info, cudaStream_t s) {
 // enqueue a copy of the exact-arithmetic overflow flag (no synchronisation)
 void exact_overflow_copy_async(int* dst, cudaStream_t s) {
   cudaMemcpyFromSymbolAsync(dst, g_exact_overflow, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+}
+
+// diagnostic build: read (and clear) the phase counters; 0 if not built in
+int phase_counters(unsigned long long* out32, cudaStream_t s) {
+#ifdef CDR_PHASES
+  cudaMemcpyFromSymbolAsync(out32, g_phase, sizeof(g_phase), 0, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  unsigned long long z[32] = {};
+  cudaMemcpyToSymbolAsync(g_phase, z, sizeof(z), 0, cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+  return 1;
+#else
+  (void)out32;
+  (void)s;
+  return 0;
+#endif
 }
 
 int exact_overflow_flag(cudaStream_t s, bool reset) {

@@ -82,5 +82,6 @@ void launch_eval_pred(int kind, const double* in, int n, int* sign, double* outp
 int exact_overflow_flag(cudaStream_t s, bool reset);
 void exact_overflow_copy_async(int* dst, cudaStream_t s);
 int checked_error(int* info, cudaStream_t s);
+int phase_counters(unsigned long long* out32, cudaStream_t s);
 
 }  // namespace cdr

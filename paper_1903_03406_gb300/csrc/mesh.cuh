@@ -123,9 +123,13 @@ enum { IS_SURV = 0, IS_UNSPL, IS_NEWCAND, IS_REJECT, IS_STALLED, IS_COUNT };
 template <int CAPC_, int CAPB_, int CAPF_, int CAPFB_, int HCAP_>
 struct Caps {
   static constexpr int CAPC = CAPC_, CAPB = CAPB_, CAPF = CAPF_, CAPFB = CAPFB_, HCAP = HCAP_;
+  static constexpr int CAP3 = 3 * CAPB_;  // boundary-table entries below this are edges
 };
-using Tier1 = Caps<64, 160, 32, 48, 256>;
-using Tier2 = Caps<4096, 16384, 8192, 24576, 32768>;
+// HCAP: the tet hash set of growth, reused afterwards as the table of boundary
+// edges and vertices (at most 3 CAPB edges + CAPB/2 + 2 vertices, kept under
+// 60% load).
+using Tier1 = Caps<64, 160, 32, 48, 1024>;
+using Tier2 = Caps<4096, 16384, 8192, 24576, 131072>;
 constexpr int kCavLimit = 4096;
 
 // Per-candidate slab in global memory (written by growth, read by selection
@@ -139,7 +143,9 @@ struct SlabLayout {
   static constexpr int OFF_FBND = OFF_FCAV + C::CAPF;
   static constexpr int OFF_BV = OFF_FBND + C::CAPFB;   // 3 vertex ids per boundary face
   static constexpr int OFF_FBV = OFF_BV + 3 * C::CAPB;  // (u, x, facet) per facet edge
-  static constexpr int STRIDE = OFF_FBV + 3 * C::CAPFB;
+  static constexpr int OFF_PART = OFF_FBV + 3 * C::CAPFB;  // per boundary-face edge: the
+                                                           // other face's edge (3 k + q), or -1
+  static constexpr int STRIDE = OFF_PART + 3 * C::CAPB;
 };
 
 struct DevRound {
