@@ -195,7 +195,8 @@ def gpu_arm(args, rank, world):
         (len(ex["xyz"]), len(ex["tets"]), len(plc["tris"]), len(plc["segs"])))
     al = cdr.TorchAllocator()
     h = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
-                          plc["facet_id"], plc["nfacets"], allocator=al, stream=stream)
+                          plc["facet_id"], plc["nfacets"], mixed_rounds=args.mixed,
+                          allocator=al, stream=stream)
     h.checkpoint()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -257,7 +258,8 @@ def gpu_arm(args, rank, world):
     ins_e2e = 0
     for _ in range(n_e2e):
         he = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
-                               plc["facet_id"], plc["nfacets"], allocator=al, stream=stream)
+                               plc["facet_id"], plc["nfacets"], mixed_rounds=args.mixed,
+                               allocator=al, stream=stream)
         st = he.refine(B, MAX_ROUNDS)
         out = he.export()
         torch.cuda.synchronize()
@@ -453,7 +455,9 @@ def workload_config(args, world):
     w = WORKLOADS[args.workload]
     return {"workload": args.workload, "points": w["n"] + 8, "segments": w["n_seg"],
             "triangles": w["n_tri"], "B": w["B"],
-            "parallelism": "independent instances x%d (replicas)" % world}
+            "parallelism": "independent instances x%d (replicas)" % world,
+            "rounds": "mixed (every class each round, class-first priority)"
+                      if getattr(args, "mixed", False) else "one class per round"}
 
 
 # ---------------------------------------------------------- CPU (oracle) arm
@@ -524,6 +528,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed", action="store_true",
+                    help="mixed rounds: every flagged element is a candidate each round")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

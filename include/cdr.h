@@ -95,6 +95,12 @@ typedef struct {
   double guard2;        /* squared shortest-edge guard; <= 0: (1e-9 * bbox diagonal)^2 */
   int32_t walk_limit;   /* point-location step limit; 0: 100000                         */
   int32_t reserve_factor; /* initial capacity multiple of the input sizes; 0: 4          */
+  int32_t mixed_rounds; /* 0: each round serves one class, the first non-empty of
+                           subsegments, subfaces, bad tetrahedra (Sec. 2's order);
+                           1: each round takes every flagged element, and the
+                           class decides priority first, so a subsegment still
+                           beats a subface and a subface beats a tetrahedron
+                           (fewer rounds)                                       */
 } cdr_options;
 
 /* Per-call statistics. */
@@ -150,7 +156,8 @@ int cdr_create(const cdr_mesh_in* in, const cdr_options* opt, const cdr_allocato
 int cdr_refine(cdr_handle* h, double B, int32_t max_rounds, cdr_stats* stats);
 
 /* Exactly one round (Sec. 2) with bound B. *cls receives the class served
- * (0 subsegments, 1 subfaces, 2 tetrahedra; -1 = nothing left). stats
+ * (0 subsegments, 1 subfaces, 2 tetrahedra, 3 several classes in a mixed
+ * round; -1 = nothing left). stats
  * (nullable) receives that round's counts. */
 int cdr_round(cdr_handle* h, double B, int32_t* cls, cdr_stats* stats);
 

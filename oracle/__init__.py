@@ -70,6 +70,8 @@ def lib():
             L.orc_prio_hash.argtypes = [ctypes.c_int, ip, ctypes.c_int]
             L.orc_prio_hash.restype = ctypes.c_uint64
             L.orc_prio_hash_xyz.argtypes = [ctypes.c_int, dp, ctypes.c_int]
+            L.orc_set_mixed.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_set_mixed.restype = None
             L.orc_prio_hash_xyz.restype = ctypes.c_uint64
             L.orc_box_delaunay.argtypes = [dp, ctypes.c_int, ip]
             L.orc_box_delaunay.restype = P
@@ -290,6 +292,10 @@ class Mesh:
                     cav=cav[: sz[2]].reshape(-1, 4), fcav=fcav[: sz[3]].reshape(-1, 3),
                     nflagS=nfs, nflagG=nfg, flagS=fls[: sz[4]].reshape(-1, 3),
                     flagG=flg[: sz[5]].reshape(-1, 2), inserted=int(sz[6]))
+
+    def set_mixed(self, mixed):
+        """Mode R with every class in every round (class-first priorities)."""
+        lib().orc_set_mixed(self.h, int(bool(mixed)))
 
     def refine_R(self, B, max_rounds=1 << 30):
         out = (ctypes.c_long * 2)()

@@ -75,6 +75,9 @@ struct Mesh {
   std::vector<V3> facetQ;                                 // per-facet reference point
   double guard2 = 0.0;                                    // squared shortest-edge guard
   int walk_limit = 100000;
+  // rounds in which every flagged element is a candidate, whatever its class
+  // (the class decides priority first); false: one class per round
+  bool mixed = false;
   int cav_limit = 4096;
 
   const double* X(int v) const { return P[v].data(); }
@@ -195,13 +198,18 @@ struct Mesh {
 enum { CLS_SUBSEG = 0, CLS_SUBFACE = 1, CLS_TET = 2, CLS_POINT = 3 };
 enum { OUT_OK = 0, OUT_REJECT = 1, OUT_UNSPL = 2, OUT_BLASTED = 4 };
 
+// Priority order (Sec. 2's predetermined priorities): class first (subsegments
+// before subfaces before tetrahedra), then the top 62 bits of the hash, then
+// the sorted vertex ids. The GPU sorts on the 64-bit key class << 62 | hash >> 2.
 struct Cand {
   uint64_t h;
   int key[4];
   int nkey;
   int elem;
+  int cls = 0;
   bool operator<(const Cand& o) const {
-    if (h != o.h) return h < o.h;
+    if (cls != o.cls) return cls < o.cls;
+    if ((h >> 2) != (o.h >> 2)) return (h >> 2) < (o.h >> 2);
     for (int i = 0; i < nkey; ++i)
       if (key[i] != o.key[i]) return key[i] < o.key[i];
     return elem < o.elem;

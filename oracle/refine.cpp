@@ -34,6 +34,7 @@ static void sorted_tet(const Tet& t, int* o) {
 
 void cand_key(const Mesh& M, int cls, int elem, Cand& c) {
   c.elem = elem;
+  c.cls = cls;
   if (cls == CLS_SUBSEG) {
     K2 k = key2(M.G[elem].a, M.G[elem].b);
     c.key[0] = k.a;
@@ -719,6 +720,12 @@ static void apply_flags(Mesh& M, const Decision& d) {
 // candidates by priority, evaluate every candidate on the same snapshot, keep
 // those holding the minimum priority on every touched element, apply the flags
 // of the others, insert the kept points (new vertex ids in priority order).
+// One round (Sec. 2): the candidates are the flagged elements of the first
+// non-empty class (subsegments, subfaces, bad tetrahedra), or of every class
+// when M.mixed (class-first priorities then keep the split order inside the
+// round). Every candidate is evaluated on the same snapshot; those whose
+// regions hold all their marks are inserted. Returns the class served (3 for a
+// round with several classes), -1 when nothing is left.
 int round_R(Mesh& M, double B, RoundReport* rep) {
   std::vector<int> q[3];
   classify(M, B, q);
@@ -731,11 +738,15 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
   if (rep) rep->clear();
   if (cls < 0) return -1;
   std::vector<Cand> cands;
-  for (int e : q[cls]) {
-    Cand c;
-    cand_key(M, cls, e, c);
-    cands.push_back(c);
-  }
+  int present = 0;
+  for (int c = cls; c <= (M.mixed ? 2 : cls); ++c)
+    for (int e : q[c]) {
+      Cand cd;
+      cand_key(M, c, e, cd);
+      cands.push_back(cd);
+      present |= 1 << c;
+    }
+  const int rcls = (present & (present - 1)) ? 3 : cls;
   std::sort(cands.begin(), cands.end());
   int n = (int)cands.size();
   std::vector<Decision> dec(n);
@@ -743,12 +754,12 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
   std::unordered_map<int, int> seeds;
   for (int i = 0; i < n; ++i) {
     std::vector<int> st;
-    Decision d0 = evaluate(M, cls, cands[i].elem, nullptr, -1, nullptr, -1, &st);
+    Decision d0 = evaluate(M, cands[i].cls, cands[i].elem, nullptr, -1, nullptr, -1, &st);
     if (d0.outcome != OUT_OK) continue;
     for (int t : st) seeds.emplace(t, i);
   }
   for (int i = 0; i < n; ++i)
-    dec[i] = evaluate(M, cls, cands[i].elem, nullptr, -1, &seeds, i, nullptr);
+    dec[i] = evaluate(M, cands[i].cls, cands[i].elem, nullptr, -1, &seeds, i, nullptr);
   std::unordered_map<int, int> tm, sm;
   for (int i = 0; i < n; ++i) {
     if (dec[i].outcome != OUT_OK) continue;
@@ -767,12 +778,12 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
     for (int s : dec[i].shellS) ok = ok && sm[s] == i;
     surv[i] = ok;
   }
-  // A subsegment round can stall: every candidate refused only because its
-  // insertion would delete another subsegment that is itself a candidate (two
-  // nearby segments whose midpoints encroach one another). Then nothing changes
-  // and the next round would be the same; the refused candidates become
-  // unsplittable instead.
-  if (cls == CLS_SUBSEG) {
+  // A round with subsegment candidates can stall: every candidate refused only
+  // because its insertion would delete another subsegment that is itself a
+  // candidate (two nearby segments whose midpoints encroach one another). If
+  // nothing was inserted, given up or newly flagged, the next round would be
+  // the same; the refused subsegment candidates become unsplittable instead.
+  if (present & 1) {
     bool progress = false;
     std::unordered_set<int> isCand(q[0].begin(), q[0].end());
     for (int i = 0; i < n && !progress; ++i) {
@@ -782,12 +793,12 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
     }
     if (!progress)
       for (int i = 0; i < n; ++i)
-        if (dec[i].outcome == OUT_REJECT) {
+        if (cands[i].cls == CLS_SUBSEG && dec[i].outcome == OUT_REJECT) {
           dec[i].outcome = OUT_UNSPL;
           dec[i].reason = RS_STRUCT;
         }
   }
-  if (rep) rep->record(M, cls, cands, dec, surv);
+  if (rep) rep->record(M, rcls, cands, dec, surv);
   for (int i = 0; i < n; ++i) apply_flags(M, dec[i]);
   int inserted = 0;
   for (int i = 0; i < n; ++i)
@@ -796,7 +807,7 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
       ++inserted;
     }
   if (rep) rep->inserted = inserted;
-  return cls;
+  return rcls;
 }
 
 // -------------------------------------------------------------- mode S

@@ -41,7 +41,7 @@ class MeshIn(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("guard2", ctypes.c_double), ("walk_limit", ctypes.c_int32),
-                ("reserve_factor", ctypes.c_int32)]
+                ("reserve_factor", ctypes.c_int32), ("mixed_rounds", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -239,9 +239,10 @@ class Handle:
     # -------------------------------------------------------------- creation
     @classmethod
     def create(cls, xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref=None,
-               guard2=0.0, walk_limit=0, reserve_factor=0, allocator=None, stream=None):
+               guard2=0.0, walk_limit=0, reserve_factor=0, mixed_rounds=False, allocator=None,
+               stream=None):
         mi, _arrays = _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref)
-        opt = Options(float(guard2), int(walk_limit), int(reserve_factor))
+        opt = Options(float(guard2), int(walk_limit), int(reserve_factor), int(bool(mixed_rounds)))
         out = ctypes.c_void_p()
         al = ctypes.byref(allocator.struct) if allocator is not None else None
         st = lib().cdr_create(ctypes.byref(mi), ctypes.byref(opt), al, _stream_handle(stream),
@@ -252,7 +253,7 @@ class Handle:
     @classmethod
     def delaunay_box(cls, xyz, walk_limit=0, allocator=None, stream=None):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
-        opt = Options(0.0, int(walk_limit), 0)
+        opt = Options(0.0, int(walk_limit), 0, 0)
         out = ctypes.c_void_p()
         sk, rd = ctypes.c_int32(0), ctypes.c_int32(0)
         al = ctypes.byref(allocator.struct) if allocator is not None else None
@@ -345,8 +346,8 @@ class Batch:
 
     STATE = {0: "free", 1: "refining", 2: "done"}
 
-    def __init__(self, guard2=0.0, walk_limit=0, allocator=None, stream=None):
-        opt = Options(float(guard2), int(walk_limit), 0)
+    def __init__(self, guard2=0.0, walk_limit=0, mixed_rounds=False, allocator=None, stream=None):
+        opt = Options(float(guard2), int(walk_limit), 0, int(bool(mixed_rounds)))
         out = ctypes.c_void_p()
         al = ctypes.byref(allocator.struct) if allocator is not None else None
         _check(lib().cdr_batch_create(ctypes.byref(opt), al, _stream_handle(stream),

@@ -80,6 +80,7 @@ struct cdr_handle {
   std::vector<int> instCls;              // host copy of the round's classes
   // batch bookkeeping (host)
   bool batch = false;
+  bool mixed = false;  // every flagged element is a candidate in every round
   struct Inst {
     int state = 0;  // 0 free slot, 1 refining, 2 done
     int of = 0, nf = 0, oseg = 0, nseg = 0;
@@ -623,7 +624,8 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   used[PG_SELECT] = true;
   // stall rule for instances serving subsegments (decided on the device)
   if (cls == CLS_SUBSEG ||
-      (cls < 0 && std::find(h->instCls.begin(), h->instCls.end(), CLS_SUBSEG) != h->instCls.end())) {
+      (cls < 0 && (std::find(h->instCls.begin(), h->instCls.end(), CLS_SUBSEG) != h->instCls.end() ||
+                   std::find(h->instCls.begin(), h->instCls.end(), 3) != h->instCls.end()))) {
     launch_stall(m, r, s);
     h->prof_ctr[15] += 1;
   }
@@ -764,19 +766,23 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
   h->instCls.assign(ni, -1);
   long long n = 0;
   for (int k = 0; k < ni; ++k) {
+    int present = 0;
     for (int c = 0; c < 3; ++c)
       if (h->pinCnt[3 * k + c] > 0) {
-        h->instCls[k] = c;
-        n += (long long)h->pinCnt[3 * k + c];
-        break;
+        present |= 1 << c;
+        if (h->instCls[k] < 0) h->instCls[k] = c;
+        if (!h->mixed) break;  // the first non-empty class only
       }
+    if (h->mixed && (present & (present - 1))) h->instCls[k] = 3;  // several classes
+    for (int c = 0; c < 3; ++c)
+      if (present & (1 << c)) n += (long long)h->pinCnt[3 * k + c];
     h->pinCls[k] = h->instCls[k];
   }
   if (ro) *ro = RoundOut();
   if (n == 0) return CDR_OK;
   if (n >= (1LL << 31) - 1) return set_err(h, CDR_ERR_OOM);
   if (!ensure_round(h, (int)n)) return CDR_ERR_OOM;
-  if (!h->batch) {  // one instance, one class: its flagged elements in id order
+  if (!h->batch && h->instCls[0] < 3) {  // one instance, one class: its flagged elements
     const int cls = h->instCls[0];
     const uint8_t* flags = cls == 0 ? ptr<uint8_t>(h->bCandG)
                                     : (cls == 1 ? ptr<uint8_t>(h->bCandS) : ptr<uint8_t>(h->bCandT));
@@ -816,7 +822,7 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
                       s);
   h->prof_ctr[15] += 1;
   st = round_core(h, -1, (int)n, B, ro);
-  if (ro) ro->cls = ni == 1 ? h->instCls[0] : 3;  // 3: several classes
+  if (ro) ro->cls = ni == 1 ? h->instCls[0] : 3;  // 3: several classes or instances
   return st;
 }
 
@@ -1028,6 +1034,7 @@ extern "C" int cdr_create(const cdr_mesh_in* in, const cdr_options* opt, const c
     h->has_alloc = true;
   }
   int rf = (opt && opt->reserve_factor > 0) ? opt->reserve_factor : 4;
+  h->mixed = opt && opt->mixed_rounds != 0;
   h->m.walk_limit = (opt && opt->walk_limit > 0) ? opt->walk_limit : 100000;
   h->m.guard2 = (opt && opt->guard2 > 0) ? opt->guard2 : default_guard2(in->xyz, in->n_verts);
   h->m.nF = in->n_facets;
@@ -1599,6 +1606,7 @@ int cdr_batch_create(const cdr_options* opt, const cdr_allocator* alloc, void* s
     h->has_alloc = true;
   }
   h->batch = true;
+  h->mixed = opt && opt->mixed_rounds != 0;
   h->ninst = 0;
   if (opt) h->opts = *opt;
   h->opts.reserve_factor = 1;  // an instance is built at its own size, then appended
@@ -1710,8 +1718,12 @@ int cdr_batch_round(cdr_handle* h, int32_t* n_active) {
     }
     ++active;
     I.st.rounds++;
-    I.st.rounds_by_class[c]++;
-    I.st.candidates += (long long)h->pinCnt[3 * k + c];
+    if (c < 3) {
+      I.st.rounds_by_class[c]++;
+      I.st.candidates += (long long)h->pinCnt[3 * k + c];
+    } else {
+      I.st.candidates += (long long)(h->pinCnt[3 * k] + h->pinCnt[3 * k + 1] + h->pinCnt[3 * k + 2]);
+    }
     if (ran) {
       const unsigned long long* q = h->pinSt + (size_t)k * IS_COUNT;
       I.st.steiner_inserted += (long long)q[IS_SURV];

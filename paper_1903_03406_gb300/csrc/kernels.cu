@@ -528,16 +528,18 @@ __global__ void k_prio(DevMesh m, int cls, const int* elems, int n, unsigned lon
     int e = cls >= 0 ? elems[i] : decode_cand(m, elems[i], c);
     int ids[4];
     int k = elem_key(m, c, e, ids);
+    uint64_t h;
     if (c == CLS_POINT) {
-      keys[i] = prio_hash(c, ids, k);
+      h = prio_hash(c, ids, k);
     } else {
-      uint64_t h = 0x9E3779B97F4A7C15ULL * (uint64_t)(c + 1);
+      h = 0x9E3779B97F4A7C15ULL * (uint64_t)(c + 1);
       for (int q = 0; q < k; ++q) {
         V4 v = m.V[CKI(ids[q], m.capV)];
         h = prio_hash_step(prio_hash_step(prio_hash_step(h, v.x), v.y), v.z);
       }
-      keys[i] = h;
     }
+    // class first (subsegments, subfaces, tetrahedra), then the hash's top 62 bits
+    keys[i] = ((uint64_t)c << 62) | (h >> 2);
   }
 }
 
@@ -651,7 +653,8 @@ void launch_count_single(const DevMesh& m, unsigned long long* cnt, cudaStream_t
                                                       cnt);
 }
 
-// This round's candidates: flagged elements of the class their instance serves.
+// This round's candidates: flagged elements of the class their instance serves
+// (of every class for an instance in mixed rounds).
 __global__ void k_round_flags(DevMesh m, const uint8_t* candG, const uint8_t* candS,
                               const uint8_t* candT, uint8_t* out) {
   const long tot = (long)m.nG + m.nS + m.nT;
@@ -671,7 +674,8 @@ __global__ void k_round_flags(DevMesh m, const uint8_t* candG, const uint8_t* ca
       f = candT[e] != 0;
       if (f) v0 = vid(m.T[CKI(e, m.capT)].v.x);
     }
-    out[i] = (f && m.instCls[vinst(m, v0)] == c) ? 1 : 0;
+    const int sel = f ? m.instCls[vinst(m, v0)] : -1;  // 3: every class
+    out[i] = (f && (sel == c || sel == 3)) ? 1 : 0;
   }
 }
 

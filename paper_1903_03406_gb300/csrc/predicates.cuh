@@ -325,6 +325,25 @@ __device__ __noinline__ int orient3d_exact(D3 a, D3 b, D3 c, D3 d) {
   return ex_sign(n, out);
 }
 
+// FP64 filter, then exact arithmetic (out of line: the FP32 stage decides
+// nearly every call, and one copy keeps the kernels' code small)
+__device__ __noinline__ int orient3d_fp64(D3 a, D3 b, D3 c, D3 d) {
+  double ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+  double vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+  double wx = d.x - a.x, wy = d.y - a.y, wz = d.z - a.z;
+  double m1 = vy * wz - vz * wy, m2 = vz * wx - vx * wz, m3 = vx * wy - vy * wx;
+  double det = ux * m1 + uy * m2 + uz * m3;
+  double perm = fabs(ux) * (fabs(vy * wz) + fabs(vz * wy)) +
+                fabs(uy) * (fabs(vz * wx) + fabs(vx * wz)) +
+                fabs(uz) * (fabs(vx * wy) + fabs(vy * wx));
+  double bound = kOrientBound * perm;
+  if (perm > kTinyPerm) {
+    if (det > bound) return 1;
+    if (-det > bound) return -1;
+  }
+  return orient3d_exact(a, b, c, d);
+}
+
 __device__ __forceinline__ int orient3d(D3 a, D3 b, D3 c, D3 d) {
   double ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
   double vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
@@ -348,17 +367,7 @@ __device__ __forceinline__ int orient3d(D3 a, D3 b, D3 c, D3 d) {
       if (-det > bound) return -1;
     }
   }
-  double m1 = vy * wz - vz * wy, m2 = vz * wx - vx * wz, m3 = vx * wy - vy * wx;
-  double det = ux * m1 + uy * m2 + uz * m3;
-  double perm = fabs(ux) * (fabs(vy * wz) + fabs(vz * wy)) +
-                fabs(uy) * (fabs(vz * wx) + fabs(vx * wz)) +
-                fabs(uz) * (fabs(vx * wy) + fabs(vy * wx));
-  double bound = kOrientBound * perm;
-  if (perm > kTinyPerm) {
-    if (det > bound) return 1;
-    if (-det > bound) return -1;
-  }
-  return orient3d_exact(a, b, c, d);
+  return orient3d_fp64(a, b, c, d);
 }
 
 // ---------------------------------------------------------------- insphere
@@ -409,6 +418,31 @@ __device__ __forceinline__ float det3f32(float ax, float ay, float az, float bx,
   return ax * m1 + ay * m2 + az * m3;
 }
 
+__device__ __noinline__ int insphere_fp64(D3 a, D3 b, D3 c, D3 d, D3 e) {
+  double ax = a.x - e.x, ay = a.y - e.y, az = a.z - e.z;
+  double bx = b.x - e.x, by = b.y - e.y, bz = b.z - e.z;
+  double cx = c.x - e.x, cy = c.y - e.y, cz = c.z - e.z;
+  double dx = d.x - e.x, dy = d.y - e.y, dz = d.z - e.z;
+  double al = ax * ax + ay * ay + az * az;
+  double bl = bx * bx + by * by + bz * bz;
+  double cl = cx * cx + cy * cy + cz * cz;
+  double dl = dx * dx + dy * dy + dz * dz;
+  double p1, p2, p3, p4;
+  double m1 = det3f(ax, ay, az, bx, by, bz, cx, cy, cz, p1);
+  double m2 = det3f(ax, ay, az, bx, by, bz, dx, dy, dz, p2);
+  double m3 = det3f(ax, ay, az, cx, cy, cz, dx, dy, dz, p3);
+  double m4 = det3f(bx, by, bz, cx, cy, cz, dx, dy, dz, p4);
+  // the lifted 4x4 determinant along its lift column, negated (inside > 0)
+  double det = -(dl * m1 - cl * m2 + bl * m3 - al * m4);
+  double perm = dl * p1 + cl * p2 + bl * p3 + al * p4;
+  double bound = kInsphereBound * perm;
+  if (perm > kTinyPerm) {
+    if (det > bound) return 1;
+    if (-det > bound) return -1;
+  }
+  return insphere_exact(a, b, c, d, e);
+}
+
 __device__ __forceinline__ int insphere(D3 a, D3 b, D3 c, D3 d, D3 e) {
   double ax = a.x - e.x, ay = a.y - e.y, az = a.z - e.z;
   double bx = b.x - e.x, by = b.y - e.y, bz = b.z - e.z;
@@ -440,24 +474,7 @@ __device__ __forceinline__ int insphere(D3 a, D3 b, D3 c, D3 d, D3 e) {
       if (-det > bound) return -1;
     }
   }
-  double al = ax * ax + ay * ay + az * az;
-  double bl = bx * bx + by * by + bz * bz;
-  double cl = cx * cx + cy * cy + cz * cz;
-  double dl = dx * dx + dy * dy + dz * dz;
-  double p1, p2, p3, p4;
-  double m1 = det3f(ax, ay, az, bx, by, bz, cx, cy, cz, p1);
-  double m2 = det3f(ax, ay, az, bx, by, bz, dx, dy, dz, p2);
-  double m3 = det3f(ax, ay, az, cx, cy, cz, dx, dy, dz, p3);
-  double m4 = det3f(bx, by, bz, cx, cy, cz, dx, dy, dz, p4);
-  // the lifted 4x4 determinant along its lift column, negated (inside > 0)
-  double det = -(dl * m1 - cl * m2 + bl * m3 - al * m4);
-  double perm = dl * p1 + cl * p2 + bl * p3 + al * p4;
-  double bound = kInsphereBound * perm;
-  if (perm > kTinyPerm) {
-    if (det > bound) return 1;
-    if (-det > bound) return -1;
-  }
-  return insphere_exact(a, b, c, d, e);
+  return insphere_fp64(a, b, c, d, e);
 }
 
 // --------------------------------------------------------------- diametral
@@ -478,7 +495,7 @@ __device__ __noinline__ int diametral_exact(D3 a, D3 b, D3 p) {
   return ex_sign(nacc, acc);
 }
 
-__device__ __forceinline__ int diametral(D3 a, D3 b, D3 p) {
+__device__ __noinline__ int diametral(D3 a, D3 b, D3 p) {
   double ax = a.x - p.x, ay = a.y - p.y, az = a.z - p.z;
   double bx = b.x - p.x, by = b.y - p.y, bz = b.z - p.z;
   double v = ax * bx + ay * by + az * bz;
@@ -547,7 +564,7 @@ __device__ __noinline__ int equatorial_exact(D3 a, D3 b, D3 c, D3 p) {
   return ex_sign(nD, D);
 }
 
-__device__ __forceinline__ int equatorial(D3 a, D3 b, D3 c, D3 p) {
+__device__ __noinline__ int equatorial(D3 a, D3 b, D3 c, D3 p) {
   double ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
   double vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
   double wx = p.x - a.x, wy = p.y - a.y, wz = p.z - a.z;

@@ -78,6 +78,25 @@ def test_batch_equals_alone(cdr, cases, alone):
     b.close()
 
 
+def test_batch_equals_alone_mixed_rounds(cdr, cases):
+    """Mixed rounds: every instance takes all its flagged elements each round;
+    still the same mesh alone and in the batch."""
+    res = []
+    for e, plc, B in cases[:3]:
+        h = cdr.Handle.create(*_args(e, plc), mixed_rounds=True)
+        st = h.refine(B)
+        res.append((h.export(), st))
+        h.close()
+    b = cdr.Batch(mixed_rounds=True)
+    slots = [b.add(B, *_args(e, plc)) for e, plc, B in cases[:3]]
+    b.refine()
+    for k, (ex, st) in zip(slots, res):
+        assert_same_mesh(b.export(k), ex, "mixed instance %d" % k)
+        assert b.stats(k)["steiner_inserted"] == st["steiner_inserted"]
+        assert b.stats(k)["rounds"] == st["rounds"]
+    b.close()
+
+
 def test_late_admission_and_slot_reuse(cdr, cases, alone):
     b = cdr.Batch()
     s0 = b.add(cases[0][2], *_args(*cases[0][:2]))

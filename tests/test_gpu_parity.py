@@ -171,6 +171,27 @@ def test_rounds_lockstep_constrained(cdr):
     assert h.round(1.4)["cls"] == -1
 
 
+def test_rounds_lockstep_mixed(cdr):
+    """Mixed rounds (every flagged element is a candidate; the class decides
+    priority first): same classes, candidates, outcomes and meshes as the
+    oracle's mixed mode R, round by round, to the end."""
+    om, e, plc = oracle_case("uniform", 700, 7, 7, 5)
+    om.set_mixed(True)
+    h = gpu_handle(cdr, e, plc, mixed_rounds=True)
+    classes = _lockstep(cdr, om, h, 1.4, 3000, "mixed700")
+    assert 3 in classes
+    assert h.round(1.4)["cls"] == -1
+
+
+def test_rounds_lockstep_mixed_stall(cdr):
+    """Mixed rounds with dense free segments: the stall rule applies per round
+    to the subsegment candidates, identically on both sides."""
+    om, e, plc = oracle_case("uniform", 2000, 120, 10, 1)
+    om.set_mixed(True)
+    h = gpu_handle(cdr, e, plc, mixed_rounds=True)
+    _lockstep(cdr, om, h, 1.4, 40, "mixed-stall2000")
+
+
 def test_rounds_lockstep_subsegment_stall(cdr):
     """Dense free segments: two nearby segments whose midpoints encroach one
     another stall a subsegment round (round 46 here); both implementations give

@@ -105,6 +105,39 @@ def test_refine_constrained_both_modes():
     assert max(sS["inserted"], sR["inserted"]) <= 1.15 * min(sS["inserted"], sR["inserted"])
 
 
+def test_mixed_rounds_contract_band_and_fewer_rounds():
+    """Mixed rounds (every flagged element a candidate, class first in the
+    priority): a valid refinement within the 1.15x band of mode S, in fewer
+    rounds than one class per round."""
+    B = 1.4
+    mS, pts, e, plc = constrained_mesh(600, 6, 6, seed=8)
+    m1 = oracle.Mesh.create(e["xyz"], e["tets"])
+    m1.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"], plc["nfacets"])
+    mM = oracle.Mesh.create(e["xyz"], e["tets"])
+    mM.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"], plc["nfacets"])
+    mM.set_mixed(True)
+    sS = mS.refine_S(B)
+    s1 = m1.refine_R(B)
+    sM = mM.refine_R(B)
+    assert_contract(mM.check(B), B)
+    assert max(sS["inserted"], sM["inserted"]) <= 1.15 * min(sS["inserted"], sM["inserted"])
+    assert sM["rounds"] < s1["rounds"]
+    # a mixed round serves several classes while they are all flagged
+    mM2 = oracle.Mesh.create(e["xyz"], e["tets"])
+    mM2.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"], plc["nfacets"])
+    mM2.set_mixed(True)
+    seen = set()
+    while True:
+        c = mM2.round(B)["cls"]
+        if c < 0:
+            break
+        seen.add(c)
+        if c == 3:
+            rep = mM2.report()
+            assert len(rep["keys"]) > 0
+    assert 3 in seen
+
+
 def test_mode_R_survivors_touch_disjoint_sets():
     m, *_ = constrained_mesh(800, 8, 8, seed=6)
     B = 1.4
