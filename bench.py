@@ -456,8 +456,10 @@ def workload_config(args, world):
     return {"workload": args.workload, "points": w["n"] + 8, "segments": w["n_seg"],
             "triangles": w["n_tri"], "B": w["B"],
             "parallelism": "independent instances x%d (replicas)" % world,
-            "rounds": "mixed (every class each round, class-first priority)"
-                      if getattr(args, "mixed", False) else "one class per round"}
+            "rounds": {0: "one class per round",
+                       1: "mixed: every class each round, class-first priority",
+                       2: "mixed: subsegments and subfaces together, class-first priority"}[
+                           getattr(args, "mixed", 0)]}
 
 
 # ---------------------------------------------------------- CPU (oracle) arm
@@ -528,8 +530,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mixed", action="store_true",
-                    help="mixed rounds: every flagged element is a candidate each round")
+    ap.add_argument("--mixed", type=int, default=0, choices=[0, 1, 2],
+                    help="round kind: 0 one class per round, 1 every class, "
+                         "2 subsegments and subfaces together")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

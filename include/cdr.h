@@ -99,8 +99,9 @@ typedef struct {
                            subsegments, subfaces, bad tetrahedra (Sec. 2's order);
                            1: each round takes every flagged element, and the
                            class decides priority first, so a subsegment still
-                           beats a subface and a subface beats a tetrahedron
-                           (fewer rounds)                                       */
+                           beats a subface and a subface beats a tetrahedron;
+                           2: subsegments and subfaces together, bad
+                           tetrahedra only once both are done (fewer rounds) */
 } cdr_options;
 
 /* Per-call statistics. */

@@ -294,8 +294,9 @@ class Mesh:
                     flagG=flg[: sz[5]].reshape(-1, 2), inserted=int(sz[6]))
 
     def set_mixed(self, mixed):
-        """Mode R with every class in every round (class-first priorities)."""
-        lib().orc_set_mixed(self.h, int(bool(mixed)))
+        """Round kind: 0/False one class, 1/True every class, 2 subsegments and
+        subfaces together (class-first priorities)."""
+        lib().orc_set_mixed(self.h, int(mixed))
 
     def refine_R(self, B, max_rounds=1 << 30):
         out = (ctypes.c_long * 2)()

@@ -304,8 +304,9 @@ void orc_set_flags(void* hp, const uint8_t* tunspl, const uint8_t* sfflag, const
     }
 }
 
-// Mode-R round kind: 0 one class per round, 1 every class in every round.
-void orc_set_mixed(void* hp, int mixed) { ((Handle*)hp)->M.mixed = mixed != 0; }
+// Mode-R round kind: 0 one class per round, 1 every class in every round,
+// 2 subsegments and subfaces together.
+void orc_set_mixed(void* hp, int mixed) { ((Handle*)hp)->M.mixed = mixed; }
 
 // One mode-R round. out: [class (-1 if done), candidates, inserted]
 int orc_round(void* hp, double B, int* out) {

@@ -75,9 +75,10 @@ struct Mesh {
   std::vector<V3> facetQ;                                 // per-facet reference point
   double guard2 = 0.0;                                    // squared shortest-edge guard
   int walk_limit = 100000;
-  // rounds in which every flagged element is a candidate, whatever its class
-  // (the class decides priority first); false: one class per round
-  bool mixed = false;
+  // which classes a round takes: 0 the first non-empty class only; 1 every
+  // class; 2 subsegments and subfaces together, tetrahedra only once both are
+  // empty (the class decides priority first)
+  int mixed = 0;
   int cav_limit = 4096;
 
   const double* X(int v) const { return P[v].data(); }

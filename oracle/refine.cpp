@@ -721,9 +721,9 @@ static void apply_flags(Mesh& M, const Decision& d) {
 // those holding the minimum priority on every touched element, apply the flags
 // of the others, insert the kept points (new vertex ids in priority order).
 // One round (Sec. 2): the candidates are the flagged elements of the first
-// non-empty class (subsegments, subfaces, bad tetrahedra), or of every class
-// when M.mixed (class-first priorities then keep the split order inside the
-// round). Every candidate is evaluated on the same snapshot; those whose
+// non-empty class (subsegments, subfaces, bad tetrahedra), of every class
+// when M.mixed == 1, or of subsegments and subfaces together when M.mixed == 2
+// (class-first priorities then keep the split order inside the round). Every candidate is evaluated on the same snapshot; those whose
 // regions hold all their marks are inserted. Returns the class served (3 for a
 // round with several classes), -1 when nothing is left.
 int round_R(Mesh& M, double B, RoundReport* rep) {
@@ -739,7 +739,8 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
   if (cls < 0) return -1;
   std::vector<Cand> cands;
   int present = 0;
-  for (int c = cls; c <= (M.mixed ? 2 : cls); ++c)
+  const int hi = M.mixed == 1 ? 2 : (M.mixed == 2 && cls <= 1 ? 1 : cls);
+  for (int c = cls; c <= hi; ++c)
     for (int e : q[c]) {
       Cand cd;
       cand_key(M, c, e, cd);

@@ -242,7 +242,7 @@ class Handle:
                guard2=0.0, walk_limit=0, reserve_factor=0, mixed_rounds=False, allocator=None,
                stream=None):
         mi, _arrays = _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref)
-        opt = Options(float(guard2), int(walk_limit), int(reserve_factor), int(bool(mixed_rounds)))
+        opt = Options(float(guard2), int(walk_limit), int(reserve_factor), int(mixed_rounds))
         out = ctypes.c_void_p()
         al = ctypes.byref(allocator.struct) if allocator is not None else None
         st = lib().cdr_create(ctypes.byref(mi), ctypes.byref(opt), al, _stream_handle(stream),
@@ -347,7 +347,7 @@ class Batch:
     STATE = {0: "free", 1: "refining", 2: "done"}
 
     def __init__(self, guard2=0.0, walk_limit=0, mixed_rounds=False, allocator=None, stream=None):
-        opt = Options(float(guard2), int(walk_limit), 0, int(bool(mixed_rounds)))
+        opt = Options(float(guard2), int(walk_limit), 0, int(mixed_rounds))
         out = ctypes.c_void_p()
         al = ctypes.byref(allocator.struct) if allocator is not None else None
         _check(lib().cdr_batch_create(ctypes.byref(opt), al, _stream_handle(stream),

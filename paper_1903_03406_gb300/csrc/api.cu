@@ -80,7 +80,7 @@ struct cdr_handle {
   std::vector<int> instCls;              // host copy of the round's classes
   // batch bookkeeping (host)
   bool batch = false;
-  bool mixed = false;  // every flagged element is a candidate in every round
+  int mixed = 0;  // round kind: 0 one class, 1 every class, 2 subsegments + subfaces
   struct Inst {
     int state = 0;  // 0 free slot, 1 refining, 2 done
     int of = 0, nf = 0, oseg = 0, nseg = 0;
@@ -625,7 +625,8 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   // stall rule for instances serving subsegments (decided on the device)
   if (cls == CLS_SUBSEG ||
       (cls < 0 && (std::find(h->instCls.begin(), h->instCls.end(), CLS_SUBSEG) != h->instCls.end() ||
-                   std::find(h->instCls.begin(), h->instCls.end(), 3) != h->instCls.end()))) {
+                   std::find(h->instCls.begin(), h->instCls.end(), 3) != h->instCls.end() ||
+                   std::find(h->instCls.begin(), h->instCls.end(), 4) != h->instCls.end()))) {
     launch_stall(m, r, s);
     h->prof_ctr[15] += 1;
   }
@@ -766,16 +767,21 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
   h->instCls.assign(ni, -1);
   long long n = 0;
   for (int k = 0; k < ni; ++k) {
-    int present = 0;
-    for (int c = 0; c < 3; ++c)
-      if (h->pinCnt[3 * k + c] > 0) {
-        present |= 1 << c;
-        if (h->instCls[k] < 0) h->instCls[k] = c;
-        if (!h->mixed) break;  // the first non-empty class only
-      }
-    if (h->mixed && (present & (present - 1))) h->instCls[k] = 3;  // several classes
-    for (int c = 0; c < 3; ++c)
-      if (present & (1 << c)) n += (long long)h->pinCnt[3 * k + c];
+    int c0 = -1;
+    for (int c = 0; c < 3 && c0 < 0; ++c)
+      if (h->pinCnt[3 * k + c] > 0) c0 = c;
+    if (c0 >= 0) {
+      // classes taken: the first non-empty one, or up to hi in mixed rounds
+      const int hi = h->mixed == 1 ? 2 : (h->mixed == 2 && c0 <= 1 ? 1 : c0);
+      int present = 0;
+      for (int c = c0; c <= hi; ++c)
+        if (h->pinCnt[3 * k + c] > 0) {
+          present |= 1 << c;
+          n += (long long)h->pinCnt[3 * k + c];
+        }
+      // 0..2 one class; 3 every class; 4 subsegments and subfaces
+      h->instCls[k] = (present & (present - 1)) ? (hi == 2 ? 3 : 4) : c0;
+    }
     h->pinCls[k] = h->instCls[k];
   }
   if (ro) *ro = RoundOut();
@@ -822,7 +828,7 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
                       s);
   h->prof_ctr[15] += 1;
   st = round_core(h, -1, (int)n, B, ro);
-  if (ro) ro->cls = ni == 1 ? h->instCls[0] : 3;  // 3: several classes or instances
+  if (ro) ro->cls = ni == 1 ? std::min(h->instCls[0], 3) : 3;  // 3: several classes or instances
   return st;
 }
 
@@ -1034,7 +1040,7 @@ extern "C" int cdr_create(const cdr_mesh_in* in, const cdr_options* opt, const c
     h->has_alloc = true;
   }
   int rf = (opt && opt->reserve_factor > 0) ? opt->reserve_factor : 4;
-  h->mixed = opt && opt->mixed_rounds != 0;
+  h->mixed = opt ? opt->mixed_rounds : 0;
   h->m.walk_limit = (opt && opt->walk_limit > 0) ? opt->walk_limit : 100000;
   h->m.guard2 = (opt && opt->guard2 > 0) ? opt->guard2 : default_guard2(in->xyz, in->n_verts);
   h->m.nF = in->n_facets;
@@ -1606,7 +1612,7 @@ int cdr_batch_create(const cdr_options* opt, const cdr_allocator* alloc, void* s
     h->has_alloc = true;
   }
   h->batch = true;
-  h->mixed = opt && opt->mixed_rounds != 0;
+  h->mixed = opt ? opt->mixed_rounds : 0;
   h->ninst = 0;
   if (opt) h->opts = *opt;
   h->opts.reserve_factor = 1;  // an instance is built at its own size, then appended
@@ -1722,7 +1728,8 @@ int cdr_batch_round(cdr_handle* h, int32_t* n_active) {
       I.st.rounds_by_class[c]++;
       I.st.candidates += (long long)h->pinCnt[3 * k + c];
     } else {
-      I.st.candidates += (long long)(h->pinCnt[3 * k] + h->pinCnt[3 * k + 1] + h->pinCnt[3 * k + 2]);
+      I.st.candidates += (long long)(h->pinCnt[3 * k] + h->pinCnt[3 * k + 1] +
+                                     (c == 3 ? h->pinCnt[3 * k + 2] : 0));
     }
     if (ran) {
       const unsigned long long* q = h->pinSt + (size_t)k * IS_COUNT;

@@ -674,8 +674,9 @@ __global__ void k_round_flags(DevMesh m, const uint8_t* candG, const uint8_t* ca
       f = candT[e] != 0;
       if (f) v0 = vid(m.T[CKI(e, m.capT)].v.x);
     }
-    const int sel = f ? m.instCls[vinst(m, v0)] : -1;  // 3: every class
-    out[i] = (f && (sel == c || sel == 3)) ? 1 : 0;
+    // sel: 0..2 one class, 3 every class, 4 subsegments and subfaces
+    const int sel = f ? m.instCls[vinst(m, v0)] : -1;
+    out[i] = (f && (sel == c || sel == 3 || (sel == 4 && c <= CLS_SUBFACE))) ? 1 : 0;
   }
 }
 

@@ -183,6 +183,17 @@ def test_rounds_lockstep_mixed(cdr):
     assert h.round(1.4)["cls"] == -1
 
 
+def test_rounds_lockstep_boundary_mixed(cdr):
+    """Subsegments and subfaces together, tetrahedra once both are done:
+    lockstep with the oracle's mode R to the end."""
+    om, e, plc = oracle_case("uniform", 700, 7, 7, 5)
+    om.set_mixed(2)
+    h = gpu_handle(cdr, e, plc, mixed_rounds=2)
+    classes = _lockstep(cdr, om, h, 1.4, 3000, "boundary-mixed700")
+    assert 3 in classes and 2 in classes
+    assert h.round(1.4)["cls"] == -1
+
+
 def test_rounds_lockstep_mixed_stall(cdr):
     """Mixed rounds with dense free segments: the stall rule applies per round
     to the subsegment candidates, identically on both sides."""
