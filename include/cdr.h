@@ -261,17 +261,20 @@ const char* cdr_status_string(int status);
  * handle's stream, and device work counters (always accumulated).
  *   enable   1 on, 2 on for the region-growth groups (4, 5) only, 0 off,
  *            -1 unchanged;  reset  nonzero clears the totals first
- *   ms[16]   accumulated milliseconds per group: 0 classify, 1 order, 2 split,
+ *   ms[32]   accumulated milliseconds per group: 0 classify, 1 order, 2 split,
  *            3 locate, 4 grow (tier 1), 5 grow (tier 2), 6 select, 7 scan,
- *            8 insert, 9 compact
- *   calls[16] launches timed per group
- *   counters[16] 0 refused, 1 unsplittable, 2 eligible-but-blasted, 3 inserted,
+ *            8 insert, 9 compact, 10 whole rounds run as one kernel (rounds
+ *            with at most 64 candidates)
+ *   calls[32] launches timed per group
+ *   counters[32] 0 refused, 1 unsplittable, 2 eligible-but-blasted, 3 inserted,
  *            4 retried in tier 2, 5 invariant failures, 6 neighbour tetrahedra
- *            tested by growth, 7 cavity tetrahedra, 8 boundary faces, 9 new
+ *            tested by growth, 7 cavity tetrahedra, 8 boundary faces (6..8 in
+ *            rounds with separately launched growth kernels), 9 new
  *            tetrahedra written, 10 refusals flagging a new candidate, 11 regions
  *            stopped on a higher-priority start, 12 tetrahedra retired by
  *            insertion, 15 kernels of this library launched (library
- *            primitives such as sorts and scans excluded)
+ *            primitives such as sorts and scans excluded), 16..18 as 6..8 in
+ *            rounds run as one kernel
  * Any output pointer may be NULL. */
 int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_t* calls,
                 int64_t* counters);

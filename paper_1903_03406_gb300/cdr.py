@@ -285,15 +285,16 @@ class Handle:
         return d
 
     GROUPS = ["classify", "order", "split", "locate", "grow1", "grow2", "select", "scan",
-              "insert", "compact"]
+              "insert", "compact", "fused"]
     COUNTERS = ["refused", "unsplittable", "blasted", "inserted", "retried", "invariant",
                 "tested", "cavity", "boundary", "new_tets", "new_candidates", "blasted_early",
-                "dead_tets", "c13", "c14", "launches"]
+                "dead_tets", "c13", "c14", "launches", "fused_tested", "fused_cavity",
+                "fused_boundary"]
 
     def profile(self, enable=-1, reset=False):
-        ms = np.zeros(16)
-        calls = np.zeros(16, dtype=np.int64)
-        ctr = np.zeros(16, dtype=np.int64)
+        ms = np.zeros(32)
+        calls = np.zeros(32, dtype=np.int64)
+        ctr = np.zeros(32, dtype=np.int64)
         _check(lib().cdr_profile(self.ptr, int(enable), int(bool(reset)), _p(ms, ctypes.c_double),
                                  _p(calls, ctypes.c_int64), _p(ctr, ctypes.c_int64)),
                "cdr_profile")

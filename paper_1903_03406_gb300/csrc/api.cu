@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -56,7 +57,7 @@ struct cdr_handle {
   // round buffers
   int capR = 0, capR2 = 0, capWs2 = 0;
   Buf bCand, bCand2, bKeys, bKeys2, bSp, bLoc, bStatus, bSurv, bCounts, bOffs, bSlab1, bSlab2of,
-      bList2, bSlab2, bWs2, bCkey, bTmp, bStats, bErr, bI32;
+      bList2, bSlab2, bWs2, bCkey, bTmp, bStats, bErr, bI32, bFused;
   size_t tmpBytes = 0;
   // points (Delaunay mode)
   Buf bPts, bHint, bPstate;
@@ -66,10 +67,11 @@ struct cdr_handle {
   // profiling: events around each kernel group, accumulated per round
   bool prof = false;
   bool profGrowOnly = false;  // time the region-growth groups only
-  cudaEvent_t ev[2 * 16] = {};
-  double prof_ms[16] = {};
-  long long prof_calls[16] = {};
-  long long prof_ctr[16] = {};
+  cudaEvent_t ev[2 * 32] = {};
+  bool fused = true;  // small rounds as one kernel
+  double prof_ms[32] = {};
+  long long prof_calls[32] = {};
+  long long prof_ctr[32] = {};
   // instances: a plain handle holds one; a batch holds several as disconnected
   // parts of this mesh (Vinst set)
   int ninst = 1, capI = 0;
@@ -368,7 +370,7 @@ unsigned next_epoch(cdr_handle* h) { return 0xFFFFFFFFu - (++h->epoch); }
 
 // kernel groups timed when profiling is on
 enum { PG_CLASSIFY = 0, PG_ORDER, PG_SPLIT, PG_LOCATE, PG_GROW1, PG_GROW2, PG_SELECT, PG_SCAN,
-       PG_INSERT, PG_COMPACT, PG_N };
+       PG_INSERT, PG_COMPACT, PG_FUSED, PG_N };
 inline void pmark(cdr_handle* h, int g, int which) {
   if (!h->prof) return;
   if (h->profGrowOnly && g != PG_GROW1 && g != PG_GROW2) return;
@@ -542,11 +544,106 @@ int maybe_compact(cdr_handle* h, bool force) {
   return cuda_status(h);
 }
 
+// A refinement round with few candidates as one kernel (k_round_fused): the
+// capacity for the largest growth the kernel could produce is reserved first,
+// the totals are read back once at the end.
+int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
+  DevMesh& m = h->m;
+  cudaStream_t s = h->stream;
+  using T2 = Tier2;
+  if (!grow_verts(h, m.nV + n) || !grow_tets(h, m.nT + n * T2::CAPB) ||
+      !grow_subfaces(h, m.nS + n * T2::CAPFB) || !grow_subsegs(h, m.nG + n) ||
+      !ensure(h, h->bSlab2, (size_t)n * SlabLayout<T2>::STRIDE * 4) ||
+      !ensure(h, h->bWs2, (size_t)kFusedBlocks * kFusedWarps * T2::HCAP * 4) ||
+      !ensure(h, h->bFused, sizeof(FusedOut)))
+    return h->err ? h->err : CDR_ERR_OOM;
+  if ((size_t)(h->hcount + 2 * n) * 2 > (size_t)m.hmask + 1) {
+    if (!rebuild_hash(h, (m.nG + 2 * n) * 2)) return CDR_ERR_OOM;
+  }
+  DevRound r = make_round(h, cls, n, B);
+  r.slab2 = ptr<int>(h->bSlab2);
+  r.ws2 = ptr<int>(h->bWs2);
+  r.nws2 = kFusedBlocks * kFusedWarps;
+  r.ckey = ptr<int4>(h->bCkey);
+  r.seed_epoch = next_epoch(h);
+  r.epoch = next_epoch(h);
+  cudaMemsetAsync(h->bStats.p, 0, ST_COUNT * 8, s);
+  cudaMemsetAsync(h->bInstSt.p, 0, (size_t)h->ninst * IS_COUNT * 8, s);
+  cudaMemsetAsync(h->bFused.p, 0, sizeof(FusedOut), s);
+  const bool stall =
+      cls == CLS_SUBSEG ||
+      (cls < 0 && (std::find(h->instCls.begin(), h->instCls.end(), CLS_SUBSEG) != h->instCls.end() ||
+                   std::find(h->instCls.begin(), h->instCls.end(), 3) != h->instCls.end() ||
+                   std::find(h->instCls.begin(), h->instCls.end(), 4) != h->instCls.end()));
+  bool used[PG_N] = {};
+  pmark(h, PG_FUSED, 0);
+  launch_round_fused(m, r, ptr<int>(h->bHint), ptr<int4>(h->bOffs), ptr<FusedOut>(h->bFused),
+                     stall, s);
+  pmark(h, PG_FUSED, 1);
+  used[PG_FUSED] = true;
+  h->prof_ctr[15] += 1;
+  FusedOut fo;
+  cudaMemcpyAsync(&h->pin->lastOff, ptr<char>(h->bFused), sizeof(int4), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&h->pin->n2, ptr<char>(h->bFused) + offsetof(FusedOut, n2), 4,
+                  cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h->pin->ctr, h->bStats.p, sizeof(h->pin->ctr), cudaMemcpyDeviceToHost, s);
+  h->pin->ovf = 0;
+  exact_overflow_copy_async(&h->pin->ovf, s);
+  if (h->batch)
+    cudaMemcpyAsync(h->pinSt, h->bInstSt.p, (size_t)h->ninst * IS_COUNT * 8,
+                    cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (cuda_status(h)) return h->err;
+  fo.tot = h->pin->lastOff;
+  fo.n2 = h->pin->n2;
+  if (h->pin->ovf) {
+    exact_overflow_flag(s, true);
+    return set_err(h, CDR_ERR_INTERNAL);
+  }
+  {
+    int info[4];
+    if (checked_error(info, s)) {
+      fprintf(stderr, "cdr checked build: bad index %d (bound %d) at kernels.cu:%d, round %u\n",
+              info[2], info[3], info[1], h->epoch);
+      return set_err(h, CDR_ERR_INTERNAL);
+    }
+  }
+  const unsigned long long* ctr = h->pin->ctr;
+  if (ctr[ST_ITER]) return set_err(h, CDR_ERR_INTERNAL);
+  m.nV += fo.tot.x;
+  m.nT += fo.tot.y;
+  m.nS += fo.tot.z;
+  m.nG += fo.tot.w;
+  h->hcount += 2 * fo.tot.w;
+  h->lastN = n;
+  h->lastN2 = fo.n2;
+  h->lastCls = cls;
+  if (ro) {
+    ro->cls = cls;
+    ro->cand = n;
+    ro->ins = (long long)ctr[ST_SURV];
+    ro->rej = (long long)ctr[ST_REJECT];
+    ro->unspl = (long long)ctr[ST_UNSPL];
+    ro->blasted = (long long)ctr[ST_OK] + (long long)ctr[ST_BLAST];
+  }
+  pcollect(h, used);
+  // growth work of fused rounds is counted apart (16..18) from the separately
+  // launched growth kernels (6..8), whose timings the roofline uses
+  for (int k = 0; k < ST_COUNT && k < 15; ++k)
+    if (k != ST_TESTED && k != ST_CAV && k != ST_BND) h->prof_ctr[k] += (long long)ctr[k];
+  h->prof_ctr[16] += (long long)ctr[ST_TESTED];
+  h->prof_ctr[17] += (long long)ctr[ST_CAV];
+  h->prof_ctr[18] += (long long)ctr[ST_BND];
+  h->deadT += (long long)ctr[ST_DEADT];
+  return cuda_status(h);
+}
+
 // the shared body of a round once the ordered candidate list is in bCand2
 int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   DevMesh& m = h->m;
   cudaStream_t s = h->stream;
   if (!ensure_pinned(h)) return CDR_ERR_OOM;
+  if (cls != CLS_POINT && n <= kFusedMax && h->fused) return round_fused(h, cls, n, B, ro);
   DevRound r = make_round(h, cls, n, B);
   cudaMemsetAsync(h->bStats.p, 0, ST_COUNT * 8, s);
   if (cls != CLS_POINT) cudaMemsetAsync(h->bInstSt.p, 0, (size_t)h->ninst * IS_COUNT * 8, s);
@@ -911,7 +1008,7 @@ void cdr_destroy(cdr_handle* h) {
                 &h->bOffs, &h->bSlab1, &h->bSlab2of, &h->bList2, &h->bSlab2, &h->bWs2, &h->bCkey,
                 &h->bTmp, &h->bStats, &h->bErr, &h->bI32, &h->bPts, &h->bHint, &h->bPstate,
                 &h->bVinst, &h->bInstB, &h->bInstG2, &h->bInstCls, &h->bInstCnt, &h->bInstSt,
-                &h->bCcls, &h->bCinst, &h->bRflags, &h->bDirtyS, &h->bDirtyG};
+                &h->bCcls, &h->bCinst, &h->bRflags, &h->bDirtyS, &h->bDirtyG, &h->bFused};
   for (Buf* b : all) dfree(h, *b);
   for (Buf& b : h->ck) dfree(h, b);
   for (auto& e : h->ev)
@@ -1983,18 +2080,18 @@ int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_
                 int64_t* counters) {
   if (!h) return CDR_ERR_INVALID_INPUT;
   if (reset) {
-    for (int g = 0; g < 16; ++g) {
+    for (int g = 0; g < 32; ++g) {
       h->prof_ms[g] = 0;
       h->prof_calls[g] = 0;
       h->prof_ctr[g] = 0;
     }
   }
   if (ms)
-    for (int g = 0; g < 16; ++g) ms[g] = h->prof_ms[g];
+    for (int g = 0; g < 32; ++g) ms[g] = h->prof_ms[g];
   if (calls)
-    for (int g = 0; g < 16; ++g) calls[g] = h->prof_calls[g];
+    for (int g = 0; g < 32; ++g) calls[g] = h->prof_calls[g];
   if (counters)
-    for (int g = 0; g < 16; ++g) counters[g] = h->prof_ctr[g];
+    for (int g = 0; g < 32; ++g) counters[g] = h->prof_ctr[g];
   if (enable >= 0) {
     h->prof = enable != 0;
     h->profGrowOnly = enable == 2;

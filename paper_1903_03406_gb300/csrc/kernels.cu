@@ -8,6 +8,7 @@
 // work proportional to region size), keep the points that hold every mark
 // (k_select: the "blast" step), and insert the kept points concurrently,
 // re-linking the new stars to the rest of the mesh (k_insert).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -681,39 +682,45 @@ __global__ void k_round_flags(DevMesh m, const uint8_t* candG, const uint8_t* ca
 }
 
 // ============================================================ split + locate
+// splitting point of candidate i (Sec. 2: midpoint, subface circumcentre,
+// tetrahedron circumcentre)
+__device__ void split_one(const DevMesh& m, const DevRound& r, int i) {
+  int e = r.cand[i];
+  const int cls = cls_of(r, i);
+  D3 p{0, 0, 0};
+  bool ok = true;
+  if (cls == CLS_SUBSEG) {
+    int4 G = m.GV[CKI(e, m.capG)];
+    p = midpoint_fixed(vtx(m, min(G.x, G.y)), vtx(m, max(G.x, G.y)));
+    ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
+  } else if (cls == CLS_SUBFACE) {
+    int ids[4];
+    elem_key(m, CLS_SUBFACE, e, ids);
+    ok = tri_circumcenter_fixed(vtx(m, ids[0]), vtx(m, ids[1]), vtx(m, ids[2]), p);
+  } else if (cls == CLS_TET) {
+    int ids[4];
+    elem_key(m, CLS_TET, e, ids);
+    D3 off;
+    ok = tet_circumcenter_fixed(vtx(m, ids[0]), vtx(m, ids[1]), vtx(m, ids[2]),
+                                vtx(m, ids[3]), p, off);
+  } else {
+    p = D3{r.given[3 * e], r.given[3 * e + 1], r.given[3 * e + 2]};
+    ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
+  }
+  r.sp[i] = make_v4(p.x, p.y, p.z, 0.0);
+  r.loc[i] = -1;
+  set_status(r, i, ok ? OUT_OK : OUT_UNSPL, ok ? RS_NONE : RS_BADPOINT);
+  r.slab2_of[i] = -1;
+  if (r.ckey) {
+    int ids[4] = {-1, -1, -1, -1};
+    elem_key(m, cls, e, ids);
+    r.ckey[i] = make_int4(ids[0], ids[1], ids[2], ids[3]);
+  }
+}
+
 __global__ void k_split(DevMesh m, DevRound r) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
-    int e = r.cand[i];
-    const int cls = cls_of(r, i);
-    D3 p{0, 0, 0};
-    bool ok = true;
-    if (cls == CLS_SUBSEG) {
-      int4 G = m.GV[CKI(e, m.capG)];
-      p = midpoint_fixed(vtx(m, min(G.x, G.y)), vtx(m, max(G.x, G.y)));
-      ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
-    } else if (cls == CLS_SUBFACE) {
-      int ids[4];
-      elem_key(m, CLS_SUBFACE, e, ids);
-      ok = tri_circumcenter_fixed(vtx(m, ids[0]), vtx(m, ids[1]), vtx(m, ids[2]), p);
-    } else if (cls == CLS_TET) {
-      int ids[4];
-      elem_key(m, CLS_TET, e, ids);
-      D3 off;
-      ok = tet_circumcenter_fixed(vtx(m, ids[0]), vtx(m, ids[1]), vtx(m, ids[2]),
-                                  vtx(m, ids[3]), p, off);
-    } else {
-      p = D3{r.given[3 * e], r.given[3 * e + 1], r.given[3 * e + 2]};
-      ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
-    }
-    r.sp[i] = make_v4(p.x, p.y, p.z, 0.0);
-    r.loc[i] = -1;
-    set_status(r, i, ok ? OUT_OK : OUT_UNSPL, ok ? RS_NONE : RS_BADPOINT);
-    r.slab2_of[i] = -1;
-    if (r.ckey) {
-      int ids[4] = {-1, -1, -1, -1};
-      elem_key(m, cls, e, ids);
-      r.ckey[i] = make_int4(ids[0], ids[1], ids[2], ids[3]);
-    }
+    split_one(m, r, i);
   }
 }
 
@@ -721,113 +728,119 @@ __global__ void k_split(DevMesh m, DevRound r) {
 // among those p lies strictly beyond) and the facet walk (same rule on edges).
 __device__ __forceinline__ void seed_claim(const DevMesh& m, const DevRound& r, int i);
 
+// locate candidate i's point (and, in refinement rounds, claim its start
+// tetrahedra)
+__device__ void locate_one(const DevMesh& m, const DevRound& r, int* hint, int i) {
+  if (r.status[i] != OUT_OK) return;
+  int e = r.cand[i];
+  const int cls = cls_of(r, i);
+  V4 q = r.sp[i];
+  D3 p{q.x, q.y, q.z};
+  if (cls == CLS_TET || cls == CLS_POINT) {
+    int t = cls == CLS_TET ? e : hint[e];
+    bool done = false;
+    for (int it = 0; it < m.walk_limit && !done; ++it) {
+      TetRec rec = ld_tet(m, t);
+      int vv[4] = {vid(rec.v.x), vid(rec.v.y), vid(rec.v.z), vid(rec.v.w)};
+      D3 c[4] = {vtx(m, vv[0]), vtx(m, vv[1]), vtx(m, vv[2]), vtx(m, vv[3])};
+      int best = -1, b0 = 0, b1 = 0, b2 = 0;
+      for (int f = 0; f < 4; ++f) {
+        if (orient_rep4(c, f, p) < 0) {
+          int w[3], k = 0;
+          for (int j = 0; j < 4; ++j)
+            if (j != f) w[k++] = vv[j];
+          sort3(w[0], w[1], w[2]);
+          if (best < 0 || lt3(w[0], w[1], w[2], b0, b1, b2)) {
+            best = f;
+            b0 = w[0];
+            b1 = w[1];
+            b2 = w[2];
+          }
+        }
+      }
+      if (best < 0) {
+        r.loc[i] = t;
+        done = true;
+        break;
+      }
+      if (face_sub(rec.v, best)) {
+        int s = ts_ptr(m, t)[best];
+        if (s < 0 || s >= m.nS) {
+          atomicAdd(&r.stats[ST_ITER], 1ULL);
+          set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
+          done = true;
+          break;
+        }
+        if (m.Sflag[CKI(s, m.capS)] & F_UNSPL) {
+          set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
+        } else {
+          set_status(r, i, OUT_REJECT, RS_WALK_SUBFACE);
+        }
+        m.Smust[CKI(s, m.capS)] = 1;
+        m.dirtyS[CKI(s, m.capS)] = 1;
+        done = true;
+        break;
+      }
+      int n = geti(rec.n, best);
+      if (n < 0) {
+        set_status(r, i, OUT_UNSPL, RS_WALK_HULL);
+        done = true;
+        break;
+      }
+      t = n >> 2;
+    }
+    if (!done) set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
+  } else if (cls == CLS_SUBFACE) {
+    int s = e;
+    bool done = false;
+    for (int it = 0; it < m.walk_limit && !done; ++it) {
+      int4 S = m.SV[CKI(s, m.capS)];
+      int w = sf_wind(m, S);
+      int best = -1, b0 = 0, b1 = 0;
+      for (int k = 0; k < 3; ++k) {
+        if (sf_orient_rep(m, S, k, p) == -w) {
+          int u = geti(S, (k + 1) % 3), x = geti(S, (k + 2) % 3);
+          int e0 = min(u, x), e1 = max(u, x);
+          if (best < 0 || e0 < b0 || (e0 == b0 && e1 < b1)) {
+            best = k;
+            b0 = e0;
+            b1 = e1;
+          }
+        }
+      }
+      if (best < 0) {
+        r.loc[i] = s;
+        done = true;
+        break;
+      }
+      int nb = geti(m.SN[CKI(s, m.capS)], best);
+      if (nb < 0) {
+        int g = hash_lookup(m, ekey(b0, b1));
+        if (g < 0) {
+          set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
+        } else {
+          if (m.Gflag[CKI(g, m.capG)] & F_UNSPL) set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
+          else set_status(r, i, OUT_REJECT, RS_WALK_SUBSEG);
+          m.Gmust[CKI(g, m.capG)] = 1;
+          m.dirtyG[CKI(g, m.capG)] = 1;
+        }
+        done = true;
+        break;
+      }
+      s = nb;
+    }
+    if (!done) set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
+  } else {
+    r.loc[i] = e;
+  }
+  // refinement rounds claim their start tetrahedra here (points do it in
+  // k_seed, after their one-per-tetrahedron filter)
+  if (r.cls != CLS_POINT && r.status[i] == OUT_OK) seed_claim(m, r, i);
+}
+
 __global__ void k_locate(DevMesh m, DevRound r, int* hint) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
-    if (r.status[i] != OUT_OK) continue;
-    int e = r.cand[i];
-    const int cls = cls_of(r, i);
-    V4 q = r.sp[i];
-    D3 p{q.x, q.y, q.z};
-    if (cls == CLS_TET || cls == CLS_POINT) {
-      int t = cls == CLS_TET ? e : hint[e];
-      bool done = false;
-      for (int it = 0; it < m.walk_limit && !done; ++it) {
-        TetRec rec = ld_tet(m, t);
-        int vv[4] = {vid(rec.v.x), vid(rec.v.y), vid(rec.v.z), vid(rec.v.w)};
-        D3 c[4] = {vtx(m, vv[0]), vtx(m, vv[1]), vtx(m, vv[2]), vtx(m, vv[3])};
-        int best = -1, b0 = 0, b1 = 0, b2 = 0;
-        for (int f = 0; f < 4; ++f) {
-          if (orient_rep4(c, f, p) < 0) {
-            int w[3], k = 0;
-            for (int j = 0; j < 4; ++j)
-              if (j != f) w[k++] = vv[j];
-            sort3(w[0], w[1], w[2]);
-            if (best < 0 || lt3(w[0], w[1], w[2], b0, b1, b2)) {
-              best = f;
-              b0 = w[0];
-              b1 = w[1];
-              b2 = w[2];
-            }
-          }
-        }
-        if (best < 0) {
-          r.loc[i] = t;
-          done = true;
-          break;
-        }
-        if (face_sub(rec.v, best)) {
-          int s = ts_ptr(m, t)[best];
-          if (s < 0 || s >= m.nS) {
-            atomicAdd(&r.stats[ST_ITER], 1ULL);
-            set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
-            done = true;
-            break;
-          }
-          if (m.Sflag[CKI(s, m.capS)] & F_UNSPL) {
-            set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
-          } else {
-            set_status(r, i, OUT_REJECT, RS_WALK_SUBFACE);
-          }
-          m.Smust[CKI(s, m.capS)] = 1;
-          m.dirtyS[CKI(s, m.capS)] = 1;
-          done = true;
-          break;
-        }
-        int n = geti(rec.n, best);
-        if (n < 0) {
-          set_status(r, i, OUT_UNSPL, RS_WALK_HULL);
-          done = true;
-          break;
-        }
-        t = n >> 2;
-      }
-      if (!done) set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
-    } else if (cls == CLS_SUBFACE) {
-      int s = e;
-      bool done = false;
-      for (int it = 0; it < m.walk_limit && !done; ++it) {
-        int4 S = m.SV[CKI(s, m.capS)];
-        int w = sf_wind(m, S);
-        int best = -1, b0 = 0, b1 = 0;
-        for (int k = 0; k < 3; ++k) {
-          if (sf_orient_rep(m, S, k, p) == -w) {
-            int u = geti(S, (k + 1) % 3), x = geti(S, (k + 2) % 3);
-            int e0 = min(u, x), e1 = max(u, x);
-            if (best < 0 || e0 < b0 || (e0 == b0 && e1 < b1)) {
-              best = k;
-              b0 = e0;
-              b1 = e1;
-            }
-          }
-        }
-        if (best < 0) {
-          r.loc[i] = s;
-          done = true;
-          break;
-        }
-        int nb = geti(m.SN[CKI(s, m.capS)], best);
-        if (nb < 0) {
-          int g = hash_lookup(m, ekey(b0, b1));
-          if (g < 0) {
-            set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
-          } else {
-            if (m.Gflag[CKI(g, m.capG)] & F_UNSPL) set_status(r, i, OUT_UNSPL, RS_ENCROACH_UNSPL);
-            else set_status(r, i, OUT_REJECT, RS_WALK_SUBSEG);
-            m.Gmust[CKI(g, m.capG)] = 1;
-            m.dirtyG[CKI(g, m.capG)] = 1;
-          }
-          done = true;
-          break;
-        }
-        s = nb;
-      }
-      if (!done) set_status(r, i, OUT_UNSPL, RS_WALK_LIMIT);
-    } else {
-      r.loc[i] = e;
-    }
-    // refinement rounds claim their start tetrahedra here (points do it in
-    // k_seed, after their one-per-tetrahedron filter)
-    if (r.cls != CLS_POINT && r.status[i] == OUT_OK) seed_claim(m, r, i);
+    locate_one(m, r, hint, i);
   }
 }
 
@@ -1763,299 +1776,311 @@ __device__ bool holds_marks(const DevMesh& m, const DevRound& r, int i, int lane
   return !__any_sync(FULLMASK, lost);
 }
 
+// outcome counts of the candidates one warp selected
+struct SelAcc {
+  unsigned surv = 0, ok = 0, rej = 0, blast = 0, unspl = 0;
+};
+// select candidate i (called by a whole warp; lane 0 writes)
+__device__ void select_one(const DevMesh& m, const DevRound& r, int i, int lane, SelAcc& a) {
+  const int outcome = r.status[i] & 0xff;
+  const bool surv = outcome == OUT_OK && holds_marks(m, r, i, lane);
+  if (lane != 0) return;
+  const int cls = cls_of(r, i);
+  r.survived[i] = surv ? 1 : 0;
+  int4 c = make_int4(0, 0, 0, 0);
+  if (surv) {
+    bool t2;
+    const int* slab = slab_of(r, i, t2);
+    c = make_int4(cls == CLS_POINT ? 0 : 1, slab[1], slab[3], cls == CLS_SUBSEG ? 1 : 0);
+  }
+  r.counts[i] = c;
+  int e = r.cand[i];
+  if (outcome == OUT_UNSPL) {
+    if (cls == CLS_SUBSEG) {
+      m.Gflag[CKI(e, m.capG)] |= F_UNSPL;
+      m.dirtyG[CKI(e, m.capG)] = 1;
+    } else if (cls == CLS_SUBFACE) {
+      m.Sflag[CKI(e, m.capS)] |= F_UNSPL;
+      m.dirtyS[CKI(e, m.capS)] = 1;
+    } else if (cls == CLS_TET) {
+      m.Tflag[CKI(e, m.capT)] |= F_UNSPL;
+      m.candT[CKI(e, m.capT)] = 0;
+    } else {
+      r.point_state[e] = 2;
+    }
+  }
+  if (outcome == OUT_OK) {
+    if (surv) ++a.surv;
+    else ++a.ok;
+  } else if (outcome == OUT_REJECT) {
+    ++a.rej;
+  } else if (outcome == OUT_BLASTED) {
+    ++a.blast;
+  } else {
+    ++a.unspl;
+  }
+  // per-instance counts for the stall rule and batch statistics (blasted
+  // regions, the bulk of a large round, need none)
+  if (m.instSt && (surv || outcome == OUT_UNSPL || outcome == OUT_REJECT)) {
+    unsigned long long* q = m.instSt + (size_t)inst_of(r, i) * IS_COUNT;
+    atomicAdd(&q[surv ? IS_SURV : (outcome == OUT_UNSPL ? IS_UNSPL : IS_REJECT)], 1ULL);
+  }
+}
+__device__ void flush_sel(const DevRound& r, const SelAcc& a, int lane) {
+  if (lane != 0) return;
+  if (a.surv) atomicAdd(&r.stats[ST_SURV], (unsigned long long)a.surv);
+  if (a.ok) atomicAdd(&r.stats[ST_OK], (unsigned long long)a.ok);
+  if (a.rej) atomicAdd(&r.stats[ST_REJECT], (unsigned long long)a.rej);
+  if (a.blast) atomicAdd(&r.stats[ST_BLAST], (unsigned long long)a.blast);
+  if (a.unspl) atomicAdd(&r.stats[ST_UNSPL], (unsigned long long)a.unspl);
+}
+
 __global__ void k_select(DevMesh m, DevRound r) {
   int lane = threadIdx.x & 31;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int nw = (gridDim.x * blockDim.x) >> 5;
-  // this warp's outcome counts: kept, eligible but lost, refused, blasted,
-  // unsplittable (added to the round totals once, at the end)
-  unsigned c_surv = 0, c_ok = 0, c_rej = 0, c_blast = 0, c_unspl = 0;
-  for (int i = warp; i < r.n; i += nw) {
-    const int outcome = r.status[i] & 0xff;
-    const bool surv = outcome == OUT_OK && holds_marks(m, r, i, lane);
-    if (lane != 0) continue;
-    const int cls = cls_of(r, i);
-    r.survived[i] = surv ? 1 : 0;
-    int4 c = make_int4(0, 0, 0, 0);
-    if (surv) {
-      bool t2;
-      const int* slab = slab_of(r, i, t2);
-      c = make_int4(cls == CLS_POINT ? 0 : 1, slab[1], slab[3], cls == CLS_SUBSEG ? 1 : 0);
-    }
-    r.counts[i] = c;
-    int e = r.cand[i];
-    if (outcome == OUT_UNSPL) {
-      if (cls == CLS_SUBSEG) {
-        m.Gflag[CKI(e, m.capG)] |= F_UNSPL;
-        m.dirtyG[CKI(e, m.capG)] = 1;
-      } else if (cls == CLS_SUBFACE) {
-        m.Sflag[CKI(e, m.capS)] |= F_UNSPL;
-        m.dirtyS[CKI(e, m.capS)] = 1;
-      } else if (cls == CLS_TET) {
-        m.Tflag[CKI(e, m.capT)] |= F_UNSPL;
-        m.candT[CKI(e, m.capT)] = 0;
-      } else {
-        r.point_state[e] = 2;
-      }
-    }
-    if (outcome == OUT_OK) {
-      if (surv) ++c_surv;
-      else ++c_ok;
-    } else if (outcome == OUT_REJECT) {
-      ++c_rej;
-    } else if (outcome == OUT_BLASTED) {
-      ++c_blast;
-    } else {
-      ++c_unspl;
-    }
-    // per-instance counts for the stall rule and batch statistics (blasted
-    // regions, the bulk of a large round, need none)
-    if (m.instSt && (surv || outcome == OUT_UNSPL || outcome == OUT_REJECT)) {
-      unsigned long long* q = m.instSt + (size_t)inst_of(r, i) * IS_COUNT;
-      atomicAdd(&q[surv ? IS_SURV : (outcome == OUT_UNSPL ? IS_UNSPL : IS_REJECT)], 1ULL);
-    }
-  }
-  if (lane == 0) {
-    if (c_surv) atomicAdd(&r.stats[ST_SURV], (unsigned long long)c_surv);
-    if (c_ok) atomicAdd(&r.stats[ST_OK], (unsigned long long)c_ok);
-    if (c_rej) atomicAdd(&r.stats[ST_REJECT], (unsigned long long)c_rej);
-    if (c_blast) atomicAdd(&r.stats[ST_BLAST], (unsigned long long)c_blast);
-    if (c_unspl) atomicAdd(&r.stats[ST_UNSPL], (unsigned long long)c_unspl);
-  }
+  SelAcc a;
+  for (int i = warp; i < r.n; i += nw) select_one(m, r, i, lane, a);
+  flush_sel(r, a, lane);
 }
 
 // ============================================================== insertion
 // One warp per kept point: new tetrahedra p + boundary face, links to the shell
 // and inside the star, new subfaces p + facet boundary edge, retire the region.
+// insert kept candidate i (called by a whole warp)
+__device__ void insert_one(const DevMesh& m, const DevRound& r, int* hint, int i, int lane) {
+  if (!r.survived[i]) return;
+  bool t2;
+  const int* slab = slab_of(r, i, t2);
+#define SLAB_OFF(name) (t2 ? SlabLayout<Tier2>::name : SlabLayout<Tier1>::name)
+  const int ncav = slab[0], nbnd = slab[1], nf = slab[2], nfb = slab[3];
+  const int* cav = slab + SLAB_OFF(OFF_CAV);
+  const int* bin = slab + SLAB_OFF(OFF_BIN);
+  const int* bout = slab + SLAB_OFF(OFF_BOUT);
+  const int* fcav = slab + SLAB_OFF(OFF_FCAV);
+  const int* fbnd = slab + SLAB_OFF(OFF_FBND);
+  const int* bv = slab + SLAB_OFF(OFF_BV);
+  const int* fbv = slab + SLAB_OFF(OFF_FBV);
+  const int* part = slab + SLAB_OFF(OFF_PART);
+#undef SLAB_OFF
+  const int4 off = r.offs[i];
+  const int e = r.cand[i];
+  const int cls = cls_of(r, i);
+  const int inst = inst_of(r, i);
+  const int vp = cls == CLS_POINT ? e : m.nV + off.x;
+  const int t0 = m.nT + off.y;
+  const int s0 = m.nS + off.z;
+  int sa = -1, sb = -1;
+  if (cls == CLS_SUBSEG) {
+    int4 G = m.GV[CKI(e, m.capG)];
+    sa = G.x;
+    sb = G.y;
+  }
+  if (lane == 0 && cls != CLS_POINT) {
+    m.V[CKI(vp, m.capV)] = r.sp[i];
+    if (m.Vinst) m.Vinst[CKI(vp, m.capV)] = inst;
+  }
+  if (lane == 0) {
+    atomicAdd(&r.stats[ST_NEWT], (unsigned long long)nbnd);
+    atomicAdd(&r.stats[ST_DEADT], (unsigned long long)ncav);
+  }
+  // step 1: new tetrahedra (p replaces the vertex opposite each boundary face)
+  for (int j = lane; j < nbnd; j += 32) {
+    int t = bin[j] >> 2, f = bin[j] & 3;
+    TetRec R = ld_tet(m, t);
+    int nid = t0 + j;
+    int4 nv;
+    for (int k = 0; k < 4; ++k) seti(nv, k, k == f ? vp : vid(geti(R.v, k)));
+    if (face_sub(R.v, f)) seti(nv, f, geti(nv, f) | (1 << kSubBit));
+    for (int ed = 0; ed < 6; ++ed) {
+      int a = edge_i(ed), b = edge_j(ed);
+      bool mark;
+      if (a != f && b != f) {
+        mark = edge_bit(R.v, ed);
+      } else {
+        int other = vid(geti(R.v, a == f ? b : a));
+        mark = cls == CLS_SUBSEG && (other == sa || other == sb);
+      }
+      if (mark) seti(nv, ed >> 1, geti(nv, ed >> 1) | (1 << (29 + (ed & 1))));
+    }
+    TetRec N;
+    N.v = nv;
+    N.n = make_int4(-1, -1, -1, -1);
+    CKL(bout[j], m.nT);
+    (void)CKI(t, m.nT);
+    seti(N.n, f, bout[j]);
+    m.T[CKI(nid, m.capT)] = N;
+    int4 ts = make_int4(-1, -1, -1, -1);
+    if (face_sub(R.v, f)) {
+      int s = ts_ptr(m, t)[f];
+      seti(ts, f, s);
+      if (s >= 0 && s < m.nS) {
+        m.SN[CKI(s, m.capS)].w = (nid << 2) | f;
+        m.dirtyS[CKI(s, m.capS)] = 1;  // one of its tetrahedra is new
+      } else {
+        atomicAdd(&r.stats[ST_ITER], 1ULL);
+      }
+    }
+    m.TS[CKI(nid, m.capT)] = ts;
+    m.Tmark[CKI(nid, m.capT)] = ~0ULL;
+    m.Tseed[CKI(nid, m.capT)] = ~0ULL;
+    m.Tfwd[CKI(nid, m.capT)] = -1;
+    if (bout[j] >= 0) tet_n_ptr(m, bout[j] >> 2)[bout[j] & 3] = (nid << 2) | f;
+  }
+  __syncwarp();
+  // step 2: links inside the star, through the boundary faces' shared edges
+  // (each edge's partner entry was recorded by growth's star check)
+  for (int it = lane; it < nbnd * 3; it += 32) {
+    int j = it / 3, q = it % 3;
+    const int* F = bv + 3 * j;
+    int t = bin[j] >> 2, f = bin[j] & 3;
+    // position in tet j of the face vertex q (the apex across the new face)
+    TetRec R = ld_tet(m, t);
+    int g = -1;
+    for (int k = 0; k < 4; ++k)
+      if (k != f && vid(geti(R.v, k)) == F[q]) g = k;
+    int link = -1;
+    const int pe = part[it];
+    if (pe >= 0) {
+      const int k2 = pe / 3;
+      const int apexv = bv[pe];  // vertex of face k2 off the shared edge
+      int t2_ = bin[k2] >> 2, f2 = bin[k2] & 3;
+      TetRec R2 = ld_tet(m, t2_);
+      int h = -1;
+      for (int k = 0; k < 4; ++k)
+        if (k != f2 && vid(geti(R2.v, k)) == apexv) h = k;
+      link = h >= 0 ? (((t0 + k2) << 2) | h) : -1;
+    }
+    CKL(link, m.nT + 0x7fffffff / 8);
+    if (link >= 0 && (link >> 2) < t0) CKL(link, 0);  // must point into this star
+    if (g >= 0) tet_n_ptr(m, t0 + j)[g] = link;
+    else atomicAdd(&r.stats[ST_ITER], 1ULL);
+  }
+  __syncwarp();
+  // step 3: new subfaces (p joined to each facet boundary edge)
+  for (int k = lane; k < nfb; k += 32) {
+    int s = fbnd[k] >> 2, ke = fbnd[k] & 3;
+    int u = fbv[3 * k], x = fbv[3 * k + 1], fid = fbv[3 * k + 2];
+    int ns = s0 + k;
+    m.SV[CKI(ns, m.capS)] = make_int4(vp, u, x, fid);
+    int outer = geti(m.SN[CKI(s, m.capS)], ke);
+    int4 sn = make_int4(outer, -1, -1, -1);
+    if (outer >= 0) {
+      int* o = sn_ptr(m, outer);
+      for (int q = 0; q < 3; ++q)
+        if (o[q] == s) o[q] = ns;
+    }
+    // across (x, p) and (p, u): the other new subface of this facet there
+    for (int k2 = 0; k2 < nfb; ++k2) {
+      if (k2 == k || fbv[3 * k2 + 2] != fid) continue;
+      int u2 = fbv[3 * k2], x2 = fbv[3 * k2 + 1];
+      if (u2 == x || x2 == x) sn.y = s0 + k2;
+      if (u2 == u || x2 == u) sn.z = s0 + k2;
+    }
+    if (sa >= 0 && (x == sa || x == sb)) sn.y = -1;  // a new subsegment bounds it
+    if (sa >= 0 && (u == sa || u == sb)) sn.z = -1;
+    // the new tetrahedra on either side of the new subface
+    int tw = -1;
+    for (int j = 0; j < nbnd; ++j) {
+      const int* F = bv + 3 * j;
+      bool hu = F[0] == u || F[1] == u || F[2] == u;
+      bool hx = F[0] == x || F[1] == x || F[2] == x;
+      if (!(hu && hx)) continue;
+      int apexv = (F[0] != u && F[0] != x) ? F[0] : ((F[1] != u && F[1] != x) ? F[1] : F[2]);
+      int t = bin[j] >> 2, f = bin[j] & 3;
+      TetRec R = ld_tet(m, t);
+      int g = -1;
+      for (int q = 0; q < 4; ++q)
+        if (q != f && vid(geti(R.v, q)) == apexv) g = q;
+      int nid = t0 + j;
+      if (g < 0) {
+        atomicAdd(&r.stats[ST_ITER], 1ULL);
+        continue;
+      }
+      ts_ptr(m, nid)[g] = ns;
+      atomicOr(&tet_v_ptr(m, nid)[g], 1 << kSubBit);
+      if (tw < 0) tw = (nid << 2) | g;
+    }
+    sn.w = tw;
+    m.SN[CKI(ns, m.capS)] = sn;
+    m.Sflag[CKI(ns, m.capS)] = 0;
+    m.Smust[CKI(ns, m.capS)] = 0;
+    m.dirtyS[CKI(ns, m.capS)] = 1;
+    m.Smark[CKI(ns, m.capS)] = ~0ULL;
+  }
+  __syncwarp();
+  // step 4: retire the cavity and the facet part
+  for (int k = lane; k < ncav; k += 32) {
+    int t = cav[k];
+    m.Tflag[CKI(t, m.capT)] |= F_DEAD;
+    m.Tfwd[CKI(t, m.capT)] = t0;
+    if (m.candT) m.candT[CKI(t, m.capT)] = 0;
+  }
+  for (int k = lane; k < nf; k += 32) {
+    m.Sflag[CKI(fcav[k], m.capS)] |= F_DEAD;
+    if (m.candS) m.candS[CKI(fcav[k], m.capS)] = 0;
+  }
+  // step 5: the split subsegment becomes (a, p) and (p, b)
+  if (cls == CLS_SUBSEG) {
+    int ta = -1, tb = -1;
+    for (int j = lane; j < nbnd; j += 32) {
+      const int* F = bv + 3 * j;
+      if (F[0] == sa || F[1] == sa || F[2] == sa) ta = t0 + j;
+      if (F[0] == sb || F[1] == sb || F[2] == sb) tb = t0 + j;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ta = max(ta, __shfl_xor_sync(FULLMASK, ta, o));
+      tb = max(tb, __shfl_xor_sync(FULLMASK, tb, o));
+    }
+    if (lane == 0) {
+      int4 G = m.GV[CKI(e, m.capG)];
+      int g2 = m.nG + off.w;
+      m.GV[CKI(e, m.capG)] = make_int4(G.x, vp, G.z, ta);
+      m.GV[CKI(g2, m.capG)] = make_int4(vp, G.y, G.z, tb);
+      m.Gflag[CKI(e, m.capG)] = 0;
+      m.Gmust[CKI(e, m.capG)] = 0;
+      m.Gflag[CKI(g2, m.capG)] = 0;
+      m.Gmust[CKI(g2, m.capG)] = 0;
+      m.dirtyG[CKI(e, m.capG)] = 1;
+      m.dirtyG[CKI(g2, m.capG)] = 1;
+      hash_insert(m, ekey(G.x, vp), e);
+      hash_insert(m, ekey(vp, G.y), g2);
+    }
+  }
+  __syncwarp();
+  // step 6: subsegment tet references and quality of the new tetrahedra
+  for (int j = lane; j < nbnd; j += 32) {
+    int nid = t0 + j;
+    int4 v = m.T[CKI(nid, m.capT)].v;
+    for (int ed = 0; ed < 6; ++ed) {
+      if (!edge_bit(v, ed)) continue;
+      int a = vid(geti(v, edge_i(ed))), b = vid(geti(v, edge_j(ed)));
+      if (a == vp || b == vp) continue;
+      int g = hash_lookup(m, ekey(a, b));
+      if (g >= 0) {
+        m.GV[CKI(g, m.capG)].w = nid;
+        if (m.dirtyG) m.dirtyG[CKI(g, m.capG)] = 1;  // its edge ring changed
+      }
+    }
+    int s4[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
+    sort4(s4);
+    bool bad = tet_bad_fixed(vtx(m, s4[0]), vtx(m, s4[1]), vtx(m, s4[2]), vtx(m, s4[3]),
+                             bound_of(m, r.B, inst));
+    m.Tflag[CKI(nid, m.capT)] = bad ? F_BAD : 0;
+    if (m.candT) m.candT[CKI(nid, m.capT)] = bad ? 1 : 0;
+  }
+  if (lane == 0 && cls == CLS_POINT) {
+    r.point_state[e] = 1;
+    hint[e] = t0;
+  }
+}
+
 __global__ void k_insert(DevMesh m, DevRound r, int* hint) {
   int lane = threadIdx.x & 31;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int nw = (gridDim.x * blockDim.x) >> 5;
   for (int i = warp; i < r.n; i += nw) {
-    if (!r.survived[i]) continue;
-    bool t2;
-    const int* slab = slab_of(r, i, t2);
-#define SLAB_OFF(name) (t2 ? SlabLayout<Tier2>::name : SlabLayout<Tier1>::name)
-    const int ncav = slab[0], nbnd = slab[1], nf = slab[2], nfb = slab[3];
-    const int* cav = slab + SLAB_OFF(OFF_CAV);
-    const int* bin = slab + SLAB_OFF(OFF_BIN);
-    const int* bout = slab + SLAB_OFF(OFF_BOUT);
-    const int* fcav = slab + SLAB_OFF(OFF_FCAV);
-    const int* fbnd = slab + SLAB_OFF(OFF_FBND);
-    const int* bv = slab + SLAB_OFF(OFF_BV);
-    const int* fbv = slab + SLAB_OFF(OFF_FBV);
-    const int* part = slab + SLAB_OFF(OFF_PART);
-#undef SLAB_OFF
-    const int4 off = r.offs[i];
-    const int e = r.cand[i];
-    const int cls = cls_of(r, i);
-    const int inst = inst_of(r, i);
-    const int vp = cls == CLS_POINT ? e : m.nV + off.x;
-    const int t0 = m.nT + off.y;
-    const int s0 = m.nS + off.z;
-    int sa = -1, sb = -1;
-    if (cls == CLS_SUBSEG) {
-      int4 G = m.GV[CKI(e, m.capG)];
-      sa = G.x;
-      sb = G.y;
-    }
-    if (lane == 0 && cls != CLS_POINT) {
-      m.V[CKI(vp, m.capV)] = r.sp[i];
-      if (m.Vinst) m.Vinst[CKI(vp, m.capV)] = inst;
-    }
-    if (lane == 0) {
-      atomicAdd(&r.stats[ST_NEWT], (unsigned long long)nbnd);
-      atomicAdd(&r.stats[ST_DEADT], (unsigned long long)ncav);
-    }
-    // step 1: new tetrahedra (p replaces the vertex opposite each boundary face)
-    for (int j = lane; j < nbnd; j += 32) {
-      int t = bin[j] >> 2, f = bin[j] & 3;
-      TetRec R = ld_tet(m, t);
-      int nid = t0 + j;
-      int4 nv;
-      for (int k = 0; k < 4; ++k) seti(nv, k, k == f ? vp : vid(geti(R.v, k)));
-      if (face_sub(R.v, f)) seti(nv, f, geti(nv, f) | (1 << kSubBit));
-      for (int ed = 0; ed < 6; ++ed) {
-        int a = edge_i(ed), b = edge_j(ed);
-        bool mark;
-        if (a != f && b != f) {
-          mark = edge_bit(R.v, ed);
-        } else {
-          int other = vid(geti(R.v, a == f ? b : a));
-          mark = cls == CLS_SUBSEG && (other == sa || other == sb);
-        }
-        if (mark) seti(nv, ed >> 1, geti(nv, ed >> 1) | (1 << (29 + (ed & 1))));
-      }
-      TetRec N;
-      N.v = nv;
-      N.n = make_int4(-1, -1, -1, -1);
-      CKL(bout[j], m.nT);
-      (void)CKI(t, m.nT);
-      seti(N.n, f, bout[j]);
-      m.T[CKI(nid, m.capT)] = N;
-      int4 ts = make_int4(-1, -1, -1, -1);
-      if (face_sub(R.v, f)) {
-        int s = ts_ptr(m, t)[f];
-        seti(ts, f, s);
-        if (s >= 0 && s < m.nS) {
-          m.SN[CKI(s, m.capS)].w = (nid << 2) | f;
-          m.dirtyS[CKI(s, m.capS)] = 1;  // one of its tetrahedra is new
-        } else {
-          atomicAdd(&r.stats[ST_ITER], 1ULL);
-        }
-      }
-      m.TS[CKI(nid, m.capT)] = ts;
-      m.Tmark[CKI(nid, m.capT)] = ~0ULL;
-      m.Tseed[CKI(nid, m.capT)] = ~0ULL;
-      m.Tfwd[CKI(nid, m.capT)] = -1;
-      if (bout[j] >= 0) tet_n_ptr(m, bout[j] >> 2)[bout[j] & 3] = (nid << 2) | f;
-    }
-    __syncwarp();
-    // step 2: links inside the star, through the boundary faces' shared edges
-    // (each edge's partner entry was recorded by growth's star check)
-    for (int it = lane; it < nbnd * 3; it += 32) {
-      int j = it / 3, q = it % 3;
-      const int* F = bv + 3 * j;
-      int t = bin[j] >> 2, f = bin[j] & 3;
-      // position in tet j of the face vertex q (the apex across the new face)
-      TetRec R = ld_tet(m, t);
-      int g = -1;
-      for (int k = 0; k < 4; ++k)
-        if (k != f && vid(geti(R.v, k)) == F[q]) g = k;
-      int link = -1;
-      const int pe = part[it];
-      if (pe >= 0) {
-        const int k2 = pe / 3;
-        const int apexv = bv[pe];  // vertex of face k2 off the shared edge
-        int t2_ = bin[k2] >> 2, f2 = bin[k2] & 3;
-        TetRec R2 = ld_tet(m, t2_);
-        int h = -1;
-        for (int k = 0; k < 4; ++k)
-          if (k != f2 && vid(geti(R2.v, k)) == apexv) h = k;
-        link = h >= 0 ? (((t0 + k2) << 2) | h) : -1;
-      }
-      CKL(link, m.nT + 0x7fffffff / 8);
-      if (link >= 0 && (link >> 2) < t0) CKL(link, 0);  // must point into this star
-      if (g >= 0) tet_n_ptr(m, t0 + j)[g] = link;
-      else atomicAdd(&r.stats[ST_ITER], 1ULL);
-    }
-    __syncwarp();
-    // step 3: new subfaces (p joined to each facet boundary edge)
-    for (int k = lane; k < nfb; k += 32) {
-      int s = fbnd[k] >> 2, ke = fbnd[k] & 3;
-      int u = fbv[3 * k], x = fbv[3 * k + 1], fid = fbv[3 * k + 2];
-      int ns = s0 + k;
-      m.SV[CKI(ns, m.capS)] = make_int4(vp, u, x, fid);
-      int outer = geti(m.SN[CKI(s, m.capS)], ke);
-      int4 sn = make_int4(outer, -1, -1, -1);
-      if (outer >= 0) {
-        int* o = sn_ptr(m, outer);
-        for (int q = 0; q < 3; ++q)
-          if (o[q] == s) o[q] = ns;
-      }
-      // across (x, p) and (p, u): the other new subface of this facet there
-      for (int k2 = 0; k2 < nfb; ++k2) {
-        if (k2 == k || fbv[3 * k2 + 2] != fid) continue;
-        int u2 = fbv[3 * k2], x2 = fbv[3 * k2 + 1];
-        if (u2 == x || x2 == x) sn.y = s0 + k2;
-        if (u2 == u || x2 == u) sn.z = s0 + k2;
-      }
-      if (sa >= 0 && (x == sa || x == sb)) sn.y = -1;  // a new subsegment bounds it
-      if (sa >= 0 && (u == sa || u == sb)) sn.z = -1;
-      // the new tetrahedra on either side of the new subface
-      int tw = -1;
-      for (int j = 0; j < nbnd; ++j) {
-        const int* F = bv + 3 * j;
-        bool hu = F[0] == u || F[1] == u || F[2] == u;
-        bool hx = F[0] == x || F[1] == x || F[2] == x;
-        if (!(hu && hx)) continue;
-        int apexv = (F[0] != u && F[0] != x) ? F[0] : ((F[1] != u && F[1] != x) ? F[1] : F[2]);
-        int t = bin[j] >> 2, f = bin[j] & 3;
-        TetRec R = ld_tet(m, t);
-        int g = -1;
-        for (int q = 0; q < 4; ++q)
-          if (q != f && vid(geti(R.v, q)) == apexv) g = q;
-        int nid = t0 + j;
-        if (g < 0) {
-          atomicAdd(&r.stats[ST_ITER], 1ULL);
-          continue;
-        }
-        ts_ptr(m, nid)[g] = ns;
-        atomicOr(&tet_v_ptr(m, nid)[g], 1 << kSubBit);
-        if (tw < 0) tw = (nid << 2) | g;
-      }
-      sn.w = tw;
-      m.SN[CKI(ns, m.capS)] = sn;
-      m.Sflag[CKI(ns, m.capS)] = 0;
-      m.Smust[CKI(ns, m.capS)] = 0;
-      m.dirtyS[CKI(ns, m.capS)] = 1;
-      m.Smark[CKI(ns, m.capS)] = ~0ULL;
-    }
-    __syncwarp();
-    // step 4: retire the cavity and the facet part
-    for (int k = lane; k < ncav; k += 32) {
-      int t = cav[k];
-      m.Tflag[CKI(t, m.capT)] |= F_DEAD;
-      m.Tfwd[CKI(t, m.capT)] = t0;
-      if (m.candT) m.candT[CKI(t, m.capT)] = 0;
-    }
-    for (int k = lane; k < nf; k += 32) {
-      m.Sflag[CKI(fcav[k], m.capS)] |= F_DEAD;
-      if (m.candS) m.candS[CKI(fcav[k], m.capS)] = 0;
-    }
-    // step 5: the split subsegment becomes (a, p) and (p, b)
-    if (cls == CLS_SUBSEG) {
-      int ta = -1, tb = -1;
-      for (int j = lane; j < nbnd; j += 32) {
-        const int* F = bv + 3 * j;
-        if (F[0] == sa || F[1] == sa || F[2] == sa) ta = t0 + j;
-        if (F[0] == sb || F[1] == sb || F[2] == sb) tb = t0 + j;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        ta = max(ta, __shfl_xor_sync(FULLMASK, ta, o));
-        tb = max(tb, __shfl_xor_sync(FULLMASK, tb, o));
-      }
-      if (lane == 0) {
-        int4 G = m.GV[CKI(e, m.capG)];
-        int g2 = m.nG + off.w;
-        m.GV[CKI(e, m.capG)] = make_int4(G.x, vp, G.z, ta);
-        m.GV[CKI(g2, m.capG)] = make_int4(vp, G.y, G.z, tb);
-        m.Gflag[CKI(e, m.capG)] = 0;
-        m.Gmust[CKI(e, m.capG)] = 0;
-        m.Gflag[CKI(g2, m.capG)] = 0;
-        m.Gmust[CKI(g2, m.capG)] = 0;
-        m.dirtyG[CKI(e, m.capG)] = 1;
-        m.dirtyG[CKI(g2, m.capG)] = 1;
-        hash_insert(m, ekey(G.x, vp), e);
-        hash_insert(m, ekey(vp, G.y), g2);
-      }
-    }
-    __syncwarp();
-    // step 6: subsegment tet references and quality of the new tetrahedra
-    for (int j = lane; j < nbnd; j += 32) {
-      int nid = t0 + j;
-      int4 v = m.T[CKI(nid, m.capT)].v;
-      for (int ed = 0; ed < 6; ++ed) {
-        if (!edge_bit(v, ed)) continue;
-        int a = vid(geti(v, edge_i(ed))), b = vid(geti(v, edge_j(ed)));
-        if (a == vp || b == vp) continue;
-        int g = hash_lookup(m, ekey(a, b));
-        if (g >= 0) {
-          m.GV[CKI(g, m.capG)].w = nid;
-          if (m.dirtyG) m.dirtyG[CKI(g, m.capG)] = 1;  // its edge ring changed
-        }
-      }
-      int s4[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
-      sort4(s4);
-      bool bad = tet_bad_fixed(vtx(m, s4[0]), vtx(m, s4[1]), vtx(m, s4[2]), vtx(m, s4[3]),
-                               bound_of(m, r.B, inst));
-      m.Tflag[CKI(nid, m.capT)] = bad ? F_BAD : 0;
-      if (m.candT) m.candT[CKI(nid, m.capT)] = bad ? 1 : 0;
-    }
-    if (lane == 0 && cls == CLS_POINT) {
-      r.point_state[e] = 1;
-      hint[e] = t0;
-    }
+    insert_one(m, r, hint, i, lane);
   }
 }
 
@@ -2467,22 +2492,28 @@ void launch_eval_pred(int kind, const double* in, int n, int* sign, double* outp
 // A subsegment round that inserted nothing, gave up nothing and flagged no new
 // candidate would repeat itself: its refused candidates become unsplittable.
 // Decided per instance from its round counters (run after selection).
-__global__ void k_stall(DevMesh m, DevRound r) {
-  unsigned moved = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
-    if (cls_of(r, i) != CLS_SUBSEG || (r.status[i] & 0xff) != OUT_REJECT) continue;
-    const unsigned long long* q = m.instSt + (size_t)inst_of(r, i) * IS_COUNT;
-    if (q[IS_SURV] || q[IS_UNSPL] || q[IS_NEWCAND]) continue;
-    r.status[i] = OUT_UNSPL | (RS_STRUCT << 8);
-    m.Gflag[CKI(r.cand[i], m.capG)] |= F_UNSPL;
-    m.dirtyG[CKI(r.cand[i], m.capG)] = 1;
-    atomicAdd(&m.instSt[(size_t)inst_of(r, i) * IS_COUNT + IS_STALLED], 1ULL);
-    ++moved;
-  }
+// stall rule for candidate i; returns 1 if it was given up
+__device__ int stall_one(const DevMesh& m, const DevRound& r, int i) {
+  if (cls_of(r, i) != CLS_SUBSEG || (r.status[i] & 0xff) != OUT_REJECT) return 0;
+  const unsigned long long* q = m.instSt + (size_t)inst_of(r, i) * IS_COUNT;
+  if (q[IS_SURV] || q[IS_UNSPL] || q[IS_NEWCAND]) return 0;
+  r.status[i] = OUT_UNSPL | (RS_STRUCT << 8);
+  m.Gflag[CKI(r.cand[i], m.capG)] |= F_UNSPL;
+  m.dirtyG[CKI(r.cand[i], m.capG)] = 1;
+  atomicAdd(&m.instSt[(size_t)inst_of(r, i) * IS_COUNT + IS_STALLED], 1ULL);
+  return 1;
+}
+__device__ void flush_stall(const DevRound& r, unsigned moved) {
   if (moved) {
     atomicAdd(&r.stats[ST_UNSPL], (unsigned long long)moved);
     atomicAdd(&r.stats[ST_REJECT], (unsigned long long)(-(long long)moved));
   }
+}
+__global__ void k_stall(DevMesh m, DevRound r) {
+  unsigned moved = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x)
+    moved += stall_one(m, r, i);
+  flush_stall(r, moved);
 }
 void launch_count_inst(const DevMesh& m, const uint8_t* candG, const uint8_t* candS,
                        const uint8_t* candT, cudaStream_t s) {
@@ -2500,6 +2531,124 @@ void launch_decode_cands(const DevMesh& m, int* cand, uint8_t* ccls, int* cinst,
 }
 void launch_stall(const DevMesh& m, const DevRound& r, cudaStream_t s) {
   if (r.n > 0) k_stall<<<grid_for(r.n, 256), 256, 0, s>>>(m, r);
+}
+
+// ============================================================ small rounds
+// A round with at most kFusedMax candidates runs in one thread-block cluster
+// (kFusedBlocks blocks on as many SMs, one warp per candidate): split, locate
+// (with the start claims), growth in tier 1 (shared-memory workspaces) and,
+// for regions that do not fit, tier 2 (global workspaces; candidate i uses
+// tier-2 slab i), selection, the stall rule, the allocation scan and
+// insertion, with cluster barriers instead of separate launches and host
+// synchronisations between the steps. The host reserves capacity for the
+// largest possible growth (tier-2 caps) before the launch and reads the totals
+// afterwards.
+// every block's global writes are visible to the whole cluster after this
+__device__ __forceinline__ void cluster_barrier() {
+  __threadfence();
+  cooperative_groups::this_cluster().sync();
+}
+
+__global__ void __launch_bounds__(32 * kFusedWarps, 1) k_round_fused(DevMesh m, DevRound r, int* hint,
+                                                                      int4* offs, FusedOut* out,
+                                                                      int do_stall) {
+  extern __shared__ int smraw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
+  const int warp = blockIdx.x * kFusedWarps + wib, nwarps = gridDim.x * kFusedWarps;
+  for (int i = tid; i < r.n; i += nthreads) {
+    split_one(m, r, i);
+    locate_one(m, r, hint, i);
+  }
+  cluster_barrier();
+  GrowAcc acc;
+  {
+    Smem1* sm = reinterpret_cast<Smem1*>(smraw) + wib;
+    Ws w{sm->cav, sm->hset, sm->bin, sm->bout, sm->bv, sm->fcav, sm->fbnd, sm->fbv};
+    for (int i = warp; i < r.n; i += nwarps) {
+      int* slab = r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
+      grow_one<Tier1>(m, r, i, w, slab, lane, acc);
+      __syncwarp();
+    }
+  }
+  cluster_barrier();
+  for (int i = warp; i < r.n; i += nwarps) {
+    if (r.status[i] != OUT_RETRY) continue;  // the same value in every lane
+    using L = SlabLayout<Tier2>;
+    int* slab = r.slab2 + (size_t)i * L::STRIDE;
+    if (lane == 0) r.slab2_of[i] = i;
+    __syncwarp();
+    Ws w2{slab + L::OFF_CAV, r.ws2 + (size_t)warp * Tier2::HCAP, slab + L::OFF_BIN,
+          slab + L::OFF_BOUT, slab + L::OFF_BV, slab + L::OFF_FCAV, slab + L::OFF_FBND,
+          slab + L::OFF_FBV};
+    grow_one<Tier2>(m, r, i, w2, slab, lane, acc);
+    __syncwarp();
+    if (lane == 0) {
+      if (r.status[i] == OUT_RETRY) set_status(r, i, OUT_UNSPL, RS_OVERFLOW);
+      atomicAdd(&out->n2, 1);
+    }
+  }
+  flush_acc(r, acc, lane);
+  cluster_barrier();
+  SelAcc sa;
+  for (int i = warp; i < r.n; i += nwarps) select_one(m, r, i, lane, sa);
+  flush_sel(r, sa, lane);
+  cluster_barrier();
+  if (do_stall) {
+    unsigned moved = 0;
+    for (int i = tid; i < r.n; i += nthreads) moved += stall_one(m, r, i);
+    flush_stall(r, moved);
+    cluster_barrier();
+  }
+  if (warp == 0) {  // exclusive scan of the new-element counts
+    int4 run = make_int4(0, 0, 0, 0);
+    for (int base = 0; base < r.n; base += 32) {
+      const int i = base + lane;
+      const int4 c = i < r.n ? r.counts[i] : make_int4(0, 0, 0, 0);
+      int4 inc = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        int4 t;
+        t.x = __shfl_up_sync(FULLMASK, inc.x, o);
+        t.y = __shfl_up_sync(FULLMASK, inc.y, o);
+        t.z = __shfl_up_sync(FULLMASK, inc.z, o);
+        t.w = __shfl_up_sync(FULLMASK, inc.w, o);
+        if (lane >= o) inc = make_int4(inc.x + t.x, inc.y + t.y, inc.z + t.z, inc.w + t.w);
+      }
+      if (i < r.n)
+        offs[i] = make_int4(run.x + inc.x - c.x, run.y + inc.y - c.y, run.z + inc.z - c.z,
+                            run.w + inc.w - c.w);
+      run.x += __shfl_sync(FULLMASK, inc.x, 31);
+      run.y += __shfl_sync(FULLMASK, inc.y, 31);
+      run.z += __shfl_sync(FULLMASK, inc.z, 31);
+      run.w += __shfl_sync(FULLMASK, inc.w, 31);
+    }
+    if (lane == 0) out->tot = run;
+  }
+  cluster_barrier();
+  for (int i = warp; i < r.n; i += nwarps) insert_one(m, r, hint, i, lane);
+}
+void launch_round_fused(const DevMesh& m, const DevRound& r, int* hint, int4* offs, FusedOut* out,
+                        bool do_stall, cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = sizeof(Smem1) * kFusedWarps;
+  if (!attr) {
+    cudaFuncSetAttribute(k_round_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  if (r.n <= 0) return;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kFusedBlocks, 1, 1);
+  cfg.blockDim = dim3(32 * kFusedWarps, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kFusedBlocks;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_round_fused, m, r, hint, offs, out, do_stall ? 1 : 0);
 }
 
 // checked build: first out-of-bounds index seen (site line, index, bound), or 0

@@ -50,6 +50,17 @@ void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_insert(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s);
 void launch_stall(const DevMesh& m, const DevRound& r, cudaStream_t s);
 
+// rounds with few candidates: the whole round in one block
+constexpr int kFusedBlocks = 4;  // one cluster
+constexpr int kFusedWarps = 16;  // per block
+constexpr int kFusedMax = kFusedBlocks * kFusedWarps;  // one warp per candidate
+struct FusedOut {
+  int4 tot;  // new vertices, tetrahedra, subfaces, subsegments
+  int n2;    // regions grown in tier 2
+};
+void launch_round_fused(const DevMesh& m, const DevRound& r, int* hint, int4* offs, FusedOut* out,
+                        bool do_stall, cudaStream_t s);
+
 // maintenance
 void launch_compact_flags(const DevMesh& m, int* alive, cudaStream_t s);
 void launch_compact_move(const DevMesh& m, const int* newid, TetRec* T2, int4* TS2,
