@@ -51,7 +51,7 @@ void launch_insert(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t 
 void launch_stall(const DevMesh& m, const DevRound& r, cudaStream_t s);
 
 // rounds with few candidates: the whole round in one block
-constexpr int kFusedBlocks = 4;  // one cluster
+constexpr int kFusedBlocks = 8;  // one cluster (the portable maximum)
 constexpr int kFusedWarps = 16;  // per block
 constexpr int kFusedMax = kFusedBlocks * kFusedWarps;  // one warp per candidate
 struct FusedOut {
