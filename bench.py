@@ -153,16 +153,19 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernels (else None)."""
+def ncu_traffic(kernel, alg_bytes_per_launch):
+    """DRAM bytes per average launch, from the committed ncu record of one launch
+    taken on the current kernels (else None): the captured launch's DRAM bytes,
+    scaled by the ratio of algorithmic bytes (traffic taken to grow in proportion
+    to the work)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         e = d.get(kernel)
         if e and e.get("kernels_sha") == kernel_hash():
-            return float(e["dram_bytes_per_launch_full"])
+            dram = float(e["dram_bytes_read"]) + float(e["dram_bytes_write"])
+            return dram * alg_bytes_per_launch / float(e["algorithmic_bytes"])
     except Exception:
         pass
     return None
@@ -282,8 +285,7 @@ def gpu_arm(args, rank, world):
     gb = grow_bytes(prof["counters"]) / 1e9
     grow_ms = ms["grow1"]
     achieved = gb / (grow_ms / 1e3) if grow_ms > 0 else 0.0
-    traffic = ncu_traffic("k_grow1")
-    per_launch_traffic = traffic if traffic is not None else None
+    per_launch_traffic = ncu_traffic("k_grow1", gb * 1e9 / max(calls["grow1"], 1))
     launches = prof["counters"].get("launches", None)
     value = ins_sum / (total_ms_max / 1e3)
     line = {
