@@ -547,7 +547,7 @@ int maybe_compact(cdr_handle* h, bool force) {
 // A refinement round with few candidates as one kernel (k_round_fused): the
 // capacity for the largest growth the kernel could produce is reserved first,
 // the totals are read back once at the end.
-int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
+int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsorted) {
   DevMesh& m = h->m;
   cudaStream_t s = h->stream;
   using T2 = Tier2;
@@ -578,7 +578,8 @@ int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   bool used[PG_N] = {};
   pmark(h, PG_FUSED, 0);
   launch_round_fused(m, r, ptr<int>(h->bHint), ptr<int4>(h->bOffs), ptr<FusedOut>(h->bFused),
-                     stall, s);
+                     stall, unsorted ? ptr<int>(h->bCand) : nullptr, ptr<int>(h->bCand2),
+                     ptr<uint8_t>(h->bCcls), ptr<int>(h->bCinst), s);
   pmark(h, PG_FUSED, 1);
   used[PG_FUSED] = true;
   h->prof_ctr[15] += 1;
@@ -638,12 +639,17 @@ int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
   return cuda_status(h);
 }
 
+// whether a refinement round of n candidates runs as one kernel
+inline bool use_fused(const cdr_handle* h, int n) { return h->fused && n <= kFusedMax; }
+
 // the shared body of a round once the ordered candidate list is in bCand2
-int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro) {
+// (unsorted: the candidates are still unordered in bCand; fused rounds only)
+int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsorted = false) {
   DevMesh& m = h->m;
   cudaStream_t s = h->stream;
   if (!ensure_pinned(h)) return CDR_ERR_OOM;
-  if (cls != CLS_POINT && n <= kFusedMax && h->fused) return round_fused(h, cls, n, B, ro);
+  if (cls != CLS_POINT && use_fused(h, n)) return round_fused(h, cls, n, B, ro, unsorted);
+  if (unsorted) return set_err(h, CDR_ERR_INTERNAL);
   DevRound r = make_round(h, cls, n, B);
   cudaMemsetAsync(h->bStats.p, 0, ST_COUNT * 8, s);
   if (cls != CLS_POINT) cudaMemsetAsync(h->bInstSt.p, 0, (size_t)h->ninst * IS_COUNT * 8, s);
@@ -898,6 +904,11 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
     tb = h->bTmp.bytes;
     cub::DeviceSelect::Flagged(h->bTmp.p, tb, thrust::counting_iterator<int>(0), flags,
                                ptr<int>(h->bCand), nsel, nall, s);
+    if (use_fused(h, (int)n)) {  // the kernel orders them itself
+      st = round_core(h, cls, (int)n, B, ro, true);
+      if (ro) ro->cls = cls;
+      return st;
+    }
     st = order_candidates(h, cls, (int)n);
     if (st) return st;
     st = round_core(h, cls, (int)n, B, ro);
@@ -919,12 +930,16 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
   cub::DeviceSelect::Flagged(h->bTmp.p, tb, thrust::counting_iterator<int>(0), flags,
                              ptr<int>(h->bCand), nsel, (int)nall, s);
   h->prof_ctr[15] += 1;
-  st = order_candidates(h, -1, (int)n);
-  if (st) return st;
-  launch_decode_cands(m, ptr<int>(h->bCand2), ptr<uint8_t>(h->bCcls), ptr<int>(h->bCinst), (int)n,
-                      s);
-  h->prof_ctr[15] += 1;
-  st = round_core(h, -1, (int)n, B, ro);
+  if (use_fused(h, (int)n)) {  // the kernel orders and decodes them itself
+    st = round_core(h, -1, (int)n, B, ro, true);
+  } else {
+    st = order_candidates(h, -1, (int)n);
+    if (st) return st;
+    launch_decode_cands(m, ptr<int>(h->bCand2), ptr<uint8_t>(h->bCcls), ptr<int>(h->bCinst),
+                        (int)n, s);
+    h->prof_ctr[15] += 1;
+    st = round_core(h, -1, (int)n, B, ro);
+  }
   if (ro) ro->cls = ni == 1 ? std::min(h->instCls[0], 3) : 3;  // 3: several classes or instances
   return st;
 }

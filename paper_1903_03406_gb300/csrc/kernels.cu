@@ -521,26 +521,31 @@ __device__ __forceinline__ int decode_cand(const DevMesh& m, int idx, int& cls) 
   return idx - m.nG - m.nS;
 }
 
+// Priority key of element e of class c: class first (subsegments, subfaces,
+// tetrahedra), then the top 62 bits of the hash of its vertex coordinates
+__device__ unsigned long long prio_key(const DevMesh& m, int c, int e) {
+  int ids[4];
+  int k = elem_key(m, c, e, ids);
+  uint64_t h;
+  if (c == CLS_POINT) {
+    h = prio_hash(c, ids, k);
+  } else {
+    h = 0x9E3779B97F4A7C15ULL * (uint64_t)(c + 1);
+    for (int q = 0; q < k; ++q) {
+      V4 v = m.V[CKI(ids[q], m.capV)];
+      h = prio_hash_step(prio_hash_step(prio_hash_step(h, v.x), v.y), v.z);
+    }
+  }
+  return ((uint64_t)c << 62) | (h >> 2);
+}
+
 // Priorities. cls >= 0: elems are element ids of that class; cls < 0: they are
 // concatenated indices.
 __global__ void k_prio(DevMesh m, int cls, const int* elems, int n, unsigned long long* keys) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int c = cls;
     int e = cls >= 0 ? elems[i] : decode_cand(m, elems[i], c);
-    int ids[4];
-    int k = elem_key(m, c, e, ids);
-    uint64_t h;
-    if (c == CLS_POINT) {
-      h = prio_hash(c, ids, k);
-    } else {
-      h = 0x9E3779B97F4A7C15ULL * (uint64_t)(c + 1);
-      for (int q = 0; q < k; ++q) {
-        V4 v = m.V[CKI(ids[q], m.capV)];
-        h = prio_hash_step(prio_hash_step(prio_hash_step(h, v.x), v.y), v.z);
-      }
-    }
-    // class first (subsegments, subfaces, tetrahedra), then the hash's top 62 bits
-    keys[i] = ((uint64_t)c << 62) | (h >> 2);
+    keys[i] = prio_key(m, c, e);
   }
 }
 
@@ -2549,13 +2554,95 @@ __device__ __forceinline__ void cluster_barrier() {
   cooperative_groups::this_cluster().sync();
 }
 
+// true if candidate a (key ka, class ca, element ea) comes before b: key, then
+// class, then the sorted vertex ids (the order of the sort + tie fix path)
+__device__ bool cand_before(const DevMesh& m, unsigned long long ka, int ca, int ea,
+                            unsigned long long kb, int cb, int eb) {
+  if (ka != kb) return ka < kb;
+  if (ca != cb) return ca < cb;
+  int x[4], y[4];
+  int nk = elem_key(m, ca, ea, x);
+  elem_key(m, cb, eb, y);
+  for (int q = 0; q < nk; ++q)
+    if (x[q] != y[q]) return x[q] < y[q];
+  return ea < eb;
+}
+
+// Block-level ordering of a fused round's candidates (block 0): src holds the
+// round's elements (cls >= 0) or concatenated indices (cls < 0); the sorted
+// element ids go to cand, with their classes and instances for cls < 0.
+__device__ void fused_order(const DevMesh& m, int cls, const int* src, int n, int* cand,
+                            uint8_t* ccls, int* cinst) {
+  __shared__ unsigned long long sk[kFusedMax];
+  __shared__ int se[kFusedMax];
+  __shared__ uint8_t sc[kFusedMax];
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (int t = threadIdx.x; t < np2; t += blockDim.x) {
+    if (t < n) {
+      int c = cls;
+      int e = cls >= 0 ? src[t] : decode_cand(m, src[t], c);
+      sk[t] = prio_key(m, c, e);
+      se[t] = e;
+      sc[t] = (uint8_t)c;
+    } else {
+      sk[t] = ~0ULL;  // after every real key (classes 0..2 stay below 3 << 62)
+      se[t] = 0x7fffffff;
+      sc[t] = 3;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= np2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < np2; t += blockDim.x) {
+        const int u = t ^ stride;
+        if (u > t) {
+          const bool up = (t & size) == 0;
+          const bool after =
+              (sk[t] == ~0ULL || sk[u] == ~0ULL)
+                  ? sk[t] > sk[u]
+                  : cand_before(m, sk[u], sc[u], se[u], sk[t], sc[t], se[t]);
+          if (after == up) {
+            unsigned long long k = sk[t];
+            sk[t] = sk[u];
+            sk[u] = k;
+            int e = se[t];
+            se[t] = se[u];
+            se[u] = e;
+            uint8_t c = sc[t];
+            sc[t] = sc[u];
+            sc[u] = c;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    cand[t] = se[t];
+    if (cls < 0) {
+      const int c = sc[t], e = se[t];
+      ccls[t] = (uint8_t)c;
+      const int v0 = c == CLS_SUBSEG ? m.GV[CKI(e, m.capG)].x
+                                     : (c == CLS_SUBFACE ? m.SV[CKI(e, m.capS)].x
+                                                         : vid(m.T[CKI(e, m.capT)].v.x));
+      cinst[t] = vinst(m, v0);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(32 * kFusedWarps, 1) k_round_fused(DevMesh m, DevRound r, int* hint,
                                                                       int4* offs, FusedOut* out,
-                                                                      int do_stall) {
+                                                                      int do_stall, const int* src,
+                                                                      int* cand_w, uint8_t* ccls_w,
+                                                                      int* cinst_w) {
   extern __shared__ int smraw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
   const int warp = blockIdx.x * kFusedWarps + wib, nwarps = gridDim.x * kFusedWarps;
+  if (src) {  // order the candidates first (instead of separate key, sort and tie launches)
+    if (blockIdx.x == 0) fused_order(m, r.cls, src, r.n, cand_w, ccls_w, cinst_w);
+    cluster_barrier();
+  }
   for (int i = tid; i < r.n; i += nthreads) {
     split_one(m, r, i);
     locate_one(m, r, hint, i);
@@ -2628,7 +2715,8 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 1) k_round_fused(DevMesh m, 
   for (int i = warp; i < r.n; i += nwarps) insert_one(m, r, hint, i, lane);
 }
 void launch_round_fused(const DevMesh& m, const DevRound& r, int* hint, int4* offs, FusedOut* out,
-                        bool do_stall, cudaStream_t s) {
+                        bool do_stall, const int* src, int* cand_w, uint8_t* ccls_w, int* cinst_w,
+                        cudaStream_t s) {
   static bool attr = false;
   const size_t smem = sizeof(Smem1) * kFusedWarps;
   if (!attr) {
@@ -2648,7 +2736,8 @@ void launch_round_fused(const DevMesh& m, const DevRound& r, int* hint, int4* of
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_round_fused, m, r, hint, offs, out, do_stall ? 1 : 0);
+  cudaLaunchKernelEx(&cfg, k_round_fused, m, r, hint, offs, out, do_stall ? 1 : 0, src, cand_w,
+                     ccls_w, cinst_w);
 }
 
 // checked build: first out-of-bounds index seen (site line, index, bound), or 0

@@ -58,8 +58,12 @@ struct FusedOut {
   int4 tot;  // new vertices, tetrahedra, subfaces, subsegments
   int n2;    // regions grown in tier 2
 };
+// src: the round's candidates before ordering (elements, or concatenated
+// indices when r.cls < 0), ordered by the kernel into cand_w (and ccls_w,
+// cinst_w); nullptr if r.cand is already in priority order
 void launch_round_fused(const DevMesh& m, const DevRound& r, int* hint, int4* offs, FusedOut* out,
-                        bool do_stall, cudaStream_t s);
+                        bool do_stall, const int* src, int* cand_w, uint8_t* ccls_w, int* cinst_w,
+                        cudaStream_t s);
 
 // maintenance
 void launch_compact_flags(const DevMesh& m, int* alive, cudaStream_t s);
