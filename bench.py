@@ -49,10 +49,6 @@ WORKLOADS = {
     "cube2k": dict(kind="cube", n=2000, seed=0, B=2.0, n_seg=0, n_tri=0),
     "clustered500k": dict(kind="clustered", n=500_000, seed=2, B=1.4, n_seg=5000, n_tri=5000),
 }
-MULTI = {
-    "batched64": dict(count=64, nmin=1000, nmax=50000, B=(1.6,), seed=1000),
-    "served40": dict(count=40, nmin=2000, nmax=200000, B=(1.4, 1.6, 2.0), seed=10 ** 6),
-}
 METRIC = "Steiner pts inserted/s on 1 GB300"
 UNIT = "Steiner points/s"
 
@@ -315,41 +311,21 @@ def gpu_arm(args, rank, world):
 
 
 # ------------------------------------------------- batched and served arms
-def multi_instances(spec, rank, cdr, stream):
-    """Seeded unit-cube PLCs with log-uniform sizes; initial meshes built on the GPU."""
-    from paper_1903_03406_gb300 import inputs, replicas
-    seed = replicas.instance_seed(spec["seed"], rank)
-    rng = np.random.default_rng(seed)
-    out = []
-    for i in range(spec["count"]):
-        n = int(round(np.exp(rng.uniform(np.log(spec["nmin"]), np.log(spec["nmax"])))))
-        B = float(spec["B"][rng.integers(len(spec["B"]))])
-        pts, _, _ = inputs.box_points("cube", n, seed * 1000 + i)
-        dt = cdr.Handle.delaunay_box(pts, stream=stream)
-        ex = dt.export()
-        dt.close()
-        k = max(1, n // 100)
-        plc = inputs.plc_from_delaunay(pts, ex["tets"], k, k, seed * 1000 + i)
-        out.append(dict(B=B, n=n, mesh=dict(xyz=ex["xyz"], tets=ex["tets"], segs=plc["segs"],
-                                            seg_id=plc["seg_id"], tris=plc["tris"],
-                                            facet_id=plc["facet_id"], nfacets=plc["nfacets"])))
-    return out
-
-
 def _margs(m):
     return (m["xyz"], m["tets"], m["segs"], m["seg_id"], m["tris"], m["facet_id"], m["nfacets"])
 
 
 def multi_arm(args, rank, world):
     import torch
-    from paper_1903_03406_gb300 import cdr, replicas, serve
+    from paper_1903_03406_gb300 import autotune, cdr, replicas, serve, workloads
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cdr.lib()
     stream = torch.cuda.current_stream()
-    spec = MULTI[args.workload]
+    spec = workloads.MULTI[args.workload]
+    tuning = autotune.load()  # the tuner's stored launch setting, if any
     t0 = time.perf_counter()
-    insts = multi_instances(spec, rank, cdr, stream)
+    insts = workloads.multi_instances(spec, rank, cdr, stream)
     log("%d instances ready in %.1fs (%d points)" % (len(insts), time.perf_counter() - t0,
                                                      sum(x["n"] for x in insts)))
     al = cdr.TorchAllocator()
@@ -375,6 +351,7 @@ def multi_arm(args, rank, world):
         t_serial = time.perf_counter() - t0
         t0 = time.perf_counter()
         b = cdr.Batch(allocator=al, stream=stream)
+        autotune.apply(b, tuning)
         slots = [b.add(x["B"], *_margs(x["mesh"])) for x in insts]
         rounds = b.refine()
         batch_ins = []
@@ -403,6 +380,7 @@ def multi_arm(args, rank, world):
                        "points_total": sum(x["n"] for x in insts), "B": spec["B"],
                        "constraints": "1% segments + 1% triangles",
                        "timed": "create/add + refine + export of every instance",
+                       "tuning": tuning or "defaults",
                        "sample": "64 of config 4's 256 instances"},
             "clocks": clk,
         }
@@ -528,7 +506,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uniform100k", choices=sorted(WORKLOADS) + sorted(MULTI))
+    from paper_1903_03406_gb300 import workloads
+    ap.add_argument("--workload", default="uniform100k",
+                    choices=sorted(WORKLOADS) + sorted(workloads.MULTI))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -551,7 +531,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    if args.workload in MULTI:
+    if args.workload in workloads.MULTI:
         line = multi_arm(args, rank, world)
         if line is not None:
             print(json.dumps(line), flush=True)

@@ -279,6 +279,21 @@ const char* cdr_status_string(int status);
 int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_t* calls,
                 int64_t* counters);
 
+/* Launch tuning of a handle (one mesh or a batch). Results do not depend on
+ * it, only speed; zero fields select the defaults.
+ *   fused_max            rounds with at most this many candidates (1..128) run
+ *                        as one kernel; -1: never; 0: 128
+ *   grow1_blocks_per_sm  at most this many blocks per SM in the region-growth
+ *                        grid (1..32); 0: 8
+ *   tier2_warps          warps (each with a global workspace) for regions that
+ *                        outgrow tier 1 (1..4864); 0: 608 */
+typedef struct {
+  int32_t fused_max;
+  int32_t grow1_blocks_per_sm;
+  int32_t tier2_warps;
+} cdr_tuning;
+int cdr_set_tuning(cdr_handle* h, const cdr_tuning* t);
+
 /* Library self-description: sm architecture compiled for, e.g. 103. */
 int cdr_device_arch(void);
 

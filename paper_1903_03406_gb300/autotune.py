@@ -1,0 +1,118 @@
+"""Launch tuning: search the settings `cdr_set_tuning` takes, for a workload.
+
+A setting changes speed only (every setting gives the same meshes), so the tuner
+times a callable that refines a sample workload under each candidate setting
+and keeps the fastest. The search is coordinate descent: one parameter at a
+time over its candidate values, starting from the defaults, repeated while a
+pass improves. The chosen setting is stored as JSON beside this module
+(`tuning.json`) and applied with `apply`.
+
+    python -m paper_1903_03406_gb300.autotune [--instances 16] [--out PATH]
+
+tunes on a sample of the batched workload (unit-cube PLCs, 1k-50k points).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_PATH = os.path.join(HERE, "tuning.json")
+
+DEFAULTS = {"fused_max": 128, "grow1_blocks_per_sm": 8, "tier2_warps": 608}
+SPACE = {
+    "fused_max": [-1, 16, 32, 64, 128],
+    "grow1_blocks_per_sm": [2, 4, 8, 16],
+    "tier2_warps": [152, 304, 608, 1216],
+}
+
+
+def search(measure, space=None, start=None, passes=2):
+    """measure(setting) -> seconds. Returns (best setting, its time, every trial)."""
+    space = SPACE if space is None else space
+    best = dict(DEFAULTS if start is None else start)
+    best_t = measure(best)
+    trials = [(dict(best), best_t)]
+    for _ in range(passes):
+        improved = False
+        for key, values in space.items():
+            for v in values:
+                if v == best[key]:
+                    continue
+                cand = dict(best)
+                cand[key] = v
+                t = measure(cand)
+                trials.append((dict(cand), t))
+                if t < best_t:
+                    best, best_t, improved = cand, t, True
+        if not improved:
+            break
+    return best, best_t, trials
+
+
+def save(setting, info=None, path=DEFAULT_PATH):
+    with open(path, "w") as f:
+        json.dump({"setting": setting, "info": info or {}}, f, indent=1)
+
+
+def load(path=DEFAULT_PATH):
+    """The stored setting, or None."""
+    try:
+        with open(path) as f:
+            return json.load(f)["setting"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def apply(obj, setting):
+    """Apply a setting to a cdr.Handle or cdr.Batch."""
+    if setting:
+        obj.tune(**setting)
+
+
+def _batch_measure(cdr, insts, allocator, stream, repeat=1):
+    import torch
+
+    def measure(setting):
+        best = float("inf")
+        for _ in range(repeat):
+            b = cdr.Batch(allocator=allocator, stream=stream)
+            apply(b, setting)
+            for x in insts:
+                m = x["mesh"]
+                b.add(x["B"], m["xyz"], m["tets"], m["segs"], m["seg_id"], m["tris"],
+                      m["facet_id"], m["nfacets"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.refine()
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+            b.close()
+        return best
+    return measure
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--instances", type=int, default=16)
+    ap.add_argument("--seed", type=int, default=4242)
+    ap.add_argument("--out", default=DEFAULT_PATH)
+    args = ap.parse_args()
+    import torch
+    from paper_1903_03406_gb300 import cdr, workloads
+    cdr.lib()
+    stream = torch.cuda.current_stream()
+    spec = dict(workloads.MULTI["batched64"], count=args.instances, seed=args.seed)
+    insts = workloads.multi_instances(spec, 0, cdr, stream)
+    measure = _batch_measure(cdr, insts, cdr.TorchAllocator(), stream)
+    measure(DEFAULTS)  # warm-up
+    best, t, trials = search(measure)
+    save(best, {"workload": "batched sample of %d instances (seed %d)" % (args.instances, args.seed),
+                "seconds": t, "trials": [[s, tt] for s, tt in trials]}, args.out)
+    print(json.dumps({"setting": best, "seconds": t, "trials": len(trials)}))
+
+
+if __name__ == "__main__":
+    main()

@@ -58,6 +58,11 @@ class Stats(ctypes.Structure):
         return d
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("fused_max", ctypes.c_int32), ("grow1_blocks_per_sm", ctypes.c_int32),
+                ("tier2_warps", ctypes.c_int32)]
+
+
 class Sizes(ctypes.Structure):
     _fields_ = [("n_verts", ctypes.c_int32), ("n_tets", ctypes.c_int32),
                 ("n_subfaces", ctypes.c_int32), ("n_subsegs", ctypes.c_int32),
@@ -131,6 +136,7 @@ def lib():
             L.cdr_batch_export.argtypes = [P, ctypes.c_int32, ctypes.POINTER(MeshOut)]
             L.cdr_batch_remove.argtypes = [P, ctypes.c_int32]
             L.cdr_batch_finished.argtypes = [P, i32p, ctypes.c_int32, i32p]
+            L.cdr_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
             _lib = L
     return _lib
 
@@ -182,6 +188,12 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def set_tuning(ptr, fused_max=0, grow1_blocks_per_sm=0, tier2_warps=0):
+    """Launch tuning of a handle or batch (cdr_set_tuning); results do not depend on it."""
+    t = Tuning(int(fused_max), int(grow1_blocks_per_sm), int(tier2_warps))
+    _check(lib().cdr_set_tuning(ptr, ctypes.byref(t)), "cdr_set_tuning")
 
 
 def _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref=None):
@@ -302,6 +314,9 @@ class Handle:
                     calls={g: int(calls[i]) for i, g in enumerate(self.GROUPS)},
                     counters={c: int(ctr[i]) for i, c in enumerate(self.COUNTERS)})
 
+    def tune(self, **kw):
+        set_tuning(self.ptr, **kw)
+
     def checkpoint(self):
         _check(lib().cdr_checkpoint(self.ptr), "cdr_checkpoint")
 
@@ -406,6 +421,9 @@ class Batch:
 
     def remove(self, slot):
         _check(lib().cdr_batch_remove(self.ptr, int(slot)), "cdr_batch_remove")
+
+    def tune(self, **kw):
+        set_tuning(self.ptr, **kw)
 
     def finished(self):
         """Slots whose instance has finished refining."""

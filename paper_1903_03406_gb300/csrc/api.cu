@@ -69,6 +69,10 @@ struct cdr_handle {
   bool profGrowOnly = false;  // time the region-growth groups only
   cudaEvent_t ev[2 * 32] = {};
   bool fused = true;  // small rounds as one kernel
+  // launch tuning (cdr_set_tuning)
+  int fusedMax = kFusedMax;   // rounds with at most this many candidates run fused
+  int grow1PerSM = 8;         // growth grid: at most this many blocks per SM
+  int tier2Warps = 152 * 4;   // warps (workspaces) for tier-2 growth
   double prof_ms[32] = {};
   long long prof_calls[32] = {};
   long long prof_ctr[32] = {};
@@ -640,7 +644,7 @@ int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unso
 }
 
 // whether a refinement round of n candidates runs as one kernel
-inline bool use_fused(const cdr_handle* h, int n) { return h->fused && n <= kFusedMax; }
+inline bool use_fused(const cdr_handle* h, int n) { return h->fused && n <= h->fusedMax; }
 
 // the shared body of a round once the ordered candidate list is in bCand2
 // (unsorted: the candidates are still unordered in bCand; fused rounds only)
@@ -681,7 +685,7 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsor
   }
   r.epoch = next_epoch(h);
   pmark(h, PG_GROW1, 0);
-  launch_grow1(m, r, s);
+  launch_grow1(m, r, h->grow1PerSM, s);
   pmark(h, PG_GROW1, 1);
   h->prof_ctr[15] += 1;
   used[PG_GROW1] = true;
@@ -701,7 +705,7 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsor
     int n2 = h->pin->n2;
     if (n2 > 0) {
       const size_t stride2 = SlabLayout<Tier2>::STRIDE;
-      int warps = std::min(n2, 152 * 4);
+      int warps = std::min(n2, h->tier2Warps);
       warps += warps & 1;  // the launch runs two warps per block
       if (!ensure(h, h->bSlab2, (size_t)n2 * stride2 * 4) ||
           !ensure(h, h->bWs2, (size_t)warps * Tier2::HCAP * 4))
@@ -2089,6 +2093,19 @@ int cdr_eval_predicates(int32_t kind, const double* in, int32_t n, int32_t* sign
   cudaFree(dout);
   if (cudaGetLastError() != cudaSuccess) return CDR_ERR_CUDA;
   return ov ? CDR_ERR_INTERNAL : CDR_OK;
+}
+
+int cdr_set_tuning(cdr_handle* h, const cdr_tuning* t) {
+  if (!h || !t) return CDR_ERR_INVALID_INPUT;
+  if (t->fused_max < -1 || t->fused_max > kFusedMax || t->grow1_blocks_per_sm < 0 ||
+      t->grow1_blocks_per_sm > 32 || t->tier2_warps < 0 || t->tier2_warps > 152 * 32)
+    return CDR_ERR_INVALID_INPUT;
+  h->fused = t->fused_max != -1;
+  h->fusedMax = t->fused_max > 0 ? t->fused_max : kFusedMax;
+  h->grow1PerSM = t->grow1_blocks_per_sm > 0 ? t->grow1_blocks_per_sm : 8;
+  int w = t->tier2_warps > 0 ? t->tier2_warps : 152 * 4;
+  h->tier2Warps = w + (w & 1);  // tier-2 launches run two warps per block
+  return CDR_OK;
 }
 
 int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_t* calls,

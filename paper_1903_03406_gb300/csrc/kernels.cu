@@ -2395,7 +2395,7 @@ void launch_locate(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t 
 void launch_seed(const DevMesh& m, const DevRound& r, cudaStream_t s) {
   if (r.n > 0) k_seed<<<grid_for(r.n, 256), 256, 0, s>>>(m, r);
 }
-void launch_grow1(const DevMesh& m, const DevRound& r, cudaStream_t s) {
+void launch_grow1(const DevMesh& m, const DevRound& r, int blocks_per_sm, cudaStream_t s) {
   if (r.n <= 0) return;
   static bool attr = false;
   size_t smem = sizeof(Smem1) * kWarps1;
@@ -2404,7 +2404,7 @@ void launch_grow1(const DevMesh& m, const DevRound& r, cudaStream_t s) {
     attr = true;
   }
   long blocks = ((long)r.n + kWarps1 - 1) / kWarps1;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > 152L * blocks_per_sm) blocks = 152L * blocks_per_sm;
   k_grow1<<<(int)blocks, 32 * kWarps1, smem, s>>>(m, r);
 }
 void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s) {

@@ -44,7 +44,7 @@ void launch_decode_cands(const DevMesh& m, int* cand, uint8_t* ccls, int* cinst,
 void launch_split(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_locate(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s);
 void launch_seed(const DevMesh& m, const DevRound& r, cudaStream_t s);
-void launch_grow1(const DevMesh& m, const DevRound& r, cudaStream_t s);
+void launch_grow1(const DevMesh& m, const DevRound& r, int blocks_per_sm, cudaStream_t s);
 void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s);
 void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_insert(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s);

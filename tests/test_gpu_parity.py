@@ -203,6 +203,27 @@ def test_rounds_lockstep_mixed_stall(cdr):
     _lockstep(cdr, om, h, 1.4, 40, "mixed-stall2000")
 
 
+def test_results_do_not_depend_on_tuning(cdr):
+    """Launch tuning changes speed only: with or without the fused small-round
+    kernel, and with other growth grids and tier-2 warp counts, the refined
+    mesh is the same."""
+    om, e, plc = oracle_case("uniform", 1500, 12, 12, 9)
+    ref = None
+    for t in [dict(), dict(fused_max=-1), dict(fused_max=16), dict(grow1_blocks_per_sm=2),
+              dict(tier2_warps=2, fused_max=-1)]:
+        h = gpu_handle(cdr, e, plc)
+        h.tune(**t)
+        st = h.refine(1.4)
+        ex = h.export()
+        h.close()
+        if ref is None:
+            ref = (ex, st)
+        else:
+            assert_same_mesh(ex, ref[0], "tuning %s" % t)
+            assert st["steiner_inserted"] == ref[1]["steiner_inserted"]
+            assert st["rounds"] == ref[1]["rounds"]
+
+
 def test_rounds_lockstep_subsegment_stall(cdr):
     """Dense free segments: two nearby segments whose midpoints encroach one
     another stall a subsegment round (round 46 here); both implementations give
