@@ -181,11 +181,12 @@ def grow_bytes(ctr):
 # -------------------------------------------------------------------- GPU arm
 def gpu_arm(args, rank, world):
     import torch
-    from paper_1903_03406_gb300 import cdr
+    from paper_1903_03406_gb300 import autotune, cdr
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cdr.lib()
+    tuning = autotune.load()  # the tuner's stored launch setting, if any
     stream = torch.cuda.current_stream()
     w = WORKLOADS[args.workload]
     B = w["B"]
@@ -196,6 +197,7 @@ def gpu_arm(args, rank, world):
     h = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
                           plc["facet_id"], plc["nfacets"], mixed_rounds=args.mixed,
                           allocator=al, stream=stream)
+    autotune.apply(h, tuning)
     h.checkpoint()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -259,6 +261,7 @@ def gpu_arm(args, rank, world):
         he = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
                                plc["facet_id"], plc["nfacets"], mixed_rounds=args.mixed,
                                allocator=al, stream=stream)
+        autotune.apply(he, tuning)
         st = he.refine(B, MAX_ROUNDS)
         out = he.export()
         torch.cuda.synchronize()
@@ -290,6 +293,7 @@ def gpu_arm(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": dict(workload_config(args, world), l2="flushed between steps (256 MB write)",
+                       tuning=tuning or "defaults",
                        steiner_per_step=last["steiner_inserted"], rounds_per_step=last["rounds"],
                        final_tets=last["n_tets"], bad_left=last["n_bad_left"], wall_s=t_wall),
         "e2e": {"value": e2e_ins / e2e_max, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -389,6 +393,7 @@ def multi_arm(args, rank, world):
     reqs = [serve.Request(i, 0.0, x["B"], x["mesh"]) for i, x in enumerate(insts)]
     nw = min(8, len(reqs))
     b = cdr.Batch(allocator=al, stream=stream)
+    autotune.apply(b, tuning)
     srv = serve.Server(b, budget_bytes=budget)
     t0 = time.perf_counter()
     for r in reqs[:nw]:
@@ -399,6 +404,7 @@ def multi_arm(args, rank, world):
     b.close()
     rate = 0.8 * closed
     b = cdr.Batch(allocator=al, stream=stream)
+    autotune.apply(b, tuning)
     srv = serve.Server(b, budget_bytes=budget)
     clocks.start()
     t0 = time.perf_counter()
@@ -425,6 +431,7 @@ def multi_arm(args, rank, world):
         "config": {"workload": args.workload, "requests": len(reqs),
                    "points_total": sum(x["n"] for x in insts), "B": spec["B"],
                    "hbm_budget_gb": budget / 1e9, "arrival": "Poisson, 0.8x closed-loop",
+                   "tuning": tuning or "defaults",
                    "sample": "40 of config 5's 2,000 requests"},
         "clocks": clk,
     }
