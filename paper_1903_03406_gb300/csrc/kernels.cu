@@ -1278,6 +1278,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   // ----------------------------------------------------------- tet part
   {
     int head = 0;
+    bool listed = false;
     for (;;) {
       while (head < ncav) {
         int end = ncav;
@@ -1321,26 +1322,52 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         retry = true;
         goto done;
       }
-      // closure
-      bool changed = false, fail = false;
+      // closure. The pass also lists the boundary faces: when it neither adds a
+      // tet nor touches the set, that list is the final one.
+      bool changed = false, fail = false, touched = false;
       int items = ncav * 4;
+      nbnd = 0;
       for (int base = 0; base < items; base += 32) {
         int it = base + lane;
         int cand = -1;
-        bool f_ = false;
+        bool f_ = false, pred = false;
+        int bi = 0, bo = -1, v0 = 0, v1 = 0, v2 = 0;
         if (it < items) {
           int t = w.cav[it >> 2], f = it & 3;
           TetRec rec = ld_tet(m, t);
           int nb = geti(rec.n, f);
+          CKL(nb, m.nT);
           bool sub = face_sub(rec.v, f);
           bool removed = sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
           bool interior = !sub && nb >= 0 && hs_find(w.hset, C::HCAP, nb >> 2) == 1;
-          if (!removed && !interior && orient_rep(m, rec, f, p) <= 0) {
+          pred = !removed && !interior;
+          if (pred && orient_rep(m, rec, f, p) <= 0) {
             if (sub || nb < 0) f_ = true;
             else cand = nb >> 2;
           }
+          bi = (t << 2) | f;
+          bo = nb;
+          int z[3], k = 0;
+          for (int j = 0; j < 4; ++j)
+            if (j != f) z[k++] = vid(geti(rec.v, j));
+          v0 = z[0];
+          v1 = z[1];
+          v2 = z[2];
+        }
+        {
+          unsigned bal = __ballot_sync(FULLMASK, pred);
+          int pos = nbnd + __popc(bal & ((1u << lane) - 1));
+          if (pred && pos < C::CAPB) {
+            w.bin[pos] = bi;
+            w.bout[pos] = bo;
+            w.bv[3 * pos] = v0;
+            w.bv[3 * pos + 1] = v1;
+            w.bv[3 * pos + 2] = v2;
+          }
+          nbnd += __popc(bal);
         }
         fail |= __any_sync(FULLMASK, f_);
+        touched |= __any_sync(FULLMASK, cand >= 0);
         unsigned grp = __match_any_sync(FULLMASK, cand);
         bool leader = cand >= 0 && (__ffs(grp) - 1) == lane;
         bool add = false, bl = false;
@@ -1369,42 +1396,46 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         retry = true;
         goto done;
       }
+      listed = !touched;
       if (!changed) break;
     }
-    // boundary faces
-    int items = ncav * 4;
-    for (int base = 0; base < items; base += 32) {
-      int it = base + lane;
-      bool pred = false;
-      int bi = 0, bo = -1, v0 = 0, v1 = 0, v2 = 0;
-      if (it < items) {
-        int t = w.cav[it >> 2], f = it & 3;
-        TetRec rec = ld_tet(m, t);
-        int nb = geti(rec.n, f);
-        bool sub = face_sub(rec.v, f);
-        bool removed = sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
-        bool interior = !sub && nb >= 0 && hs_find(w.hset, C::HCAP, nb >> 2) == 1;
-        pred = !removed && !interior;
-        bi = (t << 2) | f;
-        bo = nb;
-        CKL(nb, m.nT);
-        int z[3], k = 0;
-        for (int j = 0; j < 4; ++j)
-          if (j != f) z[k++] = vid(geti(rec.v, j));
-        v0 = z[0];
-        v1 = z[1];
-        v2 = z[2];
+    // boundary faces, listed again when the last closure pass touched the set
+    if (!listed) {
+      nbnd = 0;
+      int items = ncav * 4;
+      for (int base = 0; base < items; base += 32) {
+        int it = base + lane;
+        bool pred = false;
+        int bi = 0, bo = -1, v0 = 0, v1 = 0, v2 = 0;
+        if (it < items) {
+          int t = w.cav[it >> 2], f = it & 3;
+          TetRec rec = ld_tet(m, t);
+          int nb = geti(rec.n, f);
+          bool sub = face_sub(rec.v, f);
+          bool removed = sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
+          bool interior = !sub && nb >= 0 && hs_find(w.hset, C::HCAP, nb >> 2) == 1;
+          pred = !removed && !interior;
+          bi = (t << 2) | f;
+          bo = nb;
+          CKL(nb, m.nT);
+          int z[3], k = 0;
+          for (int j = 0; j < 4; ++j)
+            if (j != f) z[k++] = vid(geti(rec.v, j));
+          v0 = z[0];
+          v1 = z[1];
+          v2 = z[2];
+        }
+        unsigned bal = __ballot_sync(FULLMASK, pred);
+        int pos = nbnd + __popc(bal & ((1u << lane) - 1));
+        if (pred && pos < C::CAPB) {
+          w.bin[pos] = bi;
+          w.bout[pos] = bo;
+          w.bv[3 * pos] = v0;
+          w.bv[3 * pos + 1] = v1;
+          w.bv[3 * pos + 2] = v2;
+        }
+        nbnd += __popc(bal);
       }
-      unsigned bal = __ballot_sync(FULLMASK, pred);
-      int pos = nbnd + __popc(bal & ((1u << lane) - 1));
-      if (pred && pos < C::CAPB) {
-        w.bin[pos] = bi;
-        w.bout[pos] = bo;
-        w.bv[3 * pos] = v0;
-        w.bv[3 * pos + 1] = v1;
-        w.bv[3 * pos + 2] = v2;
-      }
-      nbnd += __popc(bal);
     }
     __syncwarp();  // the lists written above are read by other lanes below
     if (nbnd > C::CAPB) {
@@ -1707,7 +1738,7 @@ struct Smem1 {
   int fbv[3 * Tier1::CAPFB];
 };
 
-__global__ void __launch_bounds__(32 * kWarps1) k_grow1(DevMesh m, DevRound r) {
+__global__ void __launch_bounds__(32 * kWarps1, 3) k_grow1(DevMesh m, DevRound r) {
   extern __shared__ int smraw[];
   Smem1* sm = reinterpret_cast<Smem1*>(smraw) + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
