@@ -54,6 +54,9 @@ struct cdr_handle {
   // classification: candidate flags and dirty marks, kept from round to round
   Buf bCandS, bCandG, bCandT, bDirtyS, bDirtyG;
   bool fullClassify = true;  // the next classification tests every element
+  // the next round's classification and counts were enqueued behind the last
+  // round and are already in pinCnt / pin->cerr (one-mesh refinement only)
+  bool preCounted = false;
   // round buffers
   int capR = 0, capR2 = 0, capWs2 = 0;
   Buf bCand, bCand2, bKeys, bKeys2, bSp, bLoc, bStatus, bSurv, bCounts, bOffs, bSlab1, bSlab2of,
@@ -551,6 +554,39 @@ int maybe_compact(cdr_handle* h, bool force) {
 // A refinement round with few candidates as one kernel (k_round_fused): the
 // capacity for the largest growth the kernel could produce is reserved first,
 // the totals are read back once at the end.
+// Classification and per-instance candidate counts (Sec. 2: a round serves the
+// first class with work), read back into pinCnt and pin->cerr at the next
+// synchronisation. add: the last round's additions when the host has not read
+// them yet (one-mesh handles only), else null.
+void enqueue_classify(cdr_handle* h, const int4* add) {
+  DevMesh& m = h->m;
+  cudaStream_t s = h->stream;
+  const int ni = h->ninst;
+  cudaMemsetAsync(h->bErr.p, 0, 64, s);
+  pmark(h, PG_CLASSIFY, 0);
+  launch_classify(m, h->fullClassify, ptr<int>(h->bErr), s, add);
+  h->fullClassify = false;
+  pmark(h, PG_CLASSIFY, 1);
+  h->prof_ctr[15] += 2;  // classification + counts
+  cudaMemsetAsync(h->bInstCnt.p, 0, (size_t)ni * 3 * 8, s);
+  if (h->batch)
+    launch_count_inst(m, ptr<uint8_t>(h->bCandG), ptr<uint8_t>(h->bCandS),
+                      ptr<uint8_t>(h->bCandT), s);
+  else
+    launch_count_single(m, ptr<unsigned long long>(h->bInstCnt), s, add);
+  cudaMemcpyAsync(h->pinCnt, h->bInstCnt.p, (size_t)ni * 3 * 8, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&h->pin->cerr, h->bErr.p, 4, cudaMemcpyDeviceToHost, s);
+}
+
+// Enqueue the next round's classification behind this round's kernels, so
+// that the round's final synchronisation reads both: one-mesh refinement
+// only, and not when the next round must test every element anyway.
+bool enqueue_next_classify(cdr_handle* h, const int4* add) {
+  if (h->batch || h->dt_mode || h->fullClassify) return false;
+  enqueue_classify(h, add);
+  return true;
+}
+
 int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsorted) {
   DevMesh& m = h->m;
   cudaStream_t s = h->stream;
@@ -587,6 +623,8 @@ int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unso
   pmark(h, PG_FUSED, 1);
   used[PG_FUSED] = true;
   h->prof_ctr[15] += 1;
+  const bool next = enqueue_next_classify(
+      h, reinterpret_cast<const int4*>(ptr<char>(h->bFused) + offsetof(FusedOut, tot)));
   FusedOut fo;
   cudaMemcpyAsync(&h->pin->lastOff, ptr<char>(h->bFused), sizeof(int4), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&h->pin->n2, ptr<char>(h->bFused) + offsetof(FusedOut, n2), 4,
@@ -640,6 +678,7 @@ int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unso
   h->prof_ctr[17] += (long long)ctr[ST_CAV];
   h->prof_ctr[18] += (long long)ctr[ST_BND];
   h->deadT += (long long)ctr[ST_DEADT];
+  h->preCounted = next;
   return cuda_status(h);
 }
 
@@ -786,7 +825,9 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsor
     ro->unspl = (long long)st[ST_UNSPL];
     ro->blasted = (long long)st[ST_OK] + (long long)st[ST_BLAST];
   }
-  // one synchronisation for the round's error flags and counters
+  // one synchronisation for the round's error flags and counters (and the
+  // next round's counts)
+  const bool next = cls != CLS_POINT && enqueue_next_classify(h, nullptr);
   const unsigned long long* ctr = h->pin->ctr;
   h->pin->ovf = 0;
   exact_overflow_copy_async(&h->pin->ovf, s);
@@ -811,6 +852,7 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsor
   pcollect(h, used);
   for (int k = 0; k < ST_COUNT && k < 15; ++k) h->prof_ctr[k] += (long long)ctr[k];
   h->deadT += (long long)ctr[ST_DEADT];
+  h->preCounted = next;
   return cuda_status(h);
 }
 
@@ -849,21 +891,14 @@ int refine_round(cdr_handle* h, double B, RoundOut* ro) {
   if (!ensure_round(h, 1024) || !ensure_pinned(h) || !ensure_instances(h, h->ninst))
     return CDR_ERR_OOM;
   const int ni = h->ninst;
-  cudaMemsetAsync(h->bErr.p, 0, 64, s);
-  pmark(h, PG_CLASSIFY, 0);
-  launch_classify(m, h->fullClassify, ptr<int>(h->bErr), s);
-  h->fullClassify = false;
-  pmark(h, PG_CLASSIFY, 1);
-  h->prof_ctr[15] += 2;  // classification + counts
-  cudaMemsetAsync(h->bInstCnt.p, 0, (size_t)ni * 3 * 8, s);
-  if (h->batch)
-    launch_count_inst(m, ptr<uint8_t>(h->bCandG), ptr<uint8_t>(h->bCandS),
-                      ptr<uint8_t>(h->bCandT), s);
-  else
-    launch_count_single(m, ptr<unsigned long long>(h->bInstCnt), s);
-  cudaMemcpyAsync(h->pinCnt, h->bInstCnt.p, (size_t)ni * 3 * 8, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(&h->pin->cerr, h->bErr.p, 4, cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
+  // counts enqueued behind the last round stand unless the mesh or B changed
+  // since (each such change asks for a full classification)
+  const bool pre = h->preCounted && !h->fullClassify;
+  h->preCounted = false;
+  if (!pre) {
+    enqueue_classify(h, nullptr);
+    cudaStreamSynchronize(s);
+  }
   if (cuda_status(h)) return h->err;
   if (h->pin->cerr) return set_err(h, CDR_ERR_INTERNAL);
   {

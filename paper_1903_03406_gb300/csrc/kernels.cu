@@ -408,7 +408,17 @@ __device__ bool edge_ring(const DevMesh& m, int t0, int a, int b, F visit) {
 // subfaces, bad tetrahedra). Incremental: only subsegments and subfaces marked
 // dirty (created or touched by the last round, or flagged since) are tested;
 // tetrahedra get their flag when they are created or retired. full: test all.
-__global__ void k_classify(DevMesh m, int full, int* err) {
+// add: when not null, the element counts that the last round added on the
+// device and the host has not read yet (x vertices, y tets, z subfaces, w
+// subsegments)
+__global__ void k_classify(DevMesh m, int full, int* err, const int4* add) {
+  if (add) {
+    const int4 a = *add;
+    m.nV += a.x;
+    m.nT += a.y;
+    m.nS += a.z;
+    m.nG += a.w;
+  }
   unsigned char* candS = m.candS;
   unsigned char* candG = m.candG;
   unsigned char* candT = m.candT;
@@ -634,8 +644,15 @@ __global__ void k_count_inst(DevMesh m, const uint8_t* candG, const uint8_t* can
 // flags per thread (uint4 loads; flag arrays are allocated in whole 16-byte
 // units), one atomic per warp and class.
 __global__ void k_count_single(const uint8_t* candG, int nG, const uint8_t* candS, int nS,
-                               const uint8_t* candT, int nT, unsigned long long* cnt) {
+                               const uint8_t* candT, int nT, unsigned long long* cnt,
+                               const int4* add) {
   const int lane = threadIdx.x & 31;
+  if (add) {
+    const int4 a = *add;
+    nT += a.y;
+    nS += a.z;
+    nG += a.w;
+  }
   const uint8_t* arr[3] = {candG, candS, candT};
   const int len[3] = {nG, nS, nT};
   for (int c = 0; c < 3; ++c) {
@@ -653,10 +670,13 @@ __global__ void k_count_single(const uint8_t* candG, int nG, const uint8_t* cand
     if (lane == 0 && tot) atomicAdd(&cnt[c], (unsigned long long)tot);
   }
 }
-void launch_count_single(const DevMesh& m, unsigned long long* cnt, cudaStream_t s) {
-  long nv = ((long)std::max(m.nG, std::max(m.nS, m.nT)) + 15) / 16;
+void launch_count_single(const DevMesh& m, unsigned long long* cnt, cudaStream_t s,
+                         const int4* add) {
+  // with additions not yet known on the host the grid covers the capacities
+  long nv = add ? ((long)std::max(m.capG, std::max(m.capS, m.capT)) + 15) / 16
+                : ((long)std::max(m.nG, std::max(m.nS, m.nT)) + 15) / 16;
   k_count_single<<<grid_for(nv, 256), 256, 0, s>>>(m.candG, m.nG, m.candS, m.nS, m.candT, m.nT,
-                                                      cnt);
+                                                      cnt, add);
 }
 
 // This round's candidates: flagged elements of the class their instance serves
@@ -2405,9 +2425,10 @@ void launch_check_create(const DevMesh& m, int* err, cudaStream_t s) {
 void launch_recompute_bad(const DevMesh& m, double B, cudaStream_t s) {
   k_recompute_bad<<<grid_for(m.nT, 256), 256, 0, s>>>(m, B);
 }
-void launch_classify(const DevMesh& m, bool full, int* err, cudaStream_t s) {
-  long n = (long)m.nG + m.nS + (full ? m.nT : 0);
-  if (n > 0) k_classify<<<grid_for(n, 256), 256, 0, s>>>(m, full ? 1 : 0, err);
+void launch_classify(const DevMesh& m, bool full, int* err, cudaStream_t s, const int4* add) {
+  long n = add ? (long)m.capG + m.capS + (full ? m.capT : 0)
+               : (long)m.nG + m.nS + (full ? m.nT : 0);
+  if (n > 0) k_classify<<<grid_for(n, 256), 256, 0, s>>>(m, full ? 1 : 0, err, add);
 }
 void launch_prio(const DevMesh& m, int cls, const int* elems, int n, unsigned long long* keys,
                  cudaStream_t s) {

@@ -27,14 +27,17 @@ void launch_check_create(const DevMesh& m, int* err, cudaStream_t s);
 void launch_recompute_bad(const DevMesh& m, double B, cudaStream_t s);
 
 // classification and queues
-void launch_classify(const DevMesh& m, bool full, int* err, cudaStream_t s);
+// add: counts added by the last round that the host has not read yet, or null
+void launch_classify(const DevMesh& m, bool full, int* err, cudaStream_t s,
+                     const int4* add = nullptr);
 void launch_prio(const DevMesh& m, int cls, const int* elems, int n, unsigned long long* keys,
                  cudaStream_t s);
 void launch_tiefix(const DevMesh& m, int cls, const unsigned long long* keys, int* elems, int n,
                    cudaStream_t s);
 void launch_count_inst(const DevMesh& m, const uint8_t* candG, const uint8_t* candS,
                        const uint8_t* candT, cudaStream_t s);
-void launch_count_single(const DevMesh& m, unsigned long long* cnt, cudaStream_t s);
+void launch_count_single(const DevMesh& m, unsigned long long* cnt, cudaStream_t s,
+                         const int4* add = nullptr);
 void launch_round_flags(const DevMesh& m, const uint8_t* candG, const uint8_t* candS,
                         const uint8_t* candT, uint8_t* out, cudaStream_t s);
 void launch_decode_cands(const DevMesh& m, int* cand, uint8_t* ccls, int* cinst, int n,
