@@ -264,7 +264,7 @@ const char* cdr_status_string(int status);
  *   ms[32]   accumulated milliseconds per group: 0 classify, 1 order, 2 split,
  *            3 locate, 4 grow (tier 1), 5 grow (tier 2), 6 select, 7 scan,
  *            8 insert, 9 compact, 10 whole rounds run as one kernel (rounds
- *            with at most 64 candidates)
+ *            with at most cdr_tuning.fused_max candidates, 128 by default)
  *   calls[32] launches timed per group
  *   counters[32] 0 refused, 1 unsplittable, 2 eligible-but-blasted, 3 inserted,
  *            4 retried in tier 2, 5 invariant failures, 6 neighbour tetrahedra
