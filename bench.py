@@ -270,6 +270,12 @@ def gpu_arm(args, rank, world):
         d2h = sum(v.nbytes for v in out.values())
         he.close()
     t_e2e = time.perf_counter() - t0
+    # quality of the last exported mesh (host report, outside every timed region)
+    from paper_1903_03406_gb300 import quality
+    try:
+        qual = quality.report(out["xyz"], out["tets"], B)
+    except Exception as e:  # a report, not a measurement: never lose the line over it
+        qual = {"error": repr(e)}
 
     # max over ranks of the time, sum of the work (independent instances)
     from paper_1903_03406_gb300 import replicas
@@ -310,6 +316,7 @@ def gpu_arm(args, rank, world):
                      "group_ms_per_step_untimed_profile": {g: v for g, v in breakdown.items()
                                                            if v > 0}},
         "gpu_launches": launches,
+        "quality": qual,
         "clocks": clk,
     }
     return line
