@@ -294,3 +294,57 @@ def test_priority_hash_is_splitmix64():
     Q = P.copy()
     Q[2, 1] = 0.0
     assert oracle.prio_hash_xyz(2, P) != oracle.prio_hash_xyz(2, Q)
+
+
+def _facet_ref_point(a, b, c, s):
+    """The per-facet reference point of the in-facet reading: the triangle's
+    first vertex moved by s along its dominant normal axis (ties to the lowest)."""
+    n = np.cross(b - a, c - a)
+    k = int(np.argmax(np.abs(n)))  # argmax keeps the first of equal values
+    q = a.copy()
+    q[k] += s
+    return q
+
+
+def _ref_in_circumcircle(a, b, c, p):
+    """Exact sign of (R^2 - |p - cc|^2) with cc the rational circumcentre of abc."""
+    cc = ref_tri_circumcentre(a, b, c)
+    A, P = fr(a), fr(p)
+    return sgn(dot(sub(A, cc), sub(A, cc)) - dot(sub(P, cc), sub(P, cc)))
+
+
+def test_in_facet_circle_reading_is_the_facet_incircle():
+    """For a point in the facet's plane, the sphere through the subface and the
+    facet's reference point q_f cuts that plane in the subface's circumcircle,
+    so insphere(a, b, c, q_f, p) times the winding orient3d(a, b, c, q_f) is
+    the in-circumcircle sign of p, whatever the plane and the vertex order."""
+    rng = np.random.default_rng(17)
+    circle = [(5, 0), (0, 5), (-5, 0), (0, -5), (3, 4), (4, 3), (-3, 4), (-4, -3), (3, -4)]
+    planes = [  # maps from integer (u, v) to points exactly on a plane
+        lambda u, v: np.array([u, v, 7.0]),                 # z = 7
+        lambda u, v: np.array([u + 2.0, -3.0, v]),          # y = -3
+        lambda u, v: np.array([u, v, -u - v + 1.0]),        # x + y + z = 1 (normal ties)
+        lambda u, v: np.array([u, v, 2.0 * u - v + 3.0]),   # slanted, dominant axis z
+    ]
+    seen = {-1: 0, 0: 0, 1: 0}
+    for trial in range(600):
+        to3 = planes[trial % len(planes)]
+        if trial % 3 == 0 and trial % len(planes) < 2:
+            # cocircular quadruples on an axis-aligned plane: p on the circle
+            idx = rng.choice(len(circle), size=4, replace=False)
+            a, b, c, p = (to3(*map(float, circle[i])) for i in idx)
+        else:
+            uv = rng.integers(-6, 7, size=(4, 2)).astype(np.float64)
+            a, b, c, p = (to3(*w) for w in uv)
+        if np.linalg.norm(np.cross(b - a, c - a)) == 0:
+            continue
+        q = _facet_ref_point(a, b, c, 64.0)
+        wind = oracle.orient3d(a, b, c, q)
+        assert wind != 0
+        got = oracle.insphere(a, b, c, q, p) * wind
+        exp = _ref_in_circumcircle(a, b, c, p)
+        assert got == exp, (a, b, c, p)
+        # the reversed triangle reads the same circle
+        assert oracle.insphere(b, a, c, q, p) * oracle.orient3d(b, a, c, q) == exp
+        seen[exp] += 1
+    assert min(seen.values()) > 20, seen
