@@ -527,7 +527,7 @@ def reference_arm(args, rank, world):
         "data": "synthetic",
         "config": workload_config(args, world),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "sequential refinement, %.0f s of insertions per step" %
+                         "sample": "sequential refinement, %g s of insertions per step" %
                                    args.ref_seconds},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
