@@ -380,6 +380,12 @@ def multi_arm(args, rank, world):
         if rank != 0:
             return None
         n_all = len(insts) * world
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            log("cpu baseline: the oracle on all host cores")
+            cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else \
+                (os.cpu_count() or 1)
+            cpu = oracle_all_cores(workloads.multi_specs(spec, rank), cores)
         return {
             "metric": "batched vs serial meshes/s", "value": n_all / t_b, "unit": "meshes/s",
             "serial": {"value": n_all / t_s, "unit": "meshes/s", "steiner_per_s": ins_s / t_s},
@@ -396,6 +402,7 @@ def multi_arm(args, rank, world):
                        "tuning": tuning or "defaults",
                        "sample": "64 of config 4's 256 instances"},
             "clocks": clk,
+            "cpu_baseline": cpu,
         }
     # served: a closed-loop run of every request (all arrived at once: the
     # server's capacity), then a Poisson stream of them at 0.8x that rate
@@ -476,6 +483,43 @@ def workload_config(args, world):
 
 
 # ---------------------------------------------------------- CPU (oracle) arm
+def _oracle_instance_job(x):
+    """One instance of a multi-instance workload refined by the oracle's
+    sequential refinement, in a worker process: its Delaunay mesh and
+    constraints are built untimed, the refinement is timed."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1903_03406_gb300 import inputs, workloads
+    pts, _, _ = inputs.box_points("cube", x["n"], x["seed"])
+    om = oracle.Mesh.box_delaunay(pts)
+    e = om.export()
+    plc = workloads.instance_plc(pts, e["tets"], x["n"], x["seed"])
+    om.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"], plc["nfacets"])
+    t0 = time.perf_counter()
+    st = om.refine_S(x["B"])
+    return time.perf_counter() - t0, st["inserted"]
+
+
+def oracle_all_cores(specs, cores):
+    """The oracle on all host cores: `cores` processes (spawned, so safe after
+    CUDA is initialised) refine the first `cores` instances, one each. A core
+    that refines meshes back to back finishes one per mean refinement time, so
+    the host's rate is cores / mean time. Initial Delaunay meshes excluded."""
+    import multiprocessing as mp
+    sample = specs[:cores]
+    with mp.get_context("spawn").Pool(len(sample)) as pool:
+        res = pool.map(_oracle_instance_job, sample, chunksize=1)
+    mean_t = sum(t for t, _ in res) / len(res)
+    ins = sum(i for _, i in res)
+    return {"value": len(sample) / mean_t, "unit": "meshes/s", "cores": len(sample),
+            "kind": "oracle",
+            "sample": "the first %d instances (%d to %d points), one per core, sequential "
+                      "refinement, %d insertions, mean %.2f s per mesh" %
+                      (len(sample), min(x["n"] for x in sample), max(x["n"] for x in sample),
+                       ins, mean_t)}
+
+
 def oracle_workload(name):
     import oracle
     from paper_1903_03406_gb300 import inputs
