@@ -176,7 +176,15 @@ int cdr_export(cdr_handle* h, const cdr_mesh_out* out);
  *   pts[n_cand*3]       splitting point
  *   outcome[n_cand]     0 eligible, 1 refused (encroachment), 2 unsplittable,
  *                       4 stopped on a higher-priority start tetrahedron
- *   reason[n_cand]      detail code (see DESIGN notes in the repository)
+ *   reason[n_cand]      detail code: 0 none, 1 degenerate or non-finite point,
+ *                       2 / 3 the walk crossed a subface / subsegment,
+ *                       4 walk or ring step limit, 5 the walk left the hull,
+ *                       6 the region failed a validity check (closure, star,
+ *                       boundary vertices), 7 cavity over the limit,
+ *                       8 shortest-edge guard, 9 encroaches a subface or
+ *                       subsegment, 10 given up by the stall rule of
+ *                       subsegment rounds, 11 encroaches only unsplittable
+ *                       elements, 12 would delete a subsegment
  *   survived[n_cand]    1 if inserted
  *   n_cav[n_cand], n_bnd[n_cand], n_fcav[n_cand]  region sizes
  *   cav[n_cav_total*4]  each candidate's cavity tetrahedra as sorted vertex ids,
