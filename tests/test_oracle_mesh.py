@@ -216,3 +216,70 @@ def test_cavity_limit_gives_points_up_and_keeps_the_mesh_valid():
     m2, *_ = constrained_mesh(300, 3, 3, seed=8)
     _, overflows2 = _run_rounds(m2, B)
     assert overflows2 == 0
+
+
+def _faces(t):
+    a, b, c, d = t
+    return [tuple(sorted(x)) for x in ((b, c, d), (a, c, d), (a, b, d), (a, b, c))]
+
+
+def _check_cavities_by_brute_force(snap, rep):
+    """Every eligible candidate's cavity, on a mesh whose only constraints are
+    on the hull (so it stays Delaunay), is the Bowyer-Watson region of its
+    point: the tetrahedra whose circumsphere strictly contains p, connected
+    through shared faces to the tetrahedra that contain p. Tetrahedra with p
+    on their circumsphere may join only through the star closure. Returns
+    (candidates checked, cavities equal to the strict region)."""
+    xyz, tets = snap["xyz"], snap["tets"]
+    key = [tuple(sorted(t)) for t in tets]
+    index = {k: i for i, k in enumerate(key)}
+    f2t = {}
+    for i, t in enumerate(key):
+        for f in _faces(t):
+            f2t.setdefault(f, []).append(i)
+    off = np.concatenate([[0], np.cumsum(rep["ncav"])])
+    n = same = 0
+    for i in np.nonzero(rep["outcome"] == oracle.OUT_OK)[0]:
+        p = rep["pts"][i]
+        C = {index[tuple(t)] for t in rep["cav"][off[i]:off[i + 1]]}
+        ins = np.array([oracle.insphere(*xyz[t], p) for t in tets])
+        inside = set(np.nonzero(ins > 0)[0])
+        holds = [j for j, t in enumerate(tets)
+                 if all(oracle.orient3d(*[p if k == q else xyz[t[k]] for k in range(4)]) >= 0
+                        for q in range(4))]
+        assert holds and set(holds) <= C
+        K = {j for j in holds if j in inside}
+        stack = list(K)
+        while stack:
+            j = stack.pop()
+            for f in _faces(key[j]):
+                for nb in f2t[f]:
+                    if nb in inside and nb not in K:
+                        K.add(nb)
+                        stack.append(nb)
+        assert K <= C
+        assert all(ins[j] >= 0 for j in C)
+        n += 1
+        same += K == C
+    return n, same
+
+
+def test_cavities_are_bowyer_watson_regions():
+    """Sec. 2's Delaunay region of a splitting point, checked by brute force over
+    every tetrahedron, for the first rounds of each class."""
+    m, *_ = cube_mesh(150, seed=9)
+    B = 2.0
+    seen = {0: 0, 1: 0, 2: 0}
+    n = same = 0
+    for _ in range(2000):
+        snap = m.export()
+        cls = m.round(B)["cls"]
+        if cls < 0:
+            break
+        if seen[cls] < 3:
+            seen[cls] += 1
+            a, b = _check_cavities_by_brute_force(snap, m.report())
+            n += a
+            same += b
+    assert seen == {0: 3, 1: 3, 2: 3}
+    assert n > 50 and same == n  # no cospherical ties here: every cavity is the strict region
