@@ -283,3 +283,61 @@ def test_cavities_are_bowyer_watson_regions():
             same += b
     assert seen == {0: 3, 1: 3, 2: 3}
     assert n > 50 and same == n  # no cospherical ties here: every cavity is the strict region
+
+
+def _global_encroached(ex):
+    """Subsegments and subfaces to split, by brute force over every mesh vertex:
+    those with a vertex strictly inside their diametral (equatorial) sphere, or
+    flagged by a refused point; unsplittable ones excluded. Floating point only
+    preselects the vertices near the sphere; the exact predicates decide."""
+    xyz = ex["xyz"]
+    used = np.unique(ex["tets"])
+    V = xyz[used]
+    s2 = np.abs(xyz).max() ** 2
+    ng = ns = 0
+    for (a, b, _), fl in zip(ex["ss"], ex["ssflag"]):
+        if fl & 2:
+            continue
+        if fl & 1:
+            ng += 1
+            continue
+        A, Bv = xyz[a], xyz[b]
+        near = np.nonzero(np.einsum("ij,ij->i", A - V, Bv - V) < 1e-9 * s2)[0]
+        ng += any(oracle.diametral(A, Bv, xyz[used[j]]) < 0
+                  for j in near if used[j] not in (a, b))
+    for (a, b, c, _), fl in zip(ex["sf"], ex["sfflag"]):
+        if fl & 2:
+            continue
+        if fl & 1:
+            ns += 1
+            continue
+        A, Bv, Cv = xyz[a], xyz[b], xyz[c]
+        cc, _ok = oracle.tri_circumcenter(A, Bv, Cv)
+        R2 = np.sum((A - cc) ** 2)
+        near = np.nonzero(np.sum((V - cc) ** 2, axis=1) - R2 < 1e-9 * R2 + 1e-12 * s2)[0]
+        ns += any(oracle.equatorial(A, Bv, Cv, xyz[used[j]]) < 0
+                  for j in near if used[j] not in (a, b, c))
+    return ng, ns
+
+
+@pytest.mark.parametrize("case", ["cube", "constrained"])
+def test_local_encroachment_equals_global_brute_force(case):
+    """Reading c1/r1 tests encroachment locally (the apexes of the tetrahedra
+    around the element). On a CDT that finds every encroaching vertex: the
+    class queues equal a brute-force test over all vertices, round by round."""
+    if case == "cube":
+        m, *_ = cube_mesh(300, seed=21)
+        B, rounds = 2.0, 400
+    else:
+        m, *_ = constrained_mesh(400, 4, 4, seed=22)
+        B, rounds = 1.5, 25
+    total = [0, 0]
+    for _ in range(rounds):
+        q = m.classify(B)
+        g = _global_encroached(m.export())
+        assert (q[0], q[1]) == g
+        total[0] += g[0]
+        total[1] += g[1]
+        if m.round(B)["cls"] < 0:
+            break
+    assert total[0] > 20 and total[1] > 20
