@@ -341,3 +341,22 @@ def test_local_encroachment_equals_global_brute_force(case):
         if m.round(B)["cls"] < 0:
             break
     assert total[0] > 20 and total[1] > 20
+
+
+def test_every_round_leaves_a_cdt():
+    """Sec. 2: the mesh is a CDT again at the end of every round (the survivors'
+    regions and shells are disjoint, so their concurrent insertion is valid)."""
+    m, *_ = constrained_mesh(500, 5, 5, seed=23)
+    B = 1.5
+    classes = set()
+    for _ in range(1000):
+        o = m.round(B)
+        if o["cls"] < 0:
+            break
+        classes.add(o["cls"])
+        c = m.check(B)
+        assert c["bad_orient"] == 0 and c["nonlocal_delaunay"] == 0
+        assert abs(c["vol_rel_err"]) < 1e-12 and c["euler"] == 1
+        assert c["sf_not_face"] == 0 and c["ss_not_edge"] == 0 and c["hull_not_subface"] == 0
+        assert c["seg_chain_bad"] == 0 and c["facet_area_rel_err"] < 1e-12
+    assert classes == {0, 1, 2}
