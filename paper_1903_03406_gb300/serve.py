@@ -36,6 +36,8 @@ DEFAULT_GROWTH = {1.4: 4.6, 1.6: 2.7, 2.0: 1.6}
 # subfaces and subsegments, the per-round candidate slabs, and headroom for the
 # batch's 1.5x capacity growth
 DEFAULT_BYTES_PER_VERTEX = 1400
+# status of a failed device allocation (CDR_ERR_OOM in include/cdr.h)
+CDR_ERR_OOM = -2
 
 
 @dataclass
@@ -98,6 +100,7 @@ class Server:
     results: list = field(default_factory=list)
     used_bytes: int = 0
     rounds: int = 0
+    oom_deferrals: int = 0
 
     def submit(self, req: Request):
         n = len(req.mesh["xyz"])
@@ -108,16 +111,28 @@ class Server:
         heapq.heappush(self.waiting, (req.arrival, req.rid, req))
 
     def admit(self, now):
-        """Admit arrived requests in arrival order while the budget allows."""
+        """Admit arrived requests in arrival order while the budget allows.
+
+        A request leaves the queue only once the batch has taken it. If the
+        device runs out of memory although the estimate fit the budget
+        (status CDR_ERR_OOM), admission stops for this step and the request
+        waits for running instances to retire; with nothing running, nothing
+        would free memory, so the error is raised."""
         admitted = 0
         while self.waiting and self.waiting[0][0] <= now:
             req = self.waiting[0][2]
             if self.used_bytes + req.est_bytes > self.budget_bytes:
                 break
-            heapq.heappop(self.waiting)
             m = req.mesh
-            slot = self.batch.add(req.B, m["xyz"], m["tets"], m["segs"], m["seg_id"], m["tris"],
-                                  m["facet_id"], m["nfacets"])
+            try:
+                slot = self.batch.add(req.B, m["xyz"], m["tets"], m["segs"], m["seg_id"],
+                                      m["tris"], m["facet_id"], m["nfacets"])
+            except Exception as exc:
+                if getattr(exc, "status", None) != CDR_ERR_OOM or not self.running:
+                    raise
+                self.oom_deferrals += 1
+                break
+            heapq.heappop(self.waiting)
             self.running[slot] = (req, self.clock())
             self.used_bytes += req.est_bytes
             admitted += 1

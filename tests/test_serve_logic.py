@@ -120,3 +120,55 @@ def test_poisson_arrivals():
     t = serve.poisson_arrivals(20000, rate=50.0, seed=3)
     assert np.all(np.diff(t) > 0)
     assert abs(len(t) / t[-1] - 50.0) < 2.0
+
+
+class _Oom(RuntimeError):
+    status = serve.CDR_ERR_OOM
+
+
+class OomOnceBatch(FakeBatch):
+    """The device refuses one admission for lack of memory."""
+
+    def __init__(self, fail_at):
+        super().__init__()
+        self.calls = 0
+        self.fail_at = fail_at
+
+    def add(self, B, xyz, *rest):
+        self.calls += 1
+        if self.calls == self.fail_at:
+            raise _Oom("out of device memory")
+        return super().add(B, xyz, *rest)
+
+
+def test_out_of_memory_admission_waits_and_loses_nothing():
+    b = OomOnceBatch(fail_at=2)
+    srv = serve.Server(b, budget_bytes=10 ** 12, clock=Clock())
+    for i in range(4):
+        srv.submit(serve.Request(i, arrival=0.0, B=1.6, mesh=_mesh(300 + 100 * i)))
+    srv.admit(1.0)
+    # the second request met the refusal: it still waits, and its bytes are not counted
+    assert len(srv.running) == 1 and len(srv.waiting) == 3 and srv.oom_deferrals == 1
+    assert srv.used_bytes == srv.running[0][0].est_bytes
+    res = srv.run()
+    assert sorted(r.rid for r in res) == [0, 1, 2, 3]
+    assert srv.used_bytes == 0
+
+
+def test_out_of_memory_with_nothing_running_is_raised():
+    srv = serve.Server(OomOnceBatch(fail_at=1), budget_bytes=10 ** 12, clock=Clock())
+    srv.submit(serve.Request(0, arrival=0.0, B=1.6, mesh=_mesh(300)))
+    with pytest.raises(_Oom):
+        srv.admit(1.0)
+    assert len(srv.waiting) == 1
+
+
+def test_other_admission_errors_are_raised():
+    class Broken(FakeBatch):
+        def add(self, *a):
+            raise ValueError("malformed mesh")
+
+    srv = serve.Server(Broken(), budget_bytes=10 ** 12, clock=Clock())
+    srv.submit(serve.Request(0, arrival=0.0, B=1.6, mesh=_mesh(300)))
+    with pytest.raises(ValueError):
+        srv.admit(1.0)
