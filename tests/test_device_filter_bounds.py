@@ -1,4 +1,4 @@
-"""Soundness of the device predicates' FP32 first stage, emulated on the CPU.
+"""Soundness of the device predicates' floating-point stages, emulated on the CPU.
 
 The CUDA orient3d and insphere first decide in FP32: coordinate differences
 formed in FP64 and rounded once to FP32, the determinant and its permanent
@@ -124,6 +124,118 @@ def test_insphere_fp32_stage_never_decides_a_wrong_sign(scale):
         wrong += w
         decided += n
         wrong_small += _wrong(*insphere_stage(*args, shrink=64), ex, args)[0]
+    assert wrong == 0
+    assert decided > 1000
+    assert wrong_small > 0
+
+
+# ----------------------------------------------------------- FP64 filters
+# The second stage: the same polynomials in FP64 from FP64 differences, with
+# bounds 16u (orient3d), 40u (insphere), 12u (diametral), 48u (equatorial)
+# times the permanent, u = 2^-53, and a sign only when the permanent exceeds
+# 1e-250. Restated here in numpy float64 like the FP32 stage above.
+EPS = 2.0 ** -53
+TINY = 1e-250
+
+
+def _decide64(val, perm, k):
+    bound = k * EPS * perm
+    dec = (perm > TINY) & ((val > bound) | (-val > bound))
+    return dec, np.sign(val).astype(int)
+
+
+def orient_fp64(a, b, c, d, shrink=1):
+    u, v, w = b - a, c - a, d - a
+    det, perm = _det3(*u.T, *v.T, *w.T)
+    return _decide64(det, perm, 16 / shrink)
+
+
+def insphere_fp64(a, b, c, d, e, shrink=1):
+    A, Bq, C, D = (p - e for p in (a, b, c, d))
+    al, bl, cl, dl = ((q[:, 0] * q[:, 0] + q[:, 1] * q[:, 1]) + q[:, 2] * q[:, 2]
+                      for q in (A, Bq, C, D))
+    m1, p1 = _det3(*A.T, *Bq.T, *C.T)
+    m2, p2 = _det3(*A.T, *Bq.T, *D.T)
+    m3, p3 = _det3(*A.T, *C.T, *D.T)
+    m4, p4 = _det3(*Bq.T, *C.T, *D.T)
+    det = -(((dl * m1 - cl * m2) + bl * m3) - al * m4)
+    perm = ((dl * p1 + cl * p2) + bl * p3) + al * p4
+    return _decide64(det, perm, 40 / shrink)
+
+
+def diametral_fp64(a, b, p, shrink=1):
+    A, Bq = a - p, b - p
+    v = (A[:, 0] * Bq[:, 0] + A[:, 1] * Bq[:, 1]) + A[:, 2] * Bq[:, 2]
+    perm = (np.abs(A[:, 0] * Bq[:, 0]) + np.abs(A[:, 1] * Bq[:, 1])) + np.abs(A[:, 2] * Bq[:, 2])
+    return _decide64(v, perm, 12 / shrink)
+
+
+def equatorial_fp64(a, b, c, p, shrink=1):
+    ux, uy, uz = (b - a).T
+    vx, vy, vz = (c - a).T
+    wx, wy, wz = (p - a).T
+    ab = np.abs
+    nx, ny, nz = uy * vz - uz * vy, uz * vx - ux * vz, ux * vy - uy * vx
+    Nx, Ny, Nz = (ab(uy * vz) + ab(uz * vy), ab(uz * vx) + ab(ux * vz),
+                  ab(ux * vy) + ab(uy * vx))
+    lu = (ux * ux + uy * uy) + uz * uz
+    lv = (vx * vx + vy * vy) + vz * vz
+    lw = (wx * wx + wy * wy) + wz * wz
+    ln = (nx * nx + ny * ny) + nz * nz
+    Ln = (Nx * Nx + Ny * Ny) + Nz * Nz
+    vnx, vny, vnz = vy * nz - vz * ny, vz * nx - vx * nz, vx * ny - vy * nx
+    VNx, VNy, VNz = ab(vy) * Nz + ab(vz) * Ny, ab(vz) * Nx + ab(vx) * Nz, ab(vx) * Ny + ab(vy) * Nx
+    nux, nuy, nuz = ny * uz - nz * uy, nz * ux - nx * uz, nx * uy - ny * ux
+    NUx, NUy, NUz = Ny * ab(uz) + Nz * ab(uy), Nz * ab(ux) + Nx * ab(uz), Nx * ab(uy) + Ny * ab(ux)
+    mx, my, mz = lu * vnx + lv * nux, lu * vny + lv * nuy, lu * vnz + lv * nuz
+    Mx, My, Mz = lu * VNx + lv * NUx, lu * VNy + lv * NUy, lu * VNz + lv * NUz
+    D = lw * ln - ((wx * mx + wy * my) + wz * mz)
+    perm = lw * Ln + ((ab(wx) * Mx + ab(wy) * My) + ab(wz) * Mz)
+    return _decide64(D, perm, 48 / shrink)
+
+
+def _near_diametral(rng, n, scale, noise):
+    a, b = (rng.uniform(0, scale, size=(n, 3)) for _ in range(2))
+    dirs = rng.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    p = (a + b) / 2 + dirs * np.linalg.norm(b - a, axis=1, keepdims=True) / 2
+    return a, b, p + rng.normal(size=(n, 3)) * noise * scale
+
+
+def _near_equatorial(rng, n, scale, noise):
+    a, b, c = (rng.uniform(0, scale, size=(n, 3)) for _ in range(3))
+    u, v = b - a, c - a
+    nrm = np.cross(u, v)
+    cc = a + (np.einsum("ij,ij->i", u, u)[:, None] * np.cross(v, nrm) +
+              np.einsum("ij,ij->i", v, v)[:, None] * np.cross(nrm, u)) / \
+        (2 * np.einsum("ij,ij->i", nrm, nrm)[:, None])
+    dirs = rng.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    p = cc + dirs * np.linalg.norm(a - cc, axis=1, keepdims=True)
+    return a, b, c, p + rng.normal(size=(n, 3)) * noise * scale
+
+
+FP64_CASES = [
+    ("orient", lambda r, n, s, z: _near_coplanar(r, n, s, z), orient_fp64,
+     lambda a, b, c, d: oracle.orient3d(a, b, c, d, exact=True)),
+    ("insphere", lambda r, n, s, z: _near_cospherical(r, n, s, z), insphere_fp64,
+     lambda a, b, c, d, e: oracle.insphere(a, b, c, d, e, exact=True)),
+    ("diametral", _near_diametral, diametral_fp64, oracle.diametral),
+    ("equatorial", _near_equatorial, equatorial_fp64, oracle.equatorial),
+]
+
+
+@pytest.mark.parametrize("name,gen,stage,exact", FP64_CASES, ids=[c[0] for c in FP64_CASES])
+def test_fp64_filters_never_decide_a_wrong_sign(name, gen, stage, exact):
+    rng = np.random.default_rng(sum(map(ord, name)))
+    wrong = decided = wrong_small = 0
+    for scale in (1.0, 1000.0):
+        for noise in (1e-16, 1e-15, 1e-14, 1e-12):
+            args = gen(rng, 1500, scale, noise)
+            w, n = _wrong(*stage(*args), exact, args)
+            wrong += w
+            decided += n
+            wrong_small += _wrong(*stage(*args, shrink=256), exact, args)[0]
     assert wrong == 0
     assert decided > 1000
     assert wrong_small > 0
