@@ -71,3 +71,22 @@ def test_binding_constants_match_header():
     m = re.search(r"#define\s+CDR_EVAL_NOALLOC_MAX_ITEMS\s+(\d+)", _header_text())
     assert int(m.group(1)) == cdr.EVAL_NOALLOC_MAX_ITEMS
     assert declared_enum("CDR_ERR_TOO_LARGE") == -6
+
+
+def test_plain_c_caller(built_lib, tmp_path):
+    """cdr.h compiles as C99 and a C program links libcdr.so and calls it
+    (host-side calls only: no GPU is needed)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    exe = str(tmp_path / "c_abi_host")
+    libdir = os.path.dirname(built_lib)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi_host.c"), "-L", libdir, "-lcdr",
+                    "-Wl,-rpath," + libdir, "-o", exe], check=True)
+    p = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert p.returncode == 0, p.stdout + p.stderr
+    assert p.stdout.strip().endswith("ok")
