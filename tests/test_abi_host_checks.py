@@ -164,3 +164,39 @@ def test_binding_raises_when_the_library_is_missing(cdr, monkeypatch, tmp_path):
     with pytest.raises(RuntimeError):
         cdr.Handle.create(*[_cube()[k] for k in ("xyz", "tets", "segs", "seg_id", "tris",
                                                  "facet_id", "n_facets")])
+
+
+class _RefusingAllocator:
+    """A cdr_allocator whose alloc always fails (returns NULL); counts calls."""
+
+    def __init__(self, cdr):
+        self.allocs = 0
+        self.frees = 0
+        self._a = cdr.ALLOC_FN(self._alloc)
+        self._f = cdr.FREE_FN(self._free)
+        self.struct = cdr.Allocator(self._a, self._f, None)
+
+    def _alloc(self, nbytes, ctx, stream):
+        self.allocs += 1
+        return None
+
+    def _free(self, ptr, nbytes, ctx, stream):
+        self.frees += 1
+
+
+def test_failing_allocator_gives_out_of_memory(cdr):
+    """A caller's allocator that has no memory left: creation stops at the first
+    request with CDR_ERR_OOM, frees nothing it did not get and leaves no handle
+    (the device is never reached, so this runs without a GPU)."""
+    m = _cube()
+    al = _RefusingAllocator(cdr)
+    with pytest.raises(cdr.CdrError) as e:
+        cdr.Handle.create(m["xyz"], m["tets"], m["segs"], m["seg_id"], m["tris"],
+                          m["facet_id"], m["n_facets"], allocator=al)
+    assert e.value.status == -2
+    assert al.allocs == 1 and al.frees == 0
+    al2 = _RefusingAllocator(cdr)
+    with pytest.raises(cdr.CdrError) as e:
+        cdr.Batch(allocator=al2)
+    assert e.value.status == -2
+    assert al2.allocs == 1 and al2.frees == 0
