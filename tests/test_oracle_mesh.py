@@ -103,6 +103,8 @@ def test_refine_constrained_both_modes():
     assert cS["bad_tets_unspl"] <= 0.01 * cS["tets"]
     assert cR["bad_tets_unspl"] <= 0.01 * cR["tets"]
     assert max(sS["inserted"], sR["inserted"]) <= 1.15 * min(sS["inserted"], sR["inserted"])
+    # rounds leave no larger a fraction of bad tetrahedra than sequential refinement, within 1.15x
+    assert cR["bad_tets_unspl"] / cR["tets"] <= 1.15 * cS["bad_tets_unspl"] / cS["tets"]
 
 
 def test_mixed_rounds_contract_band_and_fewer_rounds():
