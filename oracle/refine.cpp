@@ -654,6 +654,10 @@ void apply(Mesh& M, const Decision& d, int vp, std::vector<int>* newT, std::vect
 }
 
 // ----------------------------------------------------------- classification
+// Sec. 2 splits encroached subsegments first but does not define encroachment;
+// the standard definition is used: a vertex strictly inside the subsegment's
+// diametral sphere. The vertices tested are the apexes of the tetrahedra
+// around the edge; on a CDT they include every encroaching vertex.
 bool subseg_encroached(const Mesh& M, int g) {
   const Subseg& G = M.G[g];
   auto it = M.edgeT.find(key2(G.a, G.b));
@@ -666,6 +670,9 @@ bool subseg_encroached(const Mesh& M, int g) {
     }
   return false;
 }
+// A subface is encroached by a vertex strictly inside its equatorial sphere
+// (centre and radius of its circumcircle), tested over the apexes of its one
+// or two tetrahedra (same reading as for subsegments).
 bool subface_encroached(const Mesh& M, int s) {
   const Subface& S = M.S[s];
   auto it = M.faceT.find(M.sf_key(s));
@@ -680,12 +687,17 @@ bool subface_encroached(const Mesh& M, int s) {
   }
   return false;
 }
+// Sec. 1: a tetrahedron is bad when circumradius / shortest edge > B; the test
+// compares squares, with the vertices in ascending id order.
 bool tet_bad(const Mesh& M, int t, double B) {
   int s[4];
   sorted_tet(M.T[t], s);
   return tet_is_bad(M.X(s[0]), M.X(s[1]), M.X(s[2]), M.X(s[3]), B);
 }
 
+// The three queues of Sec. 2, each in element-id order: encroached (or
+// flagged) subsegments, encroached (or flagged) subfaces, bad tetrahedra;
+// elements given up as unsplittable are left out.
 void classify(const Mesh& M, double B, std::vector<int>* q) {
   for (int c = 0; c < 3; ++c) q[c].clear();
   for (int g = 0; g < (int)M.G.size(); ++g) {
@@ -704,6 +716,8 @@ void classify(const Mesh& M, double B, std::vector<int>* q) {
   }
 }
 
+// Gives an element up (termination reading: it stays in the mesh, counted
+// among the elements left unsplit).
 static void set_unspl(Mesh& M, int cls, int elem) {
   if (cls == CLS_SUBSEG) M.G[elem].unspl = 1;
   if (cls == CLS_SUBFACE) M.S[elem].unspl = 1;
