@@ -362,3 +362,45 @@ def test_every_round_leaves_a_cdt():
         assert c["sf_not_face"] == 0 and c["ss_not_edge"] == 0 and c["hull_not_subface"] == 0
         assert c["seg_chain_bad"] == 0 and c["facet_area_rel_err"] < 1e-12
     assert classes == {0, 1, 2}
+
+
+def _splitmix_chain(cls, words):
+    """Reading r3's hash, restated: SplitMix64's finaliser chained over 64-bit words,
+    seeded by the golden-ratio constant times (class + 1)."""
+    M64 = (1 << 64) - 1
+    h = (0x9E3779B97F4A7C15 * (cls + 1)) & M64
+    for w in words:
+        z = h ^ int(w)
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        h = z ^ (z >> 31)
+    return h
+
+
+def test_candidates_follow_the_predetermined_priority():
+    """Sec. 2's predetermined priorities (reading r3): a round's candidates come
+    in the order of class << 62 | (h >> 2), h the hash of the element's vertex
+    coordinates in ascending id order, ties broken by the sorted vertex ids."""
+    m, *_ = constrained_mesh(300, 3, 3, seed=24)
+    B = 1.5
+    seen = set()
+    for _ in range(400):
+        snap = m.export()
+        o = m.round(B)
+        if o["cls"] < 0:
+            break
+        if o["cls"] in seen and len(seen) < 3:
+            continue
+        seen.add(o["cls"])
+        rep = m.report()
+        keys = [tuple(int(v) for v in k if v >= 0) for k in rep["keys"]]
+        order = []
+        for k in keys:
+            words = snap["xyz"][list(k)].reshape(-1).view(np.uint64)
+            h = _splitmix_chain(o["cls"], words)
+            order.append(((o["cls"] << 62) | (h >> 2), k))
+        assert order == sorted(order)
+        assert len(keys) == o["ncand"]
+        if seen == {0, 1, 2}:
+            break
+    assert seen == {0, 1, 2}
