@@ -1,0 +1,73 @@
+"""Host-side pieces of bench.py, on the CPU: the clock record taken during the
+timed region (parsed from nvidia-smi's CSV lines), the roofline peak and the
+algorithmic-bytes model of region growth."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+class _Done:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_record_takes_median_max_and_active_reasons():
+    c = bench.ClockSampler(0)
+    c.proc = _Done()
+    c.lines = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1965, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    r = c.stop()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+
+
+def test_clock_record_is_none_without_samples():
+    c = bench.ClockSampler(0)
+    assert c.stop() is None
+    c.proc = _Done()
+    assert c.stop() is None
+
+
+def test_peak_comes_from_the_measured_file_when_present():
+    peak, kind = bench.load_peaks()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            assert (peak, kind) == (float(json.load(f)["hbm_gbs"]), "measured")
+    else:
+        assert (peak, kind) == (6800.0, "fallback")
+
+
+def test_growth_bytes_model():
+    # 56 B per neighbour tested, 52 B per cavity tetrahedron, 36 B per boundary face
+    assert bench.grow_bytes({"tested": 1, "cavity": 0, "boundary": 0}) == 56
+    assert bench.grow_bytes({"tested": 0, "cavity": 1, "boundary": 0}) == 52
+    assert bench.grow_bytes({"tested": 0, "cavity": 0, "boundary": 1}) == 36
+    assert bench.grow_bytes({"tested": 2727545, "cavity": 1958595, "boundary": 816510}) == \
+        283983820  # the largest round's figure in profiles/ncu_traffic.json
+
+
+def test_traffic_record_scales_or_is_withheld():
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        rec = json.load(f)["k_grow1"]
+    t = bench.ncu_traffic("k_grow1", rec["algorithmic_bytes"] / 10)
+    if rec["kernels_sha"] == bench.kernel_hash():
+        # taken on the current kernels: traffic scales with the algorithmic bytes
+        dram = rec["dram_bytes_read"] + rec["dram_bytes_write"]
+        assert abs(t - dram / 10) < 1e-6 * dram
+    else:
+        # the kernels changed since the capture: no traffic figure is reported
+        assert t is None
+    assert bench.ncu_traffic("no_such_kernel", 1.0) is None
