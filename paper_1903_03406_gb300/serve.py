@@ -101,6 +101,7 @@ class Server:
     used_bytes: int = 0
     rounds: int = 0
     oom_deferrals: int = 0
+    cancelled: list = field(default_factory=list)
 
     def submit(self, req: Request):
         n = len(req.mesh["xyz"])
@@ -155,6 +156,27 @@ class Server:
             self.results.append(r)
             done.append(r)
         return done
+
+    def cancel(self, rid):
+        """Withdraw request `rid`. A waiting request leaves the queue. A running
+        one is removed from the batch between rounds (cdr_batch_remove), which
+        frees its slot and its share of the budget for the next admissions; its
+        partial mesh is dropped. Returns False if the request is unknown or has
+        already finished."""
+        for i, (_, r_id, _req) in enumerate(self.waiting):
+            if r_id == rid:
+                self.waiting.pop(i)
+                heapq.heapify(self.waiting)
+                self.cancelled.append(rid)
+                return True
+        for slot, (req, _t) in list(self.running.items()):
+            if req.rid == rid:
+                self.batch.remove(slot)
+                self.used_bytes -= req.est_bytes
+                del self.running[slot]
+                self.cancelled.append(rid)
+                return True
+        return False
 
     def step(self):
         """One scheduling step: admit, one round, retire. Returns the number of

@@ -172,3 +172,23 @@ def test_other_admission_errors_are_raised():
     srv.submit(serve.Request(0, arrival=0.0, B=1.6, mesh=_mesh(300)))
     with pytest.raises(ValueError):
         srv.admit(1.0)
+
+
+def test_cancel_frees_the_slot_and_budget():
+    b = FakeBatch()
+    per = serve.estimate_bytes(1000, 1.6)
+    srv = serve.Server(b, budget_bytes=int(2.5 * per), clock=Clock())
+    for i in range(4):
+        srv.submit(serve.Request(i, arrival=0.0, B=1.6, mesh=_mesh(1000)))
+    srv.step()                       # requests 0 and 1 run, 2 and 3 wait
+    assert sorted(r.rid for r, _ in srv.running.values()) == [0, 1]
+    slot1 = next(k for k, (r, _) in srv.running.items() if r.rid == 1)
+    assert srv.cancel(1)             # mid-flight: removed from the batch
+    assert ("remove", slot1) in b.log and srv.used_bytes == per
+    assert srv.cancel(3)             # still waiting: leaves the queue
+    assert not srv.cancel(3) and not srv.cancel(99)
+    srv.step()                       # request 2 takes the freed slot
+    assert any(ev == ("add", slot1, 1000) for ev in b.log[-3:])
+    res = srv.run()
+    assert sorted(r.rid for r in res) == [0, 2]
+    assert srv.cancelled == [1, 3] and srv.used_bytes == 0 and srv.idle()
