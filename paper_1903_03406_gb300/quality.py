@@ -15,6 +15,8 @@ import numpy as np
 # (k, l): the edge's dihedral angle is the one between faces opposite k and l
 EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
 _OFF = tuple(tuple(v for v in range(4) if v not in e) for e in EDGES)
+# bin edges of the radius-edge histogram (0.6 to 3.0 by 0.1)
+RHO_EDGES = np.round(np.arange(0.6, 3.0001, 0.1), 10)
 
 
 def _corners(xyz, tets):
@@ -86,6 +88,12 @@ def report(xyz, tets, B=None, bin_deg=10.0):
         rho = radius_edge(xyz, tets)
         out["radius_edge_max"] = float(rho.max()) if len(rho) else None
         out["frac_above_B"] = float(np.mean(rho > B)) if len(rho) else 0.0
+        # the ratio's distribution: bins of 0.1 from sqrt(6)/4 (the regular
+        # tetrahedron, the smallest possible value) rounded down to 0.6, the last
+        # bin open-ended
+        h, _ = np.histogram(np.minimum(rho, RHO_EDGES[-1] - 1e-9), bins=RHO_EDGES)
+        out["radius_edge_bins"] = [float(x) for x in RHO_EDGES]
+        out["radius_edge_hist"] = [float(x) for x in h / max(len(rho), 1)]
     return out
 
 

@@ -121,3 +121,15 @@ def test_rounds_and_sequential_refinement_give_the_same_quality():
     d_refined = quality.hist_distance(q0["dihedral_hist"], qS["dihedral_hist"])
     assert d_orders < 0.02
     assert d_refined > 5 * d_orders
+
+
+def test_radius_edge_histogram():
+    # the regular tetrahedron has the smallest ratio, sqrt(6)/4 = 0.612: first bin;
+    # a flat-ish one with a huge ratio lands in the last, open-ended bin
+    xyz = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1],
+                    [0, 0, 0], [1, 0, 0], [0, 1, 0], [0.3, 0.3, 1e-3]], dtype=float)
+    r = quality.report(xyz, [[0, 1, 2, 3], [4, 5, 6, 7]], B=2.0)
+    h = r["radius_edge_hist"]
+    assert len(h) == len(r["radius_edge_bins"]) - 1
+    assert h[0] == 0.5 and h[-1] == 0.5 and sum(h) == 1.0
+    assert r["frac_above_B"] == 0.5
