@@ -341,13 +341,17 @@ int cdr_eval_predicates(int32_t kind, const double* in, int32_t n, int32_t* sign
  *   - n > CDR_EVAL_NOALLOC_MAX_ITEMS returns CDR_ERR_TOO_LARGE and does nothing;
  *   - no call allocates or frees device memory (cudaMalloc, cudaFree or any
  *     allocating library routine);
- *   - the first call on a device, with that device current, looks the array
- *     up (cudaGetSymbolAddress) and caches its address. Make that first call
- *     before any stream capture;
- *   - every call on a device shares the array. Calls whose device work
- *     overlaps (other streams, other host threads) race on it and their results
- *     are undefined: serialise them. Each call synchronises `stream` before it
- *     returns, so calls from one host thread never overlap.
+ *   - every call looks the array up on the current device
+ *     (cudaGetSymbolAddress); no address is cached, so a call after
+ *     cudaDeviceReset finds the array where the reloaded library put it;
+ *   - the call copies through pageable host memory and synchronises `stream`,
+ *     so it cannot be made on a stream that is being captured into a graph;
+ *   - every call on a device shares the array, and the exact-arithmetic
+ *     overflow flag it reads back (one word in the library's image). Calls
+ *     whose device work overlaps (other streams, other host threads) race on
+ *     both, so their results and their CDR_ERR_INTERNAL status are undefined:
+ *     serialise them. Each call synchronises `stream` before it returns, so
+ *     calls from one host thread never overlap.
  * The array keeps the last call's contents; each call clears what must start
  * at zero (the exact-arithmetic overflow flag) and writes every output slot
  * it reads back. */

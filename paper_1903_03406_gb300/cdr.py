@@ -468,8 +468,9 @@ def eval_predicates_noalloc(kind, items, stream=None):
     processes whose device memory is held by a caching allocator (cudaMalloc can
     fail there). The device copies live in a fixed array of the library, so at
     most EVAL_NOALLOC_MAX_ITEMS items go in one call, and calls whose device work
-    overlaps (other streams or threads) race. The first call on a device looks
-    that array up; make it before any stream capture. Host buffers only (numpy).
+    overlaps (other streams or threads) race. Each call looks that array up on
+    the current device and synchronises its stream, so it cannot run on a
+    stream under graph capture. Host buffers only (numpy).
     """
     items = np.ascontiguousarray(items, dtype=np.float64).reshape(-1, 16)
     n = len(items)

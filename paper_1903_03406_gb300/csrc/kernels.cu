@@ -2510,29 +2510,9 @@ void launch_report_cav(const DevMesh& m, const DevRound& r, const int* offs, int
 // against an exact reference). Each item holds 16 doubles of input.
 __global__ void k_eval_pred(int kind, const double* in, int n, int* sign, double* outp) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double* q = in + 16 * (size_t)i;
-    D3 a{q[0], q[1], q[2]}, b{q[3], q[4], q[5]}, c{q[6], q[7], q[8]}, d{q[9], q[10], q[11]},
-        e{q[12], q[13], q[14]};
-    int sg = 0;
-    D3 o{0, 0, 0};
-    switch (kind) {
-      case 0: sg = orient3d(a, b, c, d); break;
-      case 1: sg = insphere(a, b, c, d, e); break;
-      case 2: sg = diametral(a, b, c); break;
-      case 3: sg = equatorial(a, b, c, d); break;
-      case 4: {
-        D3 off;
-        sg = tet_circumcenter_fixed(a, b, c, d, o, off) ? 1 : 0;
-        break;
-      }
-      case 5: sg = tri_circumcenter_fixed(a, b, c, o) ? 1 : 0; break;
-      case 6: o = midpoint_fixed(a, b); sg = 1; break;
-      case 7: sg = tet_bad_fixed(a, b, c, d, q[12]) ? 1 : 0; break;
-      case 8: sg = orient3d_exact(a, b, c, d); break;
-      case 9: sg = insphere_exact(a, b, c, d, e); break;
-      case 10: sg = equatorial_exact(a, b, c, d); break;
-      case 11: sg = diametral_exact(a, b, c); break;
-    }
+    int sg;
+    D3 o;
+    eval_item(kind, in + 16 * (size_t)i, &sg, &o);
     sign[i] = sg;
     if (outp) {
       outp[3 * (size_t)i] = o.x;

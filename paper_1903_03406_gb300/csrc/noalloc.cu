@@ -17,12 +17,13 @@
 // Host code never uses the name g_eval_scratch as a pointer. On the host that
 // name stands for a host-side shadow, not device memory: a kernel handed it
 // would fault, or silently touch the wrong memory where the GPU can reach host
-// memory. The device address comes from cudaGetSymbolAddress, looked up once per
-// device with that device current, on the first call made there.
+// memory. The device address comes from cudaGetSymbolAddress, looked up on every
+// call with the call's device current. Nothing is cached, so a call made after
+// the caller reset the device (cudaDeviceReset, which reloads this module and
+// may move the array) still gets the array's current address.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "../../include/cdr.h"
 
@@ -46,33 +47,14 @@ static_assert(kOffPoints % 256 == 0 && kOffSigns % 256 == 0, "scratch parts must
 static __device__ __align__(256) unsigned char g_eval_scratch[kScratchBytes];
 
 // The batch kernel of cdr_eval_predicates, reading its items from and writing
-// its results to the scratch array. Every slot i < n is written, so what an
-// earlier call left in the array is never read.
+// its results to the scratch array; both run each item through eval_item.
+// Every slot i < n is written, so what an earlier call left in the array is
+// never read.
 __global__ void k_eval_pred_noalloc(int kind, const double* in, int n, int* sign, double* outp) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double* q = in + 16 * (size_t)i;
-    D3 a{q[0], q[1], q[2]}, b{q[3], q[4], q[5]}, c{q[6], q[7], q[8]}, d{q[9], q[10], q[11]},
-        e{q[12], q[13], q[14]};
-    int sg = 0;
-    D3 o{0, 0, 0};
-    switch (kind) {
-      case 0: sg = orient3d(a, b, c, d); break;
-      case 1: sg = insphere(a, b, c, d, e); break;
-      case 2: sg = diametral(a, b, c); break;
-      case 3: sg = equatorial(a, b, c, d); break;
-      case 4: {
-        D3 off;
-        sg = tet_circumcenter_fixed(a, b, c, d, o, off) ? 1 : 0;
-        break;
-      }
-      case 5: sg = tri_circumcenter_fixed(a, b, c, o) ? 1 : 0; break;
-      case 6: o = midpoint_fixed(a, b); sg = 1; break;
-      case 7: sg = tet_bad_fixed(a, b, c, d, q[12]) ? 1 : 0; break;
-      case 8: sg = orient3d_exact(a, b, c, d); break;
-      case 9: sg = insphere_exact(a, b, c, d, e); break;
-      case 10: sg = equatorial_exact(a, b, c, d); break;
-      case 11: sg = diametral_exact(a, b, c); break;
-    }
+    int sg;
+    D3 o;
+    eval_item(kind, in + 16 * (size_t)i, &sg, &o);
     sign[i] = sg;
     outp[3 * (size_t)i] = o.x;
     outp[3 * (size_t)i + 1] = o.y;
@@ -81,36 +63,22 @@ __global__ void k_eval_pred_noalloc(int kind, const double* in, int n, int* sign
 }
 
 // Device addresses of this file's scratch array and of its copy of the
-// exact-arithmetic overflow flag, per device (null until first use there).
-constexpr int kMaxDevices = 64;
+// exact-arithmetic overflow flag on the current device, looked up afresh.
 struct DevScratch {
   unsigned char* base = nullptr;
   int* overflow = nullptr;
 };
-std::mutex g_setup_mutex;
-DevScratch g_dev[kMaxDevices];
 
 int scratch_for_current_device(DevScratch* out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  unsigned char* base = nullptr;
+  int* flag = nullptr;
+  if (cudaGetSymbolAddress((void**)&base, g_eval_scratch) != cudaSuccess ||
+      cudaGetSymbolAddress((void**)&flag, g_exact_overflow) != cudaSuccess || !base || !flag) {
     cudaGetLastError();
     return CDR_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return CDR_ERR_INVALID_INPUT;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  DevScratch& d = g_dev[dev];
-  if (!d.base) {
-    unsigned char* base = nullptr;
-    int* flag = nullptr;
-    if (cudaGetSymbolAddress((void**)&base, g_eval_scratch) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&flag, g_exact_overflow) != cudaSuccess || !base || !flag) {
-      cudaGetLastError();
-      return CDR_ERR_CUDA;
-    }
-    d.overflow = flag;
-    d.base = base;
-  }
-  *out = d;
+  out->base = base;
+  out->overflow = flag;
   return CDR_OK;
 }
 

@@ -679,6 +679,37 @@ __device__ __forceinline__ bool tet_bad_fixed(D3 a, D3 b, D3 c, D3 d, double B) 
   return divr(r2, l2) > mulr(B, B);
 }
 
+// One item of the predicate batch probe: q holds the points a, b, c, d, e as
+// (x, y, z) in doubles 0..14 (for kind 7 the bound B sits in double 12). Writes
+// the sign or flag to *sg and the point of kinds 4..6 to *o (zero otherwise).
+// Both batch entry points run their items through this one function.
+__device__ __forceinline__ void eval_item(int kind, const double* q, int* sg, D3* o) {
+  D3 a{q[0], q[1], q[2]}, b{q[3], q[4], q[5]}, c{q[6], q[7], q[8]}, d{q[9], q[10], q[11]},
+      e{q[12], q[13], q[14]};
+  int s = 0;
+  D3 r{0, 0, 0};
+  switch (kind) {
+    case 0: s = orient3d(a, b, c, d); break;
+    case 1: s = insphere(a, b, c, d, e); break;
+    case 2: s = diametral(a, b, c); break;
+    case 3: s = equatorial(a, b, c, d); break;
+    case 4: {
+      D3 off;
+      s = tet_circumcenter_fixed(a, b, c, d, r, off) ? 1 : 0;
+      break;
+    }
+    case 5: s = tri_circumcenter_fixed(a, b, c, r) ? 1 : 0; break;
+    case 6: r = midpoint_fixed(a, b); s = 1; break;
+    case 7: s = tet_bad_fixed(a, b, c, d, q[12]) ? 1 : 0; break;
+    case 8: s = orient3d_exact(a, b, c, d); break;
+    case 9: s = insphere_exact(a, b, c, d, e); break;
+    case 10: s = equatorial_exact(a, b, c, d); break;
+    case 11: s = diametral_exact(a, b, c); break;
+  }
+  *sg = s;
+  *o = r;
+}
+
 // candidate priority: SplitMix64's output function chained over sorted ids
 CDR_HD uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;

@@ -83,3 +83,28 @@ def test_noalloc_full_capacity_and_limit(cdr):
     # an empty batch is a no-op
     s0, p0 = cdr.eval_predicates_noalloc("orient", np.zeros((0, 16)))
     assert s0.shape == (0,) and p0.shape == (0, 3)
+
+
+def test_noalloc_neither_allocates_nor_waits_for_other_streams(cdr):
+    """What the entry point is for: while another stream is busy, a call on a
+    stream of its own returns before that work ends (a cudaFree inside it would
+    wait for the whole device), and the device's free memory does not move."""
+    import torch
+    rng = np.random.default_rng(2026)
+    items = _batch(rng, 512)
+    ref, _ = cdr.eval_predicates("orient", items)
+    cdr.eval_predicates_noalloc("orient", items)  # loads the module on a fresh process
+    torch.cuda.synchronize()
+    busy, mine = torch.cuda.Stream(), torch.cuda.Stream()
+    done = torch.cuda.Event()
+    free_before = torch.cuda.mem_get_info()[0]
+    with torch.cuda.stream(busy):
+        torch.cuda._sleep(int(4e8))  # one thread spinning ~0.2 s at 2 GHz
+        done.record(busy)
+    sg, _ = cdr.eval_predicates_noalloc("orient", items, stream=mine)
+    overlapped = not done.query()
+    free_after = torch.cuda.mem_get_info()[0]
+    torch.cuda.synchronize()
+    assert overlapped, "the call waited for work on another stream"
+    assert free_after == free_before
+    assert np.array_equal(sg, ref)
