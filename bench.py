@@ -4,27 +4,31 @@ One step = the whole refinement (every round, every kernel of the hot path) of
 one instance of the workload, from its initial constrained Delaunay mesh (kept
 on the device and restored at the start of the step) to the end.
 
-Workload (default): 100,000 points uniform in [0,1000]^3 plus the 8 box corners,
-1,000 segments and 1,000 triangles inside the box (constraints chosen among the
-Delaunay edges and faces; seed 1), B = 1.4. The initial Delaunay mesh is built
-on the GPU by the library's point-insertion rounds (untimed set-up).
+Workload (default, the largest single-GPU configuration): 500,000 points drawn
+from a mixture of 3 isotropic Gaussians (sigma 50) in [0,1000]^3 plus the 8 box
+corners, 5,000 segments and 5,000 triangles inside the box (constraints chosen
+among the Delaunay edges and faces; seed 2), B = 1.4. The initial Delaunay mesh
+is built on the GPU by the library's point-insertion rounds (untimed set-up).
+`--workload uniform100k` runs the 100,000-point uniform configuration instead.
+
+The line also carries:
+* quality_band: the final Steiner count and fraction of bad tetrahedra against
+  the oracle's sequential refinement of the same input run to the end (stored
+  by tests/golden/make_oracle_counts.py), with the ratios;
+* batched: a batch of unit-cube PLCs (1k-50k interior points, log-uniform; 1%
+  segments and 1% triangles; B = 1.6) refined one after another (create,
+  refine, export each) and as one batch: meshes/s of both;
+* served: a Poisson stream of requests (unit-cube PLCs with 2k-200k points, B
+  drawn from {1.4, 1.6, 2.0}) served by continuous batching under a 120 GB
+  budget: meshes/s of a closed-loop run (all requests at once), then p50 / p99
+  latency (arrival to export) and meshes/s of a Poisson stream at 0.8x that
+  rate, next to the same requests refined one after another.
+Their instance and request counts are bounded samples of the 256-instance and
+2,000-request streams (--batched / --served set them; 0 leaves the part out).
+`--workload batched64` / `served40` print those parts as lines of their own.
 
 --impl reference times the CPU oracle (sequential refinement) on the same
 workload, a bounded number of insertions per step, on the host cores.
-
-Two more workloads print their own line:
-* --workload batched64: 64 independent unit-cube PLCs (1k-50k interior points,
-  log-uniform; 1% segments and 1% triangles; B = 1.6) refined one after another
-  (create, refine, export each) and as one batch (add all, refine, export all):
-  meshes/s of both;
-* --workload served40: a Poisson stream of 40 requests (unit-cube PLCs with
-  2k-200k points, B drawn from {1.4, 1.6, 2.0}) served by continuous batching
-  under a 120 GB budget: meshes/s of a closed-loop run (all requests at once),
-  then p50 / p99 latency (arrival to export) and meshes/s of a Poisson stream
-  at 0.8x that rate, next to the same requests refined one after another.
-Their instance and request counts are bounded samples of the 256-instance and
-2,000-request streams, so that each run stays near a minute; the initial
-Delaunay meshes are built on the GPU before the timed region.
 
 Prints one JSON line (rank 0).
 """
@@ -60,6 +64,35 @@ def log(*a):
 
 T0 = time.perf_counter()
 MAX_ROUNDS = 200000
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_counts.json")
+
+
+def oracle_counts(name):
+    """The oracle's sequential refinement of `name` run to the end (stored)."""
+    try:
+        with open(GOLDEN) as f:
+            return json.load(f).get(name)
+    except (OSError, ValueError):
+        return None
+
+
+def quality_band(name, steiner, bad, tets):
+    """Steiner count and bad-tetrahedron fraction against the stored oracle run."""
+    o = oracle_counts(name)
+    if not o:
+        return None
+    frac = bad / tets if tets else 0.0
+    rs = steiner / o["steiner"] if o["steiner"] else None
+    rb = frac / o["bad_frac"] if o["bad_frac"] else (1.0 if frac == 0 else None)
+    return {"reference": "oracle sequential refinement to the end (mode S)",
+            "oracle_steiner": o["steiner"], "oracle_bad_left": o["bad_left"],
+            "oracle_tets": o["tets"], "oracle_bad_frac": o["bad_frac"],
+            "steiner": int(steiner), "bad_left": int(bad), "tets": int(tets),
+            "bad_frac": frac, "steiner_ratio": rs, "bad_frac_ratio": rb,
+            "band": 1.15,
+            "within_band": bool(rs is not None and rb is not None and rs <= 1.15 and rb <= 1.15)}
 
 
 def load_peaks():
@@ -317,6 +350,8 @@ def gpu_arm(args, rank, world):
                                                            if v > 0}},
         "gpu_launches": launches,
         "quality": qual,
+        "quality_band": quality_band(args.workload, last["steiner_inserted"],
+                                     last["n_bad_left"], last["n_tets"]),
         "clocks": clk,
     }
     return line
@@ -327,14 +362,20 @@ def _margs(m):
     return (m["xyz"], m["tets"], m["segs"], m["seg_id"], m["tris"], m["facet_id"], m["nfacets"])
 
 
-def multi_arm(args, rank, world):
+def multi_arm(args, rank, world, name=None, count=None, cpu=True):
+    """The batched or served workload `name` (default: args.workload), with
+    `count` instances / requests (default: the workload's own)."""
     import torch
     from paper_1903_03406_gb300 import autotune, cdr, replicas, serve, workloads
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cdr.lib()
     stream = torch.cuda.current_stream()
-    spec = workloads.MULTI[args.workload]
+    name = name or args.workload
+    spec = dict(workloads.MULTI[name])
+    full = workloads.FULL_COUNT[name]
+    if count:
+        spec["count"] = int(count)
     tuning = autotune.load()  # the tuner's stored launch setting, if any
     t0 = time.perf_counter()
     insts = workloads.multi_instances(spec, rank, cdr, stream)
@@ -342,7 +383,7 @@ def multi_arm(args, rank, world):
                                                      sum(x["n"] for x in insts)))
     al = cdr.TorchAllocator()
     clocks = ClockSampler(dev)
-    if args.workload.startswith("batched"):
+    if name.startswith("batched"):
         # warm-up: one small batch and one small instance alone
         for _ in range(max(1, args.warmup)):
             b = cdr.Batch(allocator=al, stream=stream)
@@ -381,7 +422,7 @@ def multi_arm(args, rank, world):
             return None
         n_all = len(insts) * world
         cpu = None
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and cpu and not args.no_cpu_baseline:
             log("cpu baseline: the oracle on all host cores")
             cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else \
                 (os.cpu_count() or 1)
@@ -394,13 +435,13 @@ def multi_arm(args, rank, world):
             "same_counts": serial_ins == batch_ins, "n_gpus": world, "steps": 1,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "instances": len(insts),
+            "config": {"workload": name, "instances": len(insts),
                        "points": [x["n"] for x in insts][:8] + ["..."],
                        "points_total": sum(x["n"] for x in insts), "B": spec["B"],
                        "constraints": "1% segments + 1% triangles",
                        "timed": "create/add + refine + export of every instance",
                        "tuning": tuning or "defaults",
-                       "sample": "64 of config 4's 256 instances"},
+                       "sample": "%d of the %d-instance batched workload" % (len(insts), full)},
             "clocks": clk,
             "cpu_baseline": cpu,
         }
@@ -461,11 +502,11 @@ def multi_arm(args, rank, world):
         "rounds": srv.rounds, "n_gpus": world, "steps": 1, "warmup": 1,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "requests": len(reqs),
+        "config": {"workload": name, "requests": len(reqs),
                    "points_total": sum(x["n"] for x in insts), "B": spec["B"],
                    "hbm_budget_gb": budget / 1e9, "arrival": "Poisson, 0.8x closed-loop",
                    "tuning": tuning or "defaults",
-                   "sample": "40 of config 5's 2,000 requests"},
+                   "sample": "%d of the %d-request served stream" % (len(reqs), full)},
         "clocks": clk,
     }
 
@@ -564,6 +605,11 @@ def reference_arm(args, rank, world):
             ins += i
             t += dt
     v = ins / t
+    o = oracle_counts(args.workload)
+    cover = ""
+    if o and o.get("steiner"):
+        cover = (", each step continuing the refinement from where the last stopped "
+                 "(%d of the %d insertions made to the end were timed)" % (ins, o["steiner"]))
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
@@ -571,10 +617,89 @@ def reference_arm(args, rank, world):
         "data": "synthetic",
         "config": workload_config(args, world),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "sequential refinement, %g s of insertions per step" %
-                                   args.ref_seconds},
+                         "sample": "sequential refinement, %g s of insertions per step%s" %
+                                   (args.ref_seconds, cover)},
+        "oracle_to_the_end": o,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+def profile_run(args):
+    """One refinement of the plain workload for a profiler to capture, round by
+    round: a first pass finds the round with the most candidates, then the same
+    refinement is replayed from a checkpoint inside an NVTX range named
+    "replay", with that round inside a range named "largest" (for example
+    ncu --nvtx --nvtx-include "replay/largest/")."""
+    import torch
+    from paper_1903_03406_gb300 import autotune, cdr
+    torch.cuda.set_device(0)
+    cdr.lib()
+    stream = torch.cuda.current_stream()
+    w = WORKLOADS[args.workload]
+    pts, ex, plc = make_workload(args.workload, 0, cdr, stream)
+    h = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
+                          plc["facet_id"], plc["nfacets"], mixed_rounds=args.mixed,
+                          allocator=cdr.TorchAllocator(), stream=stream)
+    autotune.apply(h, autotune.load())
+    h.checkpoint()
+    cands = []
+    while len(cands) < MAX_ROUNDS:
+        r = h.round(w["B"])
+        if r["cls"] < 0:
+            break
+        cands.append(r["candidates"])
+    big = max(range(len(cands)), key=lambda k: cands[k])
+    h.restore()
+    h.profile(enable=0, reset=True)
+    ins = 0
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("replay")  # the whole second refinement
+    for k in range(len(cands)):
+        if k == big:
+            torch.cuda.nvtx.range_push("largest")
+        ins += h.round(w["B"])["steiner_inserted"]
+        if k == big:
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_run": args.workload, "rounds": len(cands), "steiner": ins,
+                      "largest_round": big, "largest_candidates": cands[big],
+                      "counters": h.profile()["counters"]}), flush=True)
+    h.close()
+
+
+def _cpu_baseline_job(name, seconds):
+    """The plain workload's CPU baseline, in a spawned process: the oracle's
+    sequential refinement of the same input for about `seconds`; its initial
+    Delaunay mesh is built untimed."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    t0 = time.perf_counter()
+    om, _, _ = oracle_workload(name)
+    setup = time.perf_counter() - t0
+    ins, t = cpu_sample(om, WORKLOADS[name]["B"], seconds)
+    return ins, t, setup
+
+
+def cpu_baseline_line(name, ins, t):
+    o = oracle_counts(name)
+    cover = ""
+    if o and o.get("steiner"):
+        cover = ("; %d of the %d insertions it makes to the end (%.1f%%), the first part of "
+                 "the refinement" % (ins, o["steiner"], 100.0 * ins / o["steiner"]))
+    return {"value": ins / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "sequential refinement of the same workload for %.1f s (%d insertions, "
+                      "initial Delaunay excluded%s)" % (t, ins, cover)}
+
+
+def _nested(line):
+    """A batched / served line folded into the main line."""
+    if line is None:
+        return None
+    drop = {"n_gpus", "steps", "warmup", "higher_is_better", "scaling", "vs_baseline", "dtype",
+            "data"}
+    return {k: v for k, v in line.items() if k not in drop}
 
 
 def main():
@@ -584,15 +709,25 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     from paper_1903_03406_gb300 import workloads
-    ap.add_argument("--workload", default="uniform100k",
+    ap.add_argument("--workload", default="clustered500k",
                     choices=sorted(WORKLOADS) + sorted(workloads.MULTI))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", type=int, default=128,
+                    help="instances of the batched part of the line (0: leave it out)")
+    ap.add_argument("--served", type=int, default=40,
+                    help="requests of the served part of the line (0: leave it out)")
     ap.add_argument("--mixed", type=int, default=0, choices=[0, 1, 2],
                     help="round kind: 0 one class per round, 1 every class, "
                          "2 subsegments and subfaces together")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="for profilers: build the workload and refine it once, untimed "
+                         "(no warm-up, no other part); prints its counts, not a bench line")
     args = ap.parse_args()
+    if args.profile_run:
+        profile_run(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -603,12 +738,13 @@ def main():
         if line is not None:
             print(json.dumps(line), flush=True)
         return
+    plain = args.workload not in workloads.MULTI
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    if args.workload in workloads.MULTI:
+    if not plain:
         line = multi_arm(args, rank, world)
         if line is not None:
             print(json.dumps(line), flush=True)
@@ -618,15 +754,31 @@ def main():
             dist.destroy_process_group()
         return
     line = gpu_arm(args, rank, world)
+    batched = served = None
+    if args.batched > 0:
+        log("batched part: %d instances" % args.batched)
+        batched = multi_arm(args, rank, world, name="batched64", count=args.batched, cpu=False)
+    if args.served > 0:
+        log("served part: %d requests" % args.served)
+        served = multi_arm(args, rank, world, name="served40", count=args.served)
     if line is not None and world == 1 and not args.no_cpu_baseline:
-        log("cpu baseline: building the oracle's Delaunay mesh")
-        om, _, _ = oracle_workload(args.workload)
-        ins, t = cpu_sample(om, WORKLOADS[args.workload]["B"], args.cpu_seconds)
-        line["cpu_baseline"] = {
-            "value": ins / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "sequential refinement of the same workload for %.1f s "
-                      "(%d insertions, initial Delaunay excluded)" % (t, ins)}
+        # after every GPU-timed region, so that the host stays quiet while they run
+        log("cpu baseline: the oracle's sequential refinement (one core)")
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(1) as pool:
+            ins, t, setup = pool.apply(_cpu_baseline_job, (args.workload, args.cpu_seconds))
+        line["cpu_baseline"] = cpu_baseline_line(args.workload, ins, t)
+    if batched is not None and world == 1 and not args.no_cpu_baseline:
+        log("batched part: the oracle on all host cores")
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else \
+            (os.cpu_count() or 1)
+        spec = dict(workloads.MULTI["batched64"], count=args.batched)
+        batched["cpu_baseline"] = oracle_all_cores(workloads.multi_specs(spec, rank), cores)
     if line is not None:
+        if batched is not None:
+            line["batched"] = _nested(batched)
+        if served is not None:
+            line["served"] = _nested(served)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -280,7 +280,8 @@ const char* cdr_status_string(int status);
  *            rounds with separately launched growth kernels), 9 new
  *            tetrahedra written, 10 refusals flagging a new candidate, 11 regions
  *            stopped on a higher-priority start, 12 tetrahedra retired by
- *            insertion, 15 kernels of this library launched (library
+ *            insertion, 13 compactions of the tetrahedron arrays,
+ *            15 kernels of this library launched (library
  *            primitives such as sorts and scans excluded), 16..18 as 6..8 in
  *            rounds run as one kernel
  * Any output pointer may be NULL. */
@@ -294,11 +295,24 @@ int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_
  *   grow1_blocks_per_sm  at most this many blocks per SM in the region-growth
  *                        grid (1..32); 0: 8
  *   tier2_warps          warps (each with a global workspace) for regions that
- *                        outgrow tier 1 (1..4864); 0: 608 */
+ *                        outgrow tier 1 (1..4864); 0: 608
+ *   tier1_cavity         cavity tetrahedra a tier-1 (shared-memory) workspace
+ *                        holds before the region is re-grown in tier 2 (1..64);
+ *                        0: 64
+ *   tier1_boundary       cavity boundary faces a tier-1 workspace holds
+ *                        (1..160); 0: 160
+ *   compact_min_tets     tetrahedron slots below which the dead ones are never
+ *                        compacted away; 0: 524288
+ *   compact_dead_pct     the tetrahedron arrays are compacted once at least this
+ *                        percentage of their slots is dead (1..100); 0: 50 */
 typedef struct {
   int32_t fused_max;
   int32_t grow1_blocks_per_sm;
   int32_t tier2_warps;
+  int32_t tier1_cavity;
+  int32_t tier1_boundary;
+  int32_t compact_min_tets;
+  int32_t compact_dead_pct;
 } cdr_tuning;
 int cdr_set_tuning(cdr_handle* h, const cdr_tuning* t);
 

@@ -28,7 +28,7 @@ OUT_OK, OUT_REJECT, OUT_UNSPL, OUT_BLASTED = 0, 1, 2, 4
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so in place (g++, C++17, -O2, no FP contraction)."""
+    """Compile liboracle.so in place (g++, C++17, -O3, no FP contraction)."""
     srcs = [os.path.join(_HERE, s) for s in _SOURCES]
     deps = srcs + [os.path.join(_HERE, h) for h in _HEADERS]
     if not force and os.path.exists(_LIB_PATH):
@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(d) <= t for d in deps):
             return _LIB_PATH
     tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
-    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+    cmd = ["g++", "-std=c++17", "-O3", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
            "-shared", "-o", tmp] + srcs
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -99,6 +99,10 @@ def lib():
             L.orc_report_sizes.restype = None
             L.orc_report.argtypes = [P, ip, dp, ip, ip, ip, ip, ip, ip, ip, ip, ip, ip, ip, ip]
             L.orc_report.restype = None
+            L.orc_report_claim_sizes.argtypes = [P, ip]
+            L.orc_report_claim_sizes.restype = None
+            L.orc_report_claims.argtypes = [P, ip, ip, ip, ip]
+            L.orc_report_claims.restype = None
             L.orc_classify.argtypes = [P, ctypes.c_double, ip]
             L.orc_classify.restype = None
             L.orc_check.argtypes = [P, ctypes.c_double, dp]
@@ -287,7 +291,15 @@ class Mesh:
         flg = np.zeros(max(int(sz[5]), 1), dtype=np.int32)
         L.orc_report(self.h, _i(keys), _d(pts), _i(outcome), _i(reason), _i(surv), _i(ncav),
                      _i(nbnd), _i(nfcav), _i(cav), _i(fcav), _i(nfs), _i(nfg), _i(fls), _i(flg))
-        return dict(cls=int(sz[0]), keys=keys, pts=pts, outcome=outcome, reason=reason,
+        cs = np.zeros(2, dtype=np.int32)
+        L.orc_report_claim_sizes(self.h, _i(cs))
+        nst, nsh = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32)
+        st = np.zeros(max(4 * int(cs[0]), 1), dtype=np.int32)
+        sh = np.zeros(max(4 * int(cs[1]), 1), dtype=np.int32)
+        L.orc_report_claims(self.h, _i(nst), _i(st), _i(nsh), _i(sh))
+        return dict(nstart=nst, starts=st[: 4 * cs[0]].reshape(-1, 4), nshell=nsh,
+                    shell=sh[: 4 * cs[1]].reshape(-1, 4),
+                    cls=int(sz[0]), keys=keys, pts=pts, outcome=outcome, reason=reason,
                     surv=surv, ncav=ncav, nbnd=nbnd, nfcav=nfcav,
                     cav=cav[: sz[2]].reshape(-1, 4), fcav=fcav[: sz[3]].reshape(-1, 3),
                     nflagS=nfs, nflagG=nfg, flagS=fls[: sz[4]].reshape(-1, 3),

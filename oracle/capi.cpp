@@ -93,10 +93,30 @@ std::map<int, double> facet_areas(const Mesh& M) {
 
 namespace orc {
 void RoundReport::record(const Mesh& M, int c, const std::vector<Cand>& cands,
-                         const std::vector<Decision>& dec, const std::vector<uint8_t>& sv) {
+                         const std::vector<Decision>& dec, const std::vector<uint8_t>& sv,
+                         const std::vector<std::vector<int>>& claimed) {
   cls = c;
+  auto put_tets = [&](const std::vector<int>& ids, std::vector<int>& cnt, std::vector<int>& out) {
+    std::vector<std::array<int, 4>> ts;
+    for (int t : ids) {
+      std::array<int, 4> a = M.T[t];
+      std::sort(a.begin(), a.end());
+      ts.push_back(a);
+    }
+    std::sort(ts.begin(), ts.end());
+    ts.erase(std::unique(ts.begin(), ts.end()), ts.end());
+    cnt.push_back((int)ts.size());
+    for (auto& a : ts) out.insert(out.end(), a.begin(), a.end());
+  };
   for (size_t i = 0; i < cands.size(); ++i) {
     const Decision& d = dec[i];
+    put_tets(claimed[i], nstart, starts);
+    std::vector<int> sh;
+    for (auto& b : d.bnd) {
+      int nb = M.nbr(b.first, b.second);
+      if (nb >= 0) sh.push_back(nb);
+    }
+    put_tets(sh, nshell, shell);
     for (int k = 0; k < 4; ++k) keys.push_back(k < cands[i].nkey ? cands[i].key[k] : -1);
     for (int k = 0; k < 3; ++k) pts.push_back(d.p[k]);
     outcome.push_back(d.outcome);
@@ -435,6 +455,21 @@ void orc_report(void* hp, int* keys, double* pts, int* outcome, int* reason, int
   std::copy(r.nflagG.begin(), r.nflagG.end(), nflagG);
   std::copy(r.flagS.begin(), r.flagS.end(), flagS);
   std::copy(r.flagG.begin(), r.flagG.end(), flagG);
+}
+
+// Sizes of the start-claim / shell part of the last round's report:
+// out[0] start tuples, out[1] shell tuples (4 ints each).
+void orc_report_claim_sizes(void* hp, int* out) {
+  RoundReport& r = ((Handle*)hp)->rep;
+  out[0] = (int)r.starts.size() / 4;
+  out[1] = (int)r.shell.size() / 4;
+}
+void orc_report_claims(void* hp, int* nstart, int* starts, int* nshell, int* shell) {
+  RoundReport& r = ((Handle*)hp)->rep;
+  std::copy(r.nstart.begin(), r.nstart.end(), nstart);
+  std::copy(r.starts.begin(), r.starts.end(), starts);
+  std::copy(r.nshell.begin(), r.nshell.end(), nshell);
+  std::copy(r.shell.begin(), r.shell.end(), shell);
 }
 
 // Classification counts on the current mesh: [subsegs, subfaces, bad tets]

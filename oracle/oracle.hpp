@@ -23,9 +23,14 @@ struct RoundReport {
   std::vector<int> nflagS, nflagG;
   std::vector<int> flagS;       // sorted triples
   std::vector<int> flagG;       // sorted pairs
+  // start claims and shells (for checking the blasting rule): per candidate
+  // the start tetrahedra it claimed (none if its point was not located) and
+  // the tetrahedra across its cavity's boundary faces, as sorted tuples
+  std::vector<int> nstart, starts, nshell, shell;
   void clear() { *this = RoundReport(); }
   void record(const Mesh& M, int cls, const std::vector<Cand>& cands,
-              const std::vector<Decision>& dec, const std::vector<uint8_t>& surv);
+              const std::vector<Decision>& dec, const std::vector<uint8_t>& surv,
+              const std::vector<std::vector<int>>& claimed);
 };
 
 void cand_key(const Mesh& M, int cls, int elem, Cand& c);

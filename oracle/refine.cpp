@@ -767,11 +767,13 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
   std::vector<Decision> dec(n);
   // every candidate that locates its point claims its start tetrahedra
   std::unordered_map<int, int> seeds;
+  std::vector<std::vector<int>> claimed(n);
   for (int i = 0; i < n; ++i) {
     std::vector<int> st;
     Decision d0 = evaluate(M, cands[i].cls, cands[i].elem, nullptr, -1, nullptr, -1, &st);
     if (d0.outcome != OUT_OK) continue;
     for (int t : st) seeds.emplace(t, i);
+    claimed[i] = st;
   }
   for (int i = 0; i < n; ++i)
     dec[i] = evaluate(M, cands[i].cls, cands[i].elem, nullptr, -1, &seeds, i, nullptr);
@@ -813,7 +815,7 @@ int round_R(Mesh& M, double B, RoundReport* rep) {
           dec[i].reason = RS_STRUCT;
         }
   }
-  if (rep) rep->record(M, rcls, cands, dec, surv);
+  if (rep) rep->record(M, rcls, cands, dec, surv, claimed);
   for (int i = 0; i < n; ++i) apply_flags(M, dec[i]);
   int inserted = 0;
   for (int i = 0; i < n; ++i)

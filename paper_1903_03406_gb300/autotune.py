@@ -1,11 +1,16 @@
 """Launch tuning: search the settings `cdr_set_tuning` takes, for a workload.
 
 A setting changes speed only (every setting gives the same meshes), so the tuner
-times a callable that refines a sample workload under each candidate setting
-and keeps the fastest. The search is coordinate descent: one parameter at a
-time over its candidate values, starting from the defaults, repeated while a
-pass improves. The chosen setting is stored as JSON beside this module
-(`tuning.json`) and applied with `apply`.
+times a callable that refines a sample workload under each candidate setting.
+The settings are the launch shape (fused small rounds, growth grid, tier-2
+warps) and the region-growth buffers: how many cavity tetrahedra and boundary
+faces a tier-1 (shared-memory) workspace holds before a region moves to tier 2.
+The search is coordinate descent: one parameter at a time over its candidate
+values, starting from the defaults, repeated while a pass improves. Every
+setting is timed several times; a candidate replaces the incumbent only if its
+median is faster by more than the spread (max - min) of either one's trials, so
+that the choice is not made inside the run-to-run noise. The chosen setting is
+stored as JSON beside this module (`tuning.json`) and applied with `apply`.
 
     python -m paper_1903_03406_gb300.autotune [--instances 16] [--out PATH]
 
@@ -21,20 +26,41 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_PATH = os.path.join(HERE, "tuning.json")
 
-DEFAULTS = {"fused_max": 128, "grow1_blocks_per_sm": 8, "tier2_warps": 608}
+DEFAULTS = {"fused_max": 128, "grow1_blocks_per_sm": 8, "tier2_warps": 608,
+            "tier1_cavity": 64, "tier1_boundary": 160}
 SPACE = {
     "fused_max": [-1, 16, 32, 64, 128],
     "grow1_blocks_per_sm": [2, 4, 8, 16],
     "tier2_warps": [152, 304, 608, 1216],
+    "tier1_cavity": [16, 32, 64],
+    "tier1_boundary": [48, 96, 160],
 }
+REPEAT = 3  # timings per setting
+
+
+def _stats(times):
+    ts = sorted(float(t) for t in (times if isinstance(times, (list, tuple)) else [times]))
+    n = len(ts)
+    med = ts[n // 2] if n % 2 else 0.5 * (ts[n // 2 - 1] + ts[n // 2])
+    return med, ts[-1] - ts[0]
+
+
+def beats(cand_times, best_times):
+    """True if the candidate's median is faster than the incumbent's by more
+    than the spread of either one's timings."""
+    mc, sc = _stats(cand_times)
+    mb, sb = _stats(best_times)
+    return mc < mb - max(sc, sb)
 
 
 def search(measure, space=None, start=None, passes=2):
-    """measure(setting) -> seconds. Returns (best setting, its time, every trial)."""
+    """measure(setting) -> seconds, or a list of seconds (one per timing).
+    Returns (best setting, its median time, every trial as (setting, median,
+    spread))."""
     space = SPACE if space is None else space
     best = dict(DEFAULTS if start is None else start)
-    best_t = measure(best)
-    trials = [(dict(best), best_t)]
+    best_ts = measure(best)
+    trials = [(dict(best),) + _stats(best_ts)]
     for _ in range(passes):
         improved = False
         for key, values in space.items():
@@ -43,13 +69,13 @@ def search(measure, space=None, start=None, passes=2):
                     continue
                 cand = dict(best)
                 cand[key] = v
-                t = measure(cand)
-                trials.append((dict(cand), t))
-                if t < best_t:
-                    best, best_t, improved = cand, t, True
+                ts = measure(cand)
+                trials.append((dict(cand),) + _stats(ts))
+                if beats(ts, best_ts):
+                    best, best_ts, improved = cand, ts, True
         if not improved:
             break
-    return best, best_t, trials
+    return best, _stats(best_ts)[0], trials
 
 
 def save(setting, info=None, path=DEFAULT_PATH):
@@ -72,11 +98,11 @@ def apply(obj, setting):
         obj.tune(**setting)
 
 
-def _batch_measure(cdr, insts, allocator, stream, repeat=1):
+def _batch_measure(cdr, insts, allocator, stream, repeat=REPEAT):
     import torch
 
     def measure(setting):
-        best = float("inf")
+        times = []
         for _ in range(repeat):
             b = cdr.Batch(allocator=allocator, stream=stream)
             apply(b, setting)
@@ -88,9 +114,9 @@ def _batch_measure(cdr, insts, allocator, stream, repeat=1):
             t0 = time.perf_counter()
             b.refine()
             torch.cuda.synchronize()
-            best = min(best, time.perf_counter() - t0)
+            times.append(time.perf_counter() - t0)
             b.close()
-        return best
+        return times
     return measure
 
 
@@ -110,7 +136,8 @@ def main():
     measure(DEFAULTS)  # warm-up
     best, t, trials = search(measure)
     save(best, {"workload": "batched sample of %d instances (seed %d)" % (args.instances, args.seed),
-                "seconds": t, "trials": [[s, tt] for s, tt in trials]}, args.out)
+                "seconds": t, "timings_per_setting": REPEAT,
+                "trials": [[s, med, spread] for s, med, spread in trials]}, args.out)
     print(json.dumps({"setting": best, "seconds": t, "trials": len(trials)}))
 
 

@@ -60,7 +60,9 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("fused_max", ctypes.c_int32), ("grow1_blocks_per_sm", ctypes.c_int32),
-                ("tier2_warps", ctypes.c_int32)]
+                ("tier2_warps", ctypes.c_int32), ("tier1_cavity", ctypes.c_int32),
+                ("tier1_boundary", ctypes.c_int32), ("compact_min_tets", ctypes.c_int32),
+                ("compact_dead_pct", ctypes.c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -190,9 +192,11 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def set_tuning(ptr, fused_max=0, grow1_blocks_per_sm=0, tier2_warps=0):
+def set_tuning(ptr, fused_max=0, grow1_blocks_per_sm=0, tier2_warps=0, tier1_cavity=0,
+               tier1_boundary=0, compact_min_tets=0, compact_dead_pct=0):
     """Launch tuning of a handle or batch (cdr_set_tuning); results do not depend on it."""
-    t = Tuning(int(fused_max), int(grow1_blocks_per_sm), int(tier2_warps))
+    t = Tuning(int(fused_max), int(grow1_blocks_per_sm), int(tier2_warps), int(tier1_cavity),
+               int(tier1_boundary), int(compact_min_tets), int(compact_dead_pct))
     _check(lib().cdr_set_tuning(ptr, ctypes.byref(t)), "cdr_set_tuning")
 
 
@@ -300,7 +304,7 @@ class Handle:
               "insert", "compact", "fused"]
     COUNTERS = ["refused", "unsplittable", "blasted", "inserted", "retried", "invariant",
                 "tested", "cavity", "boundary", "new_tets", "new_candidates", "blasted_early",
-                "dead_tets", "c13", "c14", "launches", "fused_tested", "fused_cavity",
+                "dead_tets", "compactions", "c14", "launches", "fused_tested", "fused_cavity",
                 "fused_boundary"]
 
     def profile(self, enable=-1, reset=False):

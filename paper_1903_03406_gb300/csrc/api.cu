@@ -76,6 +76,10 @@ struct cdr_handle {
   int fusedMax = kFusedMax;   // rounds with at most this many candidates run fused
   int grow1PerSM = 8;         // growth grid: at most this many blocks per SM
   int tier2Warps = 152 * 4;   // warps (workspaces) for tier-2 growth
+  int tier1Cav = 0;           // tier-1 cavity capacity (0: Tier1::CAPC)
+  int tier1Bnd = 0;           // tier-1 boundary-face capacity (0: Tier1::CAPB)
+  int compactMin = 1 << 19;   // no compaction below this many tetrahedra
+  int compactPct = 50;        // compact once this percentage of the slots is dead
   double prof_ms[32] = {};
   long long prof_calls[32] = {};
   long long prof_ctr[32] = {};
@@ -468,6 +472,8 @@ DevRound make_round(cdr_handle* h, int cls, int n, double B) {
   DevRound r{};
   r.cls = cls;
   r.n = n;
+  r.t1cav = h->tier1Cav;
+  r.t1bnd = h->tier1Bnd;
   r.cand = ptr<int>(h->bCand2);
   r.given = ptr<double>(h->bPts);
   r.loc = ptr<int>(h->bLoc);
@@ -501,8 +507,9 @@ struct RoundOut {
 // count the live tetrahedra; compact when more than half are dead
 int maybe_compact(cdr_handle* h, bool force) {
   DevMesh& m = h->m;
-  if (!force && m.nT < (1 << 19)) return 0;
-  if (!force && h->deadKnown && h->deadT * 2 < m.nT) return 0;
+  if (!force && m.nT < h->compactMin) return 0;
+  if (!force && h->deadKnown && (long long)h->deadT * 100 < (long long)m.nT * h->compactPct)
+    return 0;
   Buf alive, newid;
   if (!ensure(h, alive, (size_t)m.nT * 4 + 64) || !ensure(h, newid, (size_t)(m.nT + 1) * 4 + 64))
     return CDR_ERR_OOM;
@@ -519,7 +526,7 @@ int maybe_compact(cdr_handle* h, bool force) {
   int live = last[0] + last[1];
   h->deadT = m.nT - live;
   h->deadKnown = true;
-  if (!force && live * 2 > m.nT) {
+  if (!force && (long long)h->deadT * 100 < (long long)m.nT * h->compactPct) {
     dfree(h, alive);
     dfree(h, newid);
     return 0;
@@ -548,6 +555,7 @@ int maybe_compact(cdr_handle* h, bool force) {
   cudaMemsetAsync(h->bTfwd.p, 0xff, (size_t)h->capT * 4, h->stream);
   dfree(h, alive);
   dfree(h, newid);
+  h->prof_ctr[13] += 1;  // compactions run
   return cuda_status(h);
 }
 
@@ -639,6 +647,7 @@ int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unso
   if (cuda_status(h)) return h->err;
   fo.tot = h->pin->lastOff;
   fo.n2 = h->pin->n2;
+  h->prof_ctr[ST_RETRY] += fo.n2;  // regions re-grown in tier 2
   if (h->pin->ovf) {
     exact_overflow_flag(s, true);
     return set_err(h, CDR_ERR_INTERNAL);
@@ -742,6 +751,7 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsor
     cudaMemcpyAsync(&h->pin->n2, nsel, 4, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     int n2 = h->pin->n2;
+    h->prof_ctr[ST_RETRY] += n2;  // regions re-grown in tier 2
     if (n2 > 0) {
       const size_t stride2 = SlabLayout<Tier2>::STRIDE;
       int warps = std::min(n2, h->tier2Warps);
@@ -2133,8 +2143,15 @@ int cdr_eval_predicates(int32_t kind, const double* in, int32_t n, int32_t* sign
 int cdr_set_tuning(cdr_handle* h, const cdr_tuning* t) {
   if (!h || !t) return CDR_ERR_INVALID_INPUT;
   if (t->fused_max < -1 || t->fused_max > kFusedMax || t->grow1_blocks_per_sm < 0 ||
-      t->grow1_blocks_per_sm > 32 || t->tier2_warps < 0 || t->tier2_warps > 152 * 32)
+      t->grow1_blocks_per_sm > 32 || t->tier2_warps < 0 || t->tier2_warps > 152 * 32 ||
+      t->tier1_cavity < 0 || t->tier1_cavity > Tier1::CAPC || t->tier1_boundary < 0 ||
+      t->tier1_boundary > Tier1::CAPB || t->compact_min_tets < 0 || t->compact_dead_pct < 0 ||
+      t->compact_dead_pct > 100)
     return CDR_ERR_INVALID_INPUT;
+  h->tier1Cav = t->tier1_cavity;
+  h->tier1Bnd = t->tier1_boundary;
+  h->compactMin = t->compact_min_tets > 0 ? t->compact_min_tets : (1 << 19);
+  h->compactPct = t->compact_dead_pct > 0 ? t->compact_dead_pct : 50;
   h->fused = t->fused_max != -1;
   h->fusedMax = t->fused_max > 0 ? t->fused_max : kFusedMax;
   h->grow1PerSM = t->grow1_blocks_per_sm > 0 ? t->grow1_blocks_per_sm : 8;

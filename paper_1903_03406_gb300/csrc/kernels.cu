@@ -1057,6 +1057,12 @@ template <class C>
 __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w, int* slab,
                          int lane, GrowAcc& acc) {
   using L = SlabLayout<C>;
+  // Tier 1's cavity and boundary-face capacities can be lowered at run time
+  // (a tuning setting; the arrays keep their compile-time size): a region that
+  // outgrows them is re-run in tier 2, so the result does not change.
+  constexpr bool kTier1 = C::CAPC == Tier1::CAPC && C::HCAP == Tier1::HCAP;
+  const int capc = kTier1 && r.t1cav > 0 ? min(r.t1cav, C::CAPC) : C::CAPC;
+  const int capb = kTier1 && r.t1bnd > 0 ? min(r.t1bnd, C::CAPB) : C::CAPB;
   const int cls = cls_of(r, i);
   int st = r.status[i];
   if (st != OUT_OK && st != OUT_RETRY) {
@@ -1107,7 +1113,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
     if (lane == 0) {
       int4 G = m.GV[CKI(elem, m.capG)];
       bool ok = edge_ring(m, G.w, sa, sb, [&](int t, const TetRec& rec) {
-        if (nc < C::CAPC) w.cav[nc] = t;
+        if (nc < capc) w.cav[nc] = t;
         ++nc;
         if (seed_blasts(m, r, t, i)) bad |= 2;
         hs_put(w.hset, C::HCAP, t, 1, false);
@@ -1139,7 +1145,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       reason = RS_WALK_LIMIT;
       goto done;
     }
-    if (nc > C::CAPC || nfl > C::CAPF) {
+    if (nc > capc || nfl > C::CAPF) {
       retry = true;
       goto done;
     }
@@ -1282,12 +1288,12 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           }
           retry = __any_sync(FULLMASK, retry);
           blast |= __any_sync(FULLMASK, bl);
-          wappend(w.cav, ncav, C::CAPC, pred, c, lane);
+          wappend(w.cav, ncav, capc, pred, c, lane);
         }
         __syncwarp();
       }
       if (blast) goto done;
-      if (retry || ncav > C::CAPC) {
+      if (retry || ncav > capc) {
         retry = true;
         goto done;
       }
@@ -1330,15 +1336,15 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           }
           retry = __any_sync(FULLMASK, retry);
           blast |= __any_sync(FULLMASK, bl);
-          wappend(w.cav, ncav, C::CAPC, add, cand, lane);
+          wappend(w.cav, ncav, capc, add, cand, lane);
           __syncwarp();
-          if (blast || retry || ncav > C::CAPC) break;
+          if (blast || retry || ncav > capc) break;
         }
         head = end;
-        if (blast || retry || ncav > C::CAPC) break;
+        if (blast || retry || ncav > capc) break;
       }
       if (blast) goto done;
-      if (retry || ncav > C::CAPC) {
+      if (retry || ncav > capc) {
         retry = true;
         goto done;
       }
@@ -1377,7 +1383,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         {
           unsigned bal = __ballot_sync(FULLMASK, pred);
           int pos = nbnd + __popc(bal & ((1u << lane) - 1));
-          if (pred && pos < C::CAPB) {
+          if (pred && pos < capb) {
             w.bin[pos] = bi;
             w.bout[pos] = bo;
             w.bv[3 * pos] = v0;
@@ -1402,17 +1408,17 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         blast |= __any_sync(FULLMASK, bl);
         __syncwarp();
         // a tet appended earlier in this pass is already in; skip duplicates
-        if (add && in_list(w.cav, min(ncav, C::CAPC), cand)) add = false;
+        if (add && in_list(w.cav, min(ncav, capc), cand)) add = false;
         __syncwarp();
         int before = ncav;
-        wappend(w.cav, ncav, C::CAPC, add, cand, lane);
+        wappend(w.cav, ncav, capc, add, cand, lane);
         changed |= ncav != before;
         __syncwarp();
-        if (retry || ncav > C::CAPC) break;
+        if (retry || ncav > capc) break;
       }
       cfail |= fail;
       if (blast) goto done;
-      if (retry || ncav > C::CAPC) {
+      if (retry || ncav > capc) {
         retry = true;
         goto done;
       }
@@ -1447,7 +1453,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         }
         unsigned bal = __ballot_sync(FULLMASK, pred);
         int pos = nbnd + __popc(bal & ((1u << lane) - 1));
-        if (pred && pos < C::CAPB) {
+        if (pred && pos < capb) {
           w.bin[pos] = bi;
           w.bout[pos] = bo;
           w.bv[3 * pos] = v0;
@@ -1458,7 +1464,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       }
     }
     __syncwarp();  // the lists written above are read by other lanes below
-    if (nbnd > C::CAPB) {
+    if (nbnd > capb) {
       retry = true;
       goto done;
     }
@@ -1741,7 +1747,7 @@ done:
              reason == RS_ENCROACH_UNSPL) {
     // the cavity is complete: keep its tets for the round report
     if (w.cav != slab + L::OFF_CAV)
-      for (int k = lane; k < min(ncav, C::CAPC); k += 32) slab[L::OFF_CAV + k] = w.cav[k];
+      for (int k = lane; k < min(ncav, capc); k += 32) slab[L::OFF_CAV + k] = w.cav[k];
   }
 }
 

@@ -179,6 +179,8 @@ struct DevRound {
   const int* cinst;
   int4* ckey;                  // per candidate: sorted vertex ids (round report)
   int* rflag;                  // per candidate: 1 if its region needs tier 2
+  int t1cav, t1bnd;            // tier-1 cavity / boundary-face capacities in use
+                               // (0: the compile-time Tier1 sizes)
 };
 
 // device counters

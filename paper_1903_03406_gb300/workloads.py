@@ -9,6 +9,8 @@ MULTI = {
     "batched64": dict(count=64, nmin=1000, nmax=50000, B=(1.6,), seed=1000),
     "served40": dict(count=40, nmin=2000, nmax=200000, B=(1.4, 1.6, 2.0), seed=10 ** 6),
 }
+# instances / requests of the whole workloads these are samples of
+FULL_COUNT = {"batched64": 256, "served40": 2000}
 
 
 def multi_specs(spec, rank):

@@ -5,7 +5,8 @@ from paper_1903_03406_gb300 import autotune
 
 
 def test_coordinate_search_finds_the_best_setting():
-    target = {"fused_max": 64, "grow1_blocks_per_sm": 4, "tier2_warps": 1216}
+    target = {"fused_max": 64, "grow1_blocks_per_sm": 4, "tier2_warps": 1216,
+              "tier1_cavity": 32, "tier1_boundary": 96}
     calls = []
 
     def measure(s):
@@ -25,10 +26,33 @@ def test_search_keeps_the_start_when_nothing_is_faster():
     assert len(trials) == 1 + sum(len(v) - 1 for v in autotune.SPACE.values())
 
 
+def test_a_win_inside_the_noise_is_not_taken():
+    """Repeated timings: a setting 1% faster on the median but with a 5% spread
+    does not replace the incumbent; one faster by more than the spread does."""
+    def noisy(base):
+        return [base * 0.975, base, base * 1.025]
+
+    fast = dict(autotune.DEFAULTS, grow1_blocks_per_sm=16)
+
+    def measure(s):
+        return noisy(0.99 if s == fast else 1.0)
+
+    best, _, _ = autotune.search(measure)
+    assert best == autotune.DEFAULTS
+
+    def measure2(s):
+        return noisy(0.9 if s == fast else 1.0)
+
+    best, t, trials = autotune.search(measure2)
+    assert best == fast and abs(t - 0.9) < 1e-12
+    assert all(len(x) == 3 for x in trials)  # setting, median, spread
+
+
 def test_save_load_apply(tmp_path):
     p = tmp_path / "t.json"
     assert autotune.load(str(p)) is None
-    s = {"fused_max": 32, "grow1_blocks_per_sm": 8, "tier2_warps": 608}
+    s = {"fused_max": 32, "grow1_blocks_per_sm": 8, "tier2_warps": 608, "tier1_cavity": 32,
+         "tier1_boundary": 160}
     autotune.save(s, {"note": "x"}, str(p))
     assert autotune.load(str(p)) == s
 

@@ -71,3 +71,27 @@ def test_traffic_record_scales_or_is_withheld():
         # the kernels changed since the capture: no traffic figure is reported
         assert t is None
     assert bench.ncu_traffic("no_such_kernel", 1.0) is None
+
+
+def test_quality_band_against_the_stored_oracle_run():
+    """The band object compares the GPU's final counts with the stored oracle
+    run: ratios of the Steiner count and of the bad-tetrahedron fraction."""
+    o = bench.oracle_counts("clustered500k")
+    assert o and o["steiner"] > 0 and o["contract_ok"]
+    b = bench.quality_band("clustered500k", o["steiner"], o["bad_left"], o["tets"])
+    assert b["steiner_ratio"] == 1.0 and abs(b["bad_frac_ratio"] - 1.0) < 1e-12
+    assert b["within_band"]
+    b = bench.quality_band("clustered500k", int(o["steiner"] * 1.2), o["bad_left"], o["tets"])
+    assert not b["within_band"]
+    # a workload with no bad tetrahedra left on either side is in the band
+    c = bench.oracle_counts("cube2k")
+    b = bench.quality_band("cube2k", c["steiner"], 0, c["tets"])
+    assert c["bad_left"] == 0 and b["bad_frac_ratio"] == 1.0 and b["within_band"]
+    assert bench.quality_band("no_such_workload", 1, 0, 1) is None
+
+
+def test_cpu_baseline_states_its_coverage():
+    o = bench.oracle_counts("clustered500k")
+    line = bench.cpu_baseline_line("clustered500k", 50000, 15.0)
+    assert line["value"] == 50000 / 15.0 and line["cores"] == 1 and line["kind"] == "oracle"
+    assert "of the %d insertions" % o["steiner"] in line["sample"]

@@ -33,6 +33,8 @@ def _check_line(line, n_gpus):
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    # the oracle's run of the same input to the end, stored beside the tests
+    assert line["oracle_to_the_end"]["steiner"] == bench.oracle_counts("cube2k")["steiner"]
 
 
 def test_reference_arm_single_process():

@@ -6,7 +6,10 @@ Instances of different sizes, constraint counts and bounds B are refined alone
 instance the identical mesh: same vertex coordinates in the same order, same
 tetrahedra, subfaces and subsegments with the same flags (the tolerance is zero).
 That holds whether an instance joins at the start or after other instances
-have run rounds, and when it takes the slot of a removed instance.
+have run rounds, and when it takes the slot of a removed instance. Every
+instance's batched result is also compared with the oracle's round-by-round
+refinement (mode R) of the same input, so a fault shared by the batched and
+the one-mesh paths cannot pass.
 """
 import numpy as np
 import pytest
@@ -43,6 +46,19 @@ def cases():
     return out
 
 
+def _oracle_refined(i, mixed=0):
+    kind, n, ns, nt, seed, B = CASES[i]
+    om, _, _ = oracle_case(kind, n, ns, nt, seed)
+    om.set_mixed(mixed)
+    so = om.refine_R(B)
+    return om.export(), so
+
+
+@pytest.fixture(scope="module")
+def oracle_results():
+    return [_oracle_refined(i) for i in range(len(CASES))]
+
+
 def _args(e, plc):
     return (e["xyz"], e["tets"], plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"],
             plc["nfacets"])
@@ -60,14 +76,16 @@ def alone(cdr, cases):
     return res
 
 
-def test_batch_equals_alone(cdr, cases, alone):
+def test_batch_equals_alone(cdr, cases, alone, oracle_results):
     b = cdr.Batch()
     slots = [b.add(B, *_args(e, plc)) for e, plc, B in cases]
     assert slots == list(range(len(cases)))
     rounds = b.refine()
     assert rounds == max(a[1]["rounds"] for a in alone)
-    for k, (ex, st) in zip(slots, alone):
+    for k, (ex, st), (oe, so) in zip(slots, alone, oracle_results):
         assert_same_mesh(b.export(k), ex, "instance %d" % k)
+        assert_same_mesh(b.export(k), oe, "instance %d against the oracle" % k)
+        assert st["steiner_inserted"] == so["inserted"] and st["rounds"] == so["rounds"]
         s = b.stats(k)
         assert s["state"] == "done"
         assert s["steiner_inserted"] == st["steiner_inserted"]
@@ -92,12 +110,15 @@ def test_batch_equals_alone_mixed_rounds(cdr, cases):
     b.refine()
     for k, (ex, st) in zip(slots, res):
         assert_same_mesh(b.export(k), ex, "mixed instance %d" % k)
+        oe, so = _oracle_refined(k, mixed=1)
+        assert_same_mesh(b.export(k), oe, "mixed instance %d against the oracle" % k)
+        assert so["inserted"] == st["steiner_inserted"]
         assert b.stats(k)["steiner_inserted"] == st["steiner_inserted"]
         assert b.stats(k)["rounds"] == st["rounds"]
     b.close()
 
 
-def test_late_admission_and_slot_reuse(cdr, cases, alone):
+def test_late_admission_and_slot_reuse(cdr, cases, alone, oracle_results):
     b = cdr.Batch()
     s0 = b.add(cases[0][2], *_args(*cases[0][:2]))
     s1 = b.add(cases[1][2], *_args(*cases[1][:2]))
@@ -113,6 +134,8 @@ def test_late_admission_and_slot_reuse(cdr, cases, alone):
     assert_same_mesh(b.export(s0), alone[0][0], "first")
     assert_same_mesh(b.export(s2), alone[2][0], "late")
     assert_same_mesh(b.export(s3), alone[3][0], "reused slot")
+    assert_same_mesh(b.export(s2), oracle_results[2][0], "late, against the oracle")
+    assert_same_mesh(b.export(s3), oracle_results[3][0], "reused slot, against the oracle")
     assert b.stats(s3)["steiner_inserted"] == alone[3][1]["steiner_inserted"]
     b.close()
 

@@ -12,9 +12,15 @@ within a test, so:
   volume equals the box's, the Euler characteristic is 1, every input segment
   is a chain of subsegments, and every subface bounds one or two tetrahedra;
 * the splitting points of full-size rounds are bit-identical to the oracle's
-  formulas, candidate by candidate.
+  formulas, candidate by candidate;
+* the final Steiner count and fraction of bad tetrahedra left stay within
+  1.15x of the oracle's sequential refinement of the same input run to the end
+  (its counts stored in tests/golden/oracle_counts.json by
+  tests/golden/make_oracle_counts.py, which calls only the oracle).
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -160,7 +166,12 @@ def test_full_size_refinement_properties(cdr, name):
     assert st["status"] == 0 and st["steiner_inserted"] > w["n"]
     ex = h.export()
     h.close()
-    assert st["n_bad_left"] <= 0.01 * len(ex["tets"])
+    # the quality band against the oracle's sequential refinement to the end
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_counts.json")) as f:
+        ref = json.load(f)[name]
+    assert ref["contract_ok"] and ref["points_in"] == len(ex0["xyz"])
+    assert st["steiner_inserted"] <= 1.15 * ref["steiner"]
+    assert st["n_bad_left"] / len(ex["tets"]) <= 1.15 * ref["bad_frac"]
     _check(ex, plc, w["B"], lo, hi, np.random.default_rng(7))
 
 

@@ -194,6 +194,25 @@ def test_rounds_lockstep_boundary_mixed(cdr):
     assert h.round(1.4)["cls"] == -1
 
 
+@pytest.mark.parametrize("fused", [False, True])
+def test_rounds_lockstep_tier2_growth(cdr, fused):
+    """Tier-1 workspaces shrunk to 8 cavity tetrahedra and 24 boundary faces, so
+    that most regions are re-grown in tier 2 (the separate k_grow2 launch, or
+    the fused round's own tier 2): lockstep with mode R to the end."""
+    om, e, plc = oracle_case("uniform", 700, 7, 7, 5)
+    h = gpu_handle(cdr, e, plc)
+    h.tune(fused_max=0 if fused else -1, tier1_cavity=8, tier1_boundary=24)
+    h.profile(enable=1, reset=True)
+    classes = _lockstep(cdr, om, h, 1.4, 3000, "tier2-700")
+    assert set(classes) == {0, 1, 2}
+    prof = h.profile(enable=0)
+    assert prof["counters"]["retried"] > 100
+    if fused:
+        assert prof["calls"]["fused"] > 0
+    else:
+        assert prof["calls"]["grow2"] > 0 and prof["calls"]["fused"] == 0
+
+
 def test_rounds_lockstep_mixed_stall(cdr):
     """Mixed rounds with dense free segments: the stall rule applies per round
     to the subsegment candidates, identically on both sides."""
@@ -241,8 +260,13 @@ def test_refine_cube2k_equals_round_oracle(cdr):
     GPU equals the oracle's round-by-round result, and meets the contract."""
     om, e, plc = oracle_case("cube", 2000, 0, 0, 0)
     h = gpu_handle(cdr, e, plc)
+    # compact the tetrahedron arrays whenever a tenth of the slots is dead, so
+    # that compaction runs (and is checked) inside this refinement
+    h.tune(compact_min_tets=1, compact_dead_pct=10)
+    h.profile(reset=True)
     st = h.refine(2.0)
     assert st["status"] == 0 and st["n_bad_left"] == 0
+    assert h.profile()["counters"]["compactions"] > 0
     so = om.refine_R(2.0)
     assert st["rounds"] == so["rounds"] and st["steiner_inserted"] == so["inserted"]
     ex = h.export()

@@ -1,6 +1,7 @@
 """Serving (continuous batching over cdr_batch_*) on the GPU: requests that
 arrive while others refine are admitted as memory frees up, and each result is
-the mesh the request gets alone (needs a GPU)."""
+the mesh the request gets alone and the mesh of the oracle's round-by-round
+refinement (mode R) of the same input (needs a GPU)."""
 import numpy as np
 import pytest
 
@@ -36,9 +37,9 @@ class StepClock:
 
 def test_served_results_equal_alone(cdr):
     from paper_1903_03406_gb300 import serve
-    reqs, alone = [], []
+    reqs, alone, orc = [], [], []
     for i, (kind, n, ns, nt, seed, B) in enumerate(CASES):
-        _, e, plc = oracle_case(kind, n, ns, nt, seed)
+        om, e, plc = oracle_case(kind, n, ns, nt, seed)
         mesh = dict(xyz=e["xyz"], tets=e["tets"], segs=plc["segs"], seg_id=plc["seg_id"],
                     tris=plc["tris"], facet_id=plc["facet_id"], nfacets=plc["nfacets"])
         h = cdr.Handle.create(mesh["xyz"], mesh["tets"], mesh["segs"], mesh["seg_id"],
@@ -46,6 +47,8 @@ def test_served_results_equal_alone(cdr):
         st = h.refine(B)
         alone.append((h.export(), st))
         h.close()
+        so = om.refine_R(B)
+        orc.append((om.export(), so))
         reqs.append(serve.Request(i, arrival=float(6 * i), B=B, mesh=mesh))
     b = cdr.Batch()
     # room for about two requests at a time: later ones queue, then join the
@@ -59,7 +62,8 @@ def test_served_results_equal_alone(cdr):
     for r in res:
         ex, st = alone[r.rid]
         assert_same_mesh(r.mesh, ex, "request %d" % r.rid)
-        assert r.stats["steiner_inserted"] == st["steiner_inserted"]
+        assert_same_mesh(r.mesh, orc[r.rid][0], "request %d against the oracle" % r.rid)
+        assert r.stats["steiner_inserted"] == st["steiner_inserted"] == orc[r.rid][1]["inserted"]
         assert r.done > r.admitted >= r.arrival
     # requests overlapped on the device: fewer rounds than run one after another
     assert srv.rounds < sum(st["rounds"] for _, st in alone)
