@@ -49,11 +49,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOADS = {
-    "uniform100k": dict(kind="uniform", n=100_000, seed=1, B=1.4, n_seg=1000, n_tri=1000),
-    "cube2k": dict(kind="cube", n=2000, seed=0, B=2.0, n_seg=0, n_tri=0),
-    "clustered500k": dict(kind="clustered", n=500_000, seed=2, B=1.4, n_seg=5000, n_tri=5000),
-}
+from paper_1903_03406_gb300.inputs import CONFIGS as WORKLOADS  # noqa: E402
 METRIC = "Steiner pts inserted/s on 1 GB300"
 UNIT = "Steiner points/s"
 
@@ -166,6 +162,16 @@ def make_workload(name, rank, cdr, stream):
     from paper_1903_03406_gb300 import replicas
     seed = replicas.instance_seed(w["seed"], rank)
     pts, _, _ = inputs.box_points(w["kind"], w["n"], seed)
+    if w["recipe"] == "recovered":
+        from paper_1903_03406_gb300 import recover
+        segs = inputs.free_segments(pts, w["n_seg"], seed)
+        log("recovering %d segments on the GPU (%d points)" % (len(segs), len(pts)))
+        xyz, tets, chains, passes = recover.recover_segments(pts, segs, cdr, stream=stream)
+        log("recovery: %d passes, %d midpoints" % (passes, len(xyz) - len(pts)))
+        ex = {"xyz": xyz, "tets": tets, "recovery_passes": passes,
+              "midpoints": len(xyz) - len(pts)}
+        plc = inputs.plc_with_chains(xyz, tets, chains, len(pts), w["n_tri"], seed)
+        return pts, ex, plc
     log("building the initial Delaunay mesh on the GPU (%d points)" % len(pts))
     dt = cdr.Handle.delaunay_box(pts, stream=stream)
     log("delaunay: %d rounds, %d skipped" % (dt.dt_rounds, dt.skipped))
@@ -333,6 +339,10 @@ def gpu_arm(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": dict(workload_config(args, world), l2="flushed between steps (256 MB write)",
+                       initial_mesh=({"segment_recovery_passes": ex["recovery_passes"],
+                                      "midpoints": ex["midpoints"],
+                                      "built": "on the GPU, untimed"}
+                                     if "recovery_passes" in ex else "GPU Delaunay, untimed"),
                        tuning=tuning or "defaults",
                        steiner_per_step=last["steiner_inserted"], rounds_per_step=last["rounds"],
                        final_tets=last["n_tets"], bad_left=last["n_bad_left"], wall_s=t_wall),
@@ -516,6 +526,10 @@ def workload_config(args, world):
     w = WORKLOADS[args.workload]
     return {"workload": args.workload, "points": w["n"] + 8, "segments": w["n_seg"],
             "triangles": w["n_tri"], "B": w["B"],
+            "constraints": {"recovered": "free segments between nearby points, recovered by "
+                                         "midpoints; triangles (some in edge-sharing pairs) "
+                                         "among the recovered mesh's faces",
+                            "delaunay": "among the Delaunay edges and faces"}[w["recipe"]],
             "parallelism": "independent instances x%d (replicas)" % world,
             "rounds": {0: "one class per round",
                        1: "mixed: every class each round, class-first priority",
@@ -566,9 +580,16 @@ def oracle_workload(name):
     from paper_1903_03406_gb300 import inputs
     w = WORKLOADS[name]
     pts, _, _ = inputs.box_points(w["kind"], w["n"], w["seed"])
-    om = oracle.Mesh.box_delaunay(pts)
-    e = om.export()
-    plc = inputs.plc_from_delaunay(pts, e["tets"], w["n_seg"], w["n_tri"], w["seed"])
+    if w["recipe"] == "recovered":
+        from oracle.recover import recover_segments
+        segs = inputs.free_segments(pts, w["n_seg"], w["seed"])
+        om, xyz, chains, _ = recover_segments(pts, segs)
+        e = om.export()
+        plc = inputs.plc_with_chains(xyz, e["tets"], chains, len(pts), w["n_tri"], w["seed"])
+    else:
+        om = oracle.Mesh.box_delaunay(pts)
+        e = om.export()
+        plc = inputs.plc_from_delaunay(pts, e["tets"], w["n_seg"], w["n_tri"], w["seed"])
     om.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"], plc["nfacets"])
     return om, e, plc
 
@@ -654,17 +675,24 @@ def profile_run(args):
     ins = 0
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("replay")  # the whole second refinement
+    c0 = c1 = None
     for k in range(len(cands)):
         if k == big:
+            c0 = h.profile()["counters"]
             torch.cuda.nvtx.range_push("largest")
         ins += h.round(w["B"])["steiner_inserted"]
         if k == big:
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_pop()
+            c1 = h.profile()["counters"]
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    delta = {c: c1[c] - c0[c] for c in ("tested", "cavity", "boundary")}
     print(json.dumps({"profile_run": args.workload, "rounds": len(cands), "steiner": ins,
                       "largest_round": big, "largest_candidates": cands[big],
+                      "largest_round_growth": delta,
+                      "largest_round_algorithmic_bytes": grow_bytes(delta),
+                      "kernels_sha": kernel_hash(),
                       "counters": h.profile()["counters"]}), flush=True)
     h.close()
 

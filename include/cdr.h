@@ -300,7 +300,7 @@ int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_
  *                        holds before the region is re-grown in tier 2 (1..64);
  *                        0: 64
  *   tier1_boundary       cavity boundary faces a tier-1 workspace holds
- *                        (1..160); 0: 160
+ *                        (1..96); 0: 96
  *   compact_min_tets     tetrahedron slots below which the dead ones are never
  *                        compacted away; 0: 524288
  *   compact_dead_pct     the tetrahedron arrays are compacted once at least this

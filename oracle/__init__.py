@@ -75,6 +75,8 @@ def lib():
             L.orc_prio_hash_xyz.restype = ctypes.c_uint64
             L.orc_box_delaunay.argtypes = [dp, ctypes.c_int, ip]
             L.orc_box_delaunay.restype = P
+            L.orc_insert_points.argtypes = [P, dp, ctypes.c_int]
+            L.orc_insert_points.restype = ctypes.c_int
             L.orc_create.argtypes = [dp, ctypes.c_int, ip, ctypes.c_int]
             L.orc_create.restype = P
             L.orc_free.argtypes = [P]
@@ -213,6 +215,16 @@ class Mesh:
         m = cls(h)
         m.skipped = sk.value
         return m
+
+    def insert_points(self, pts):
+        """More points into a box Delaunay mesh (before set_constraints): the
+        sequential Bowyer-Watson step, in Morton order. Returns the duplicates
+        skipped."""
+        pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 3))
+        r = lib().orc_insert_points(self.h, _d(pts), len(pts))
+        if r < 0:
+            raise ValueError("a point lies outside the box")
+        return r
 
     @classmethod
     def create(cls, xyz, tets):

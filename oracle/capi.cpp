@@ -217,6 +217,11 @@ void* orc_box_delaunay(const double* pts, int n, int* skipped) {
   return h;
 }
 
+// More points into a box Delaunay mesh (before constraints are labelled).
+int orc_insert_points(void* hp, const double* pts, int n) {
+  return insert_box_points(((Handle*)hp)->M, pts, n);
+}
+
 void* orc_create(const double* xyz, int nv, const int* tets, int nt) {
   Handle* h = new Handle();
   h->M.P.resize(nv);

@@ -46,5 +46,6 @@ void classify(const Mesh& M, double B, std::vector<int>* q);
 int round_R(Mesh& M, double B, RoundReport* rep);
 long refine_S(Mesh& M, double B, long max_steps, SeqStats* st);
 int build_box_delaunay(Mesh& M, const double* pts, int n);
+int insert_box_points(Mesh& M, const double* pts, int n);
 
 }  // namespace orc

@@ -1050,4 +1050,49 @@ int build_box_delaunay(Mesh& M, const double* pts, int n) {
   return skipped;
 }
 
+// Inserts n more points into a mesh built by build_box_delaunay (no
+// constraints labelled yet): each is appended to the vertices and inserted by
+// the same sequential Bowyer-Watson step, in Morton order of the new points.
+// Returns the points skipped as duplicates, or -1 if a point lies outside the box.
+int insert_box_points(Mesh& M, const double* pts, int n) {
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (auto& q : M.P)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], q[k]);
+      hi[k] = std::max(hi[k], q[k]);
+    }
+  const int base = (int)M.P.size();
+  for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k)
+      if (!(pts[3 * i + k] > lo[k] && pts[3 * i + k] < hi[k])) return -1;
+    M.P.push_back(V3{pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]});
+  }
+  std::vector<std::pair<uint64_t, int>> order;
+  for (int i = base; i < base + n; ++i) {
+    double x = (M.P[i][0] - lo[0]) / (hi[0] - lo[0]);
+    double y = (M.P[i][1] - lo[1]) / (hi[1] - lo[1]);
+    double z = (M.P[i][2] - lo[2]) / (hi[2] - lo[2]);
+    order.push_back({morton3(x, y, z), i});
+  }
+  std::sort(order.begin(), order.end());
+  int hint = (int)M.T.size() - 1;
+  int skipped = 0;
+  double saved = M.guard2;
+  M.guard2 = 0.0;
+  for (auto& o : order) {
+    int i = o.second;
+    while (!M.talive[hint]) --hint;
+    Decision d = evaluate(M, CLS_POINT, i, M.X(i), hint, nullptr, -1, nullptr);
+    if (d.outcome != OUT_OK) {
+      ++skipped;
+      continue;
+    }
+    apply(M, d, i, nullptr, nullptr, nullptr);
+    hint = (int)M.T.size() - 1;
+  }
+  M.guard2 = saved;
+  return skipped;
+}
+
 }  // namespace orc
+

@@ -34,6 +34,9 @@ def _flags():
         f.append("-DCDR_CHECKED")  # bounds-checked diagnostic build
     if os.environ.get("CDR_PHASES"):
         f.append("-DCDR_PHASES")  # per-phase timing of region growth (diagnostic build)
+    # build-time sizes of the growth workspaces (CDR_T1_CAPB, CDR_T1_HCAP,
+    # CDR_G1_MINB), e.g. CDR_DEFS="CDR_T1_HCAP=512 CDR_G1_MINB=4"
+    f += ["-D" + d for d in os.environ.get("CDR_DEFS", "").split()]
     return f
 
 

@@ -1053,7 +1053,9 @@ __device__ __forceinline__ void flush_acc(const DevRound& r, const GrowAcc& a, i
   }
 }
 
-template <class C>
+// kOnly >= 0: every candidate of the launch has that class (a one-class
+// round), so the code of the other classes is compiled out. -1: any class.
+template <class C, int kOnly = -1>
 __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w, int* slab,
                          int lane, GrowAcc& acc) {
   using L = SlabLayout<C>;
@@ -1063,7 +1065,9 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   constexpr bool kTier1 = C::CAPC == Tier1::CAPC && C::HCAP == Tier1::HCAP;
   const int capc = kTier1 && r.t1cav > 0 ? min(r.t1cav, C::CAPC) : C::CAPC;
   const int capb = kTier1 && r.t1bnd > 0 ? min(r.t1bnd, C::CAPB) : C::CAPB;
-  const int cls = cls_of(r, i);
+  // tetrahedra only: no facet part, no subsegment ring
+  constexpr bool kFacets = kOnly != CLS_TET;
+  const int cls = kOnly >= 0 ? kOnly : cls_of(r, i);
   int st = r.status[i];
   if (st != OUT_OK && st != OUT_RETRY) {
     if (lane == 0) {
@@ -1156,7 +1160,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
 
   PHASE(1);  // start sets
   // ---------------------------------------------------------- facet part
-  if (nf > 0) {
+  if (kFacets && nf > 0) {
     int head = 0;
     for (;;) {
       while (head < nf) {
@@ -1364,7 +1368,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           int nb = geti(rec.n, f);
           CKL(nb, m.nT);
           bool sub = face_sub(rec.v, f);
-          bool removed = sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
+          bool removed = kFacets && sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
           bool interior = !sub && nb >= 0 && hs_find(w.hset, C::HCAP, nb >> 2) == 1;
           pred = !removed && !interior;
           if (pred && orient_rep(m, rec, f, p) <= 0) {
@@ -1438,7 +1442,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           TetRec rec = ld_tet(m, t);
           int nb = geti(rec.n, f);
           bool sub = face_sub(rec.v, f);
-          bool removed = sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
+          bool removed = kFacets && sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
           bool interior = !sub && nb >= 0 && hs_find(w.hset, C::HCAP, nb >> 2) == 1;
           pred = !removed && !interior;
           bi = (t << 2) | f;
@@ -1764,7 +1768,12 @@ struct Smem1 {
   int fbv[3 * Tier1::CAPFB];
 };
 
-__global__ void __launch_bounds__(32 * kWarps1, 3) k_grow1(DevMesh m, DevRound r) {
+// blocks per SM the register budget is sized for (build-time, CDR_G1_MINB)
+#ifndef CDR_G1_MINB
+#define CDR_G1_MINB 4
+#endif
+template <int kOnly>
+__global__ void __launch_bounds__(32 * kWarps1, CDR_G1_MINB) k_grow1(DevMesh m, DevRound r) {
   extern __shared__ int smraw[];
   Smem1* sm = reinterpret_cast<Smem1*>(smraw) + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
@@ -1774,7 +1783,7 @@ __global__ void __launch_bounds__(32 * kWarps1, 3) k_grow1(DevMesh m, DevRound r
   GrowAcc acc;
   for (int i = warp; i < r.n; i += nw) {
     int* slab = r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
-    grow_one<Tier1>(m, r, i, w, slab, lane, acc);
+    grow_one<Tier1, kOnly>(m, r, i, w, slab, lane, acc);
     __syncwarp();
     if (lane == 0 && r.rflag) r.rflag[i] = r.status[i] == OUT_RETRY ? 1 : 0;
   }
@@ -2458,12 +2467,18 @@ void launch_grow1(const DevMesh& m, const DevRound& r, int blocks_per_sm, cudaSt
   static bool attr = false;
   size_t smem = sizeof(Smem1) * kWarps1;
   if (!attr) {
-    cudaFuncSetAttribute(k_grow1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_grow1<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_grow1<CLS_TET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr = true;
   }
   long blocks = ((long)r.n + kWarps1 - 1) / kWarps1;
   if (blocks > 152L * blocks_per_sm) blocks = 152L * blocks_per_sm;
-  k_grow1<<<(int)blocks, 32 * kWarps1, smem, s>>>(m, r);
+  // a round of bad tetrahedra alone runs the tetrahedron-only growth
+  if (r.cls == CLS_TET && !r.ccls)
+    k_grow1<CLS_TET><<<(int)blocks, 32 * kWarps1, smem, s>>>(m, r);
+  else
+    k_grow1<-1><<<(int)blocks, 32 * kWarps1, smem, s>>>(m, r);
 }
 void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s) {
   if (r.n2 <= 0 || r.nws2 <= 0) return;

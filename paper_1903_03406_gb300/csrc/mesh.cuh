@@ -126,9 +126,18 @@ struct Caps {
   static constexpr int CAP3 = 3 * CAPB_;  // boundary-table entries below this are edges
 };
 // HCAP: the tet hash set of growth, reused afterwards as the table of boundary
-// edges and vertices (at most 3 CAPB edges + CAPB/2 + 2 vertices, kept under
-// 60% load).
-using Tier1 = Caps<64, 160, 32, 48, 1024>;
+// edges and vertices (at most 3 CAPB edges + CAPB/2 + 2 vertices: 338 entries,
+// two thirds of tier 1's 512 slots; a full table sends the region to tier 2).
+// Tier 1's boundary-face capacity and table size can be set at build time
+// (CDR_T1_CAPB, CDR_T1_HCAP) to trade shared memory per warp against the share
+// of regions that move to tier 2; results do not depend on them.
+#ifndef CDR_T1_CAPB
+#define CDR_T1_CAPB 96
+#endif
+#ifndef CDR_T1_HCAP
+#define CDR_T1_HCAP 512
+#endif
+using Tier1 = Caps<64, CDR_T1_CAPB, 32, 48, CDR_T1_HCAP>;
 using Tier2 = Caps<4096, 16384, 8192, 24576, 131072>;
 constexpr int kCavLimit = 4096;
 

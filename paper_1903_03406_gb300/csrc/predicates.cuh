@@ -327,7 +327,14 @@ __device__ __noinline__ int orient3d_exact(D3 a, D3 b, D3 c, D3 d) {
 
 // FP64 filter, then exact arithmetic (out of line: the FP32 stage decides
 // nearly every call, and one copy keeps the kernels' code small)
-__device__ __noinline__ int orient3d_fp64(D3 a, D3 b, D3 c, D3 d) {
+// The FP64 stages are kept out of line by default (smaller code at every call
+// site); CDR_FP64_INLINE builds them inline (no call, no register save).
+#ifdef CDR_FP64_INLINE
+#define CDR_FP64_STAGE __device__ __forceinline__
+#else
+#define CDR_FP64_STAGE __device__ __noinline__
+#endif
+CDR_FP64_STAGE int orient3d_fp64(D3 a, D3 b, D3 c, D3 d) {
   double ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
   double vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
   double wx = d.x - a.x, wy = d.y - a.y, wz = d.z - a.z;
@@ -418,7 +425,7 @@ __device__ __forceinline__ float det3f32(float ax, float ay, float az, float bx,
   return ax * m1 + ay * m2 + az * m3;
 }
 
-__device__ __noinline__ int insphere_fp64(D3 a, D3 b, D3 c, D3 d, D3 e) {
+CDR_FP64_STAGE int insphere_fp64(D3 a, D3 b, D3 c, D3 d, D3 e) {
   double ax = a.x - e.x, ay = a.y - e.y, az = a.z - e.z;
   double bx = b.x - e.x, by = b.y - e.y, bz = b.z - e.z;
   double cx = c.x - e.x, cy = c.y - e.y, cz = c.z - e.z;

@@ -30,15 +30,34 @@ segment, as a PLC polygon's boundary edges belong to E.
 Facet ids: 0..5 are the box faces (x=lo, x=hi, y=lo, y=hi, z=lo, z=hi), then one
 per triangle. Segment ids: 0..11 are the box edges, then the free segments, then
 three per triangle.
+
+Recovered recipe (``free_segments`` + ``plc_with_chains``, the single-mesh
+workloads): the free segments join two input points drawn at random, the
+second among the first's 16 nearest neighbours. A segment is rejected if it
+shares a point with an earlier one or passes within a quarter of the shorter
+length of an earlier one (in 3D two random segments never meet exactly, so
+"crossing" is read as coming that close). Such segments are in general not
+edges of the points' Delaunay mesh: the caller recovers them by inserting
+midpoints (each segment becomes a chain of subsegments). The triangles are
+then drawn among the faces of the recovered Delaunay mesh whose three corners
+are input points touching no other constraint (every angle >= 45 degrees);
+after each triangle, with probability 1/4, a second triangle sharing one of
+its edges is added as a facet of its own when the two meet at a dihedral
+angle of at least 70 degrees, so some interior facets share a segment.
 """
 from __future__ import annotations
 
 import numpy as np
 
+# recipe "delaunay": constraints among the Delaunay edges and faces
+# (plc_from_delaunay); "recovered": free segments recovered by midpoints, then
+# triangles among the recovered mesh's faces (free_segments, plc_with_chains)
 CONFIGS = {
-    "cube2k": dict(kind="cube", n=2000, seed=0, B=2.0, n_seg=0, n_tri=0),
-    "uniform100k": dict(kind="uniform", n=100_000, seed=1, B=1.4, n_seg=1000, n_tri=1000),
-    "clustered500k": dict(kind="clustered", n=500_000, seed=2, B=1.4, n_seg=5000, n_tri=5000),
+    "cube2k": dict(kind="cube", n=2000, seed=0, B=2.0, n_seg=0, n_tri=0, recipe="delaunay"),
+    "uniform100k": dict(kind="uniform", n=100_000, seed=1, B=1.4, n_seg=1000, n_tri=1000,
+                        recipe="recovered"),
+    "clustered500k": dict(kind="clustered", n=500_000, seed=2, B=1.4, n_seg=5000, n_tri=5000,
+                          recipe="recovered"),
 }
 
 
@@ -84,18 +103,9 @@ def _faces_edges(tets: np.ndarray):
     return uf, cnt, ue
 
 
-def plc_from_delaunay(pts: np.ndarray, tets: np.ndarray, n_seg: int, n_tri: int, seed: int,
-                      min_angle: float = 45.0) -> dict:
-    """Constraint labels for a box PLC whose initial CDT is the Delaunay mesh
-    ``tets`` of ``pts`` (8 box corners first)."""
-    pts = np.asarray(pts, dtype=np.float64)
-    if len(pts) >= (1 << 21):
-        raise ValueError("too many points for the face packing")
-    rng = np.random.default_rng(seed + 7919)
+def _box_labels(pts, faces, cnt):
+    """Box facets (hull faces grouped by box face) and the 12 box edges."""
     lo, hi = pts.min(axis=0), pts.max(axis=0)
-    faces, cnt, edges = _faces_edges(tets)
-
-    # box facets: the hull faces, grouped by the box face they lie on
     hull = faces[cnt == 1]
     tris, fids = [], []
     for f in hull:
@@ -117,6 +127,37 @@ def plc_from_delaunay(pts: np.ndarray, tets: np.ndarray, n_seg: int, n_tri: int,
             if not (c >> k) & 1:
                 segs.append((c, c | (1 << k)))
                 sids.append(len(sids))
+    return tris, fids, segs, sids
+
+
+def _angles_ok(P, cosmax):
+    for j in range(3):
+        u = P[(j + 1) % 3] - P[j]
+        v = P[(j + 2) % 3] - P[j]
+        c = np.dot(u, v) / np.sqrt(np.dot(u, u) * np.dot(v, v))
+        if c > cosmax:
+            return False
+    return True
+
+
+def _labels(tris, fids, segs, sids, nf):
+    return dict(segs=np.asarray(segs, dtype=np.int32).reshape(-1, 2),
+                seg_id=np.asarray(sids, dtype=np.int32),
+                tris=np.asarray(tris, dtype=np.int32).reshape(-1, 3),
+                facet_id=np.asarray(fids, dtype=np.int32),
+                nfacets=nf)
+
+
+def plc_from_delaunay(pts: np.ndarray, tets: np.ndarray, n_seg: int, n_tri: int, seed: int,
+                      min_angle: float = 45.0) -> dict:
+    """Constraint labels for a box PLC whose initial CDT is the Delaunay mesh
+    ``tets`` of ``pts`` (8 box corners first)."""
+    pts = np.asarray(pts, dtype=np.float64)
+    if len(pts) >= (1 << 21):
+        raise ValueError("too many points for the face packing")
+    rng = np.random.default_rng(seed + 7919)
+    faces, cnt, edges = _faces_edges(tets)
+    tris, fids, segs, sids = _box_labels(pts, faces, cnt)
     used = np.zeros(len(pts), dtype=bool)
     used[:8] = True
 
@@ -147,15 +188,7 @@ def plc_from_delaunay(pts: np.ndarray, tets: np.ndarray, n_seg: int, n_tri: int,
         f = inner[i]
         if used[f].any():
             continue
-        P = pts[f]
-        ok = True
-        for j in range(3):
-            u = P[(j + 1) % 3] - P[j]
-            v = P[(j + 2) % 3] - P[j]
-            c = np.dot(u, v) / np.sqrt(np.dot(u, u) * np.dot(v, v))
-            if c > cosmax:
-                ok = False
-        if not ok:
+        if not _angles_ok(pts[f], cosmax):
             continue
         used[f] = True
         tris.append(f)
@@ -167,8 +200,164 @@ def plc_from_delaunay(pts: np.ndarray, tets: np.ndarray, n_seg: int, n_tri: int,
         got += 1
     if got < n_tri:
         raise ValueError("not enough well-shaped faces")
-    return dict(segs=np.asarray(segs, dtype=np.int32).reshape(-1, 2),
-                seg_id=np.asarray(sids, dtype=np.int32),
-                tris=np.asarray(tris, dtype=np.int32).reshape(-1, 3),
-                facet_id=np.asarray(fids, dtype=np.int32),
-                nfacets=nf)
+    return _labels(tris, fids, segs, sids, nf)
+
+
+def _seg_dist(p0, p1, Q0, Q1):
+    """Closest distance between segment p0p1 and each segment Q0[i]Q1[i]."""
+    d1 = p1 - p0
+    D2 = Q1 - Q0
+    r = p0 - Q0
+    a = np.dot(d1, d1)
+    e = np.einsum("ij,ij->i", D2, D2)
+    f = np.einsum("ij,ij->i", D2, r)
+    c = r @ d1
+    b = D2 @ d1
+    den = a * e - b * b
+    s = np.where(den > 1e-300, np.clip((b * f - c * e) / np.where(den > 1e-300, den, 1.0), 0, 1),
+                 0.0)
+    t = (b * s + f) / np.where(e > 0, e, 1.0)
+    s = np.where(t < 0, np.clip(-c / a, 0, 1), np.where(t > 1, np.clip((b - c) / a, 0, 1), s))
+    t = np.clip(t, 0, 1)
+    diff = (p0 + s[:, None] * d1) - (Q0 + t[:, None] * D2)
+    return np.sqrt(np.einsum("ij,ij->i", diff, diff))
+
+
+def free_segments(pts: np.ndarray, n_seg: int, seed: int, knn: int = 16,
+                  gap: float = 0.25) -> np.ndarray:
+    """n_seg segments between input points (the recovered recipe above):
+    the first end uniform among the non-corner points, the second among its
+    knn nearest neighbours; rejected if it shares a point with, or passes
+    within gap x the shorter length of, an earlier segment."""
+    from scipy.spatial import cKDTree
+    pts = np.asarray(pts, dtype=np.float64)
+    rng = np.random.default_rng(seed + 104729)
+    tree = cKDTree(pts)
+    used = np.zeros(len(pts), dtype=bool)
+    used[:8] = True
+    A, Bq, L = [], [], []
+    tries = 0
+    while len(A) < n_seg:
+        tries += 1
+        if tries > 50 * n_seg + 1000:
+            raise ValueError("not enough free segments")
+        a = int(rng.integers(8, len(pts)))
+        if used[a]:
+            continue
+        _, nb = tree.query(pts[a], k=knn + 1)
+        b = int(nb[1 + rng.integers(0, knn)])
+        if used[b] or b < 8:
+            continue
+        la = float(np.linalg.norm(pts[b] - pts[a]))
+        if A:
+            P0, P1 = pts[np.asarray(A)], pts[np.asarray(Bq)]
+            d = _seg_dist(pts[a], pts[b], P0, P1)
+            if np.any(d < gap * np.minimum(la, np.asarray(L))):
+                continue
+        used[a] = used[b] = True
+        A.append(a)
+        Bq.append(b)
+        L.append(la)
+    return np.stack([np.asarray(A, dtype=np.int32), np.asarray(Bq, dtype=np.int32)], axis=1)
+
+
+def _dihedral_deg(P, Q, e0, e1):
+    """Angle at edge (e0, e1) between the half-planes through P and Q."""
+    u = e1 - e0
+    u = u / np.linalg.norm(u)
+    a = P - e0
+    b = Q - e0
+    a = a - np.dot(a, u) * u
+    b = b - np.dot(b, u) * u
+    c = np.dot(a, b) / np.sqrt(np.dot(a, a) * np.dot(b, b))
+    return float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
+
+
+def plc_with_chains(xyz: np.ndarray, tets: np.ndarray, chains, n_in: int, n_tri: int, seed: int,
+                    min_angle: float = 45.0, pair_prob: float = 0.25,
+                    min_dihedral: float = 70.0) -> dict:
+    """Constraint labels for the recovered recipe: ``xyz`` holds the n_in input
+    points (8 box corners first) followed by the recovery's midpoints, ``tets``
+    is their Delaunay mesh and ``chains[s]`` the vertex ids along free segment
+    s (each consecutive pair an edge of ``tets``). Adds the box facets and
+    edges, one segment per chain (its subsegments), and n_tri triangles drawn
+    among the faces (some in edge-sharing pairs, see the module notes)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    if len(xyz) >= (1 << 21):
+        raise ValueError("too many points for the face packing")
+    rng = np.random.default_rng(seed + 7919)
+    faces, cnt, edges = _faces_edges(tets)
+    tris, fids, segs, sids = _box_labels(xyz, faces, cnt)
+    used = np.zeros(len(xyz), dtype=bool)
+    used[:8] = True
+    used[n_in:] = True  # recovery midpoints lie on their segments
+    nseg = 12
+    for ch in chains:
+        for k in range(len(ch) - 1):
+            segs.append((int(ch[k]), int(ch[k + 1])))
+            sids.append(nseg)
+        used[np.asarray(ch)] = True
+        nseg += 1
+    inner = faces[cnt == 2]
+    # (edge, apex) of every inner face, sorted by edge key, for the pairs
+    ek = np.concatenate([(inner[:, 0] << 21) | inner[:, 1], (inner[:, 0] << 21) | inner[:, 2],
+                         (inner[:, 1] << 21) | inner[:, 2]])
+    ap = np.concatenate([inner[:, 2], inner[:, 1], inner[:, 0]])
+    srt = np.argsort(ek, kind="stable")
+    ek, ap = ek[srt], ap[srt]
+
+    def apexes(u, v):
+        k = (min(u, v) << 21) | max(u, v)
+        lo_, hi_ = np.searchsorted(ek, k, "left"), np.searchsorted(ek, k, "right")
+        return sorted(int(x) for x in ap[lo_:hi_])
+
+    order = rng.permutation(len(inner))
+    cosmax = np.cos(np.radians(min_angle))
+    got = 0
+    nf = 6
+    for i in order:
+        if got >= n_tri:
+            break
+        f = [int(v) for v in inner[i]]
+        if used[f].any() or not _angles_ok(xyz[f], cosmax):
+            continue
+        used[f] = True
+        tris.append(f)
+        fids.append(nf)
+        nf += 1
+        got += 1
+        for j in range(3):
+            segs.append((f[j], f[(j + 1) % 3]))
+            sids.append(nseg)
+            nseg += 1
+        if got >= n_tri or rng.random() >= pair_prob:
+            continue
+        # a second triangle on one of the edges, a facet of its own: its other
+        # two edges are new segments, the shared edge stays one segment
+        j0 = int(rng.integers(0, 3))
+        for dj in range(3):
+            e0, e1 = f[(j0 + dj) % 3], f[(j0 + dj + 1) % 3]
+            opp = f[(j0 + dj + 2) % 3]
+            g = None
+            for v in apexes(e0, e1):
+                if v == opp or used[v]:
+                    continue
+                if (_angles_ok(xyz[[e0, e1, v]], cosmax) and
+                        _dihedral_deg(xyz[opp], xyz[v], xyz[e0], xyz[e1]) >= min_dihedral):
+                    g = [e0, e1, v]
+                    break
+            if g is None:
+                continue
+            used[g[2]] = True
+            tris.append(g)
+            fids.append(nf)
+            nf += 1
+            got += 1
+            for p_, q_ in ((e1, g[2]), (g[2], e0)):
+                segs.append((p_, q_))
+                sids.append(nseg)
+                nseg += 1
+            break
+    if got < n_tri:
+        raise ValueError("not enough well-shaped faces")
+    return _labels(tris, fids, segs, sids, nf)

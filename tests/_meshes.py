@@ -8,9 +8,21 @@ from paper_1903_03406_gb300 import inputs
 FULL_REASONS = {0, 9, 8, 12}
 
 
-def oracle_case(kind, n, n_seg, n_tri, seed):
-    """Oracle Delaunay mesh of a seeded point set with constraint labels."""
+def oracle_case(kind, n, n_seg, n_tri, seed, recovered=False):
+    """Oracle Delaunay mesh of a seeded point set with constraint labels; with
+    recovered=True, free segments recovered by midpoints (inputs.py's
+    recovered recipe)."""
     pts, _, _ = inputs.box_points(kind, n, seed)
+    if recovered:
+        from oracle.recover import recover_segments
+        segs = inputs.free_segments(pts, n_seg, seed)
+        om, xyz, chains, _ = recover_segments(pts, segs)
+        e = om.export()
+        plc = inputs.plc_with_chains(xyz, e["tets"], chains, len(pts), n_tri, seed)
+        bad = om.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"],
+                                 plc["nfacets"])
+        assert bad == 0
+        return om, e, plc
     om = oracle.Mesh.box_delaunay(pts)
     e = om.export()
     plc = inputs.plc_from_delaunay(pts, e["tets"], n_seg, n_tri, seed)

@@ -31,9 +31,16 @@ def run(name):
     w = inputs.CONFIGS[name]
     pts, _, _ = inputs.box_points(w["kind"], w["n"], w["seed"])
     t0 = time.perf_counter()
-    om = oracle.Mesh.box_delaunay(pts)
-    e = om.export()
-    plc = inputs.plc_from_delaunay(pts, e["tets"], w["n_seg"], w["n_tri"], w["seed"])
+    if w["recipe"] == "recovered":
+        from oracle.recover import recover_segments
+        segs = inputs.free_segments(pts, w["n_seg"], w["seed"])
+        om, xyz, chains, passes = recover_segments(pts, segs)
+        e = om.export()
+        plc = inputs.plc_with_chains(xyz, e["tets"], chains, len(pts), w["n_tri"], w["seed"])
+    else:
+        om = oracle.Mesh.box_delaunay(pts)
+        e = om.export()
+        plc = inputs.plc_from_delaunay(pts, e["tets"], w["n_seg"], w["n_tri"], w["seed"])
     assert om.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"],
                               plc["nfacets"]) == 0
     t_setup = time.perf_counter() - t0
@@ -43,7 +50,8 @@ def run(name):
     c = om.check(w["B"])
     bad = int(c["bad_tets"] + c["bad_tets_unspl"])
     return {
-        "B": w["B"], "points_in": int(len(pts)), "steiner": int(st["inserted"]),
+        "B": w["B"], "points_in": int(len(pts)), "mesh_verts_in": int(len(e["xyz"])),
+        "recipe": w["recipe"], "steiner": int(st["inserted"]),
         "evaluated": int(st["evaluated"]), "tets": int(c["tets"]), "bad_left": bad,
         "bad_frac": bad / c["tets"], "contract_ok": bool(
             c["bad_orient"] == 0 and c["nonlocal_delaunay"] == 0 and c["euler"] == 1

@@ -6,7 +6,7 @@ from paper_1903_03406_gb300 import autotune
 
 def test_coordinate_search_finds_the_best_setting():
     target = {"fused_max": 64, "grow1_blocks_per_sm": 4, "tier2_warps": 1216,
-              "tier1_cavity": 32, "tier1_boundary": 96}
+              "tier1_cavity": 32, "tier1_boundary": 72}
     calls = []
 
     def measure(s):
@@ -52,7 +52,7 @@ def test_save_load_apply(tmp_path):
     p = tmp_path / "t.json"
     assert autotune.load(str(p)) is None
     s = {"fused_max": 32, "grow1_blocks_per_sm": 8, "tier2_warps": 608, "tier1_cavity": 32,
-         "tier1_boundary": 160}
+         "tier1_boundary": 96}
     autotune.save(s, {"note": "x"}, str(p))
     assert autotune.load(str(p)) == s
 

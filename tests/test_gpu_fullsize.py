@@ -31,8 +31,9 @@ from paper_1903_03406_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 CASES = {
-    "uniform100k": dict(kind="uniform", n=100_000, seed=1, B=1.4, ns=1000, nt=1000),
-    "clustered500k": dict(kind="clustered", n=500_000, seed=2, B=1.4, ns=5000, nt=5000),
+    name: dict(kind=w["kind"], n=w["n"], seed=w["seed"], B=w["B"], ns=w["n_seg"], nt=w["n_tri"],
+               recipe=w["recipe"])
+    for name, w in inputs.CONFIGS.items() if name in ("uniform100k", "clustered500k")
 }
 NSAMPLE = 2000
 
@@ -48,7 +49,14 @@ def cdr():
 
 
 def _workload(cdr, w):
+    """The benchmark's initial mesh, built on the GPU as bench.py builds it."""
     pts, lo, hi = inputs.box_points(w["kind"], w["n"], w["seed"])
+    if w["recipe"] == "recovered":
+        from paper_1903_03406_gb300 import recover
+        segs = inputs.free_segments(pts, w["ns"], w["seed"])
+        xyz, tets, chains, _ = recover.recover_segments(pts, segs, cdr)
+        plc = inputs.plc_with_chains(xyz, tets, chains, len(pts), w["nt"], w["seed"])
+        return {"xyz": xyz, "tets": tets}, plc, lo, hi
     dt = cdr.Handle.delaunay_box(pts)
     ex = dt.export()
     dt.close()
@@ -141,16 +149,21 @@ def _check(ex, plc, B, lo, hi, rng):
             continue  # given up (unsplittable): may stay encroached
         for v in ring:
             assert oracle.diametral(xyz[e[0]], xyz[e[1]], xyz[v]) >= 0
-    # every input segment is a chain of subsegments between its endpoints
+    # every input segment is a chain of subsegments between its endpoints (the
+    # ends of the chain it had in the initial mesh)
     segs, sid = plc["segs"], plc["seg_id"]
-    for k in rng.choice(len(segs), size=min(300, len(segs)), replace=False):
-        parts = ss[ss[:, 2] == sid[k]][:, :2]
+
+    def chain_ends(parts):
         deg = {}
         for p, q in parts:
-            deg[p] = deg.get(p, 0) + 1
-            deg[q] = deg.get(q, 0) + 1
-        ends = sorted(v for v, c in deg.items() if c == 1)
-        assert ends == sorted(segs[k].tolist()) and all(c in (1, 2) for c in deg.values())
+            deg[int(p)] = deg.get(int(p), 0) + 1
+            deg[int(q)] = deg.get(int(q), 0) + 1
+        assert all(c in (1, 2) for c in deg.values())
+        return sorted(v for v, c in deg.items() if c == 1)
+
+    for k in rng.choice(np.unique(sid), size=min(300, len(np.unique(sid))), replace=False):
+        ends = chain_ends(ss[ss[:, 2] == k][:, :2])
+        assert len(ends) == 2 and ends == chain_ends(segs[sid == k])
     # quality: the tetrahedra that were not given up are not bad (sampled)
     ok = np.nonzero((tflag & 2) == 0)[0]
     for t in rng.choice(ok, size=min(NSAMPLE, len(ok)), replace=False):
@@ -169,7 +182,7 @@ def test_full_size_refinement_properties(cdr, name):
     # the quality band against the oracle's sequential refinement to the end
     with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_counts.json")) as f:
         ref = json.load(f)[name]
-    assert ref["contract_ok"] and ref["points_in"] == len(ex0["xyz"])
+    assert ref["contract_ok"] and ref["mesh_verts_in"] == len(ex0["xyz"])
     assert st["steiner_inserted"] <= 1.15 * ref["steiner"]
     assert st["n_bad_left"] / len(ex["tets"]) <= 1.15 * ref["bad_frac"]
     _check(ex, plc, w["B"], lo, hi, np.random.default_rng(7))

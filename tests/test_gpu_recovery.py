@@ -1,0 +1,66 @@
+"""Segment recovery on the GPU against the oracle's recovery (needs a GPU).
+
+The GPU recovery (Delaunay meshes built by the library's point-insertion
+rounds, midpoints by its midpoint formula) must give the oracle's recovery bit
+for bit on small inputs: the same points in the same order, the same chains
+and the same tetrahedra. A PLC built on the recovered mesh is then refined in
+lockstep with the oracle's mode R, round by round, to the end.
+"""
+import numpy as np
+import pytest
+
+from _meshes import assert_same_mesh, compare_reports
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cdr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_03406_gb300 import cdr as c
+    c.lib()
+    return c
+
+
+def _canon_tets(t):
+    t = np.sort(np.asarray(t), axis=1)
+    return t[np.lexsort(t.T[::-1])]
+
+
+@pytest.mark.parametrize("kind,n,ns,seed", [("uniform", 3000, 60, 3), ("clustered", 4000, 80, 4),
+                                            ("uniform", 20000, 300, 8)])
+def test_gpu_recovery_equals_oracle(cdr, kind, n, ns, seed):
+    from oracle.recover import recover_segments as oracle_recover
+    from paper_1903_03406_gb300 import inputs, recover
+    pts, _, _ = inputs.box_points(kind, n, seed)
+    segs = inputs.free_segments(pts, ns, seed)
+    xyz, tets, chains, passes = recover.recover_segments(pts, segs, cdr)
+    om, oxyz, ochains, opasses = oracle_recover(pts, segs)
+    assert passes == opasses and passes >= 1
+    assert np.array_equal(xyz, oxyz)
+    assert chains == ochains
+    assert np.array_equal(_canon_tets(tets), _canon_tets(om.export()["tets"]))
+
+
+def test_rounds_lockstep_on_recovered_segments(cdr):
+    """Free segments recovered by midpoints and triangles sharing segments:
+    every round of the GPU equals mode R's, to the end."""
+    from _meshes import oracle_case
+    om, e, plc = oracle_case("uniform", 900, 10, 10, 5, recovered=True)
+    h = cdr.Handle.create(e["xyz"], e["tets"], plc["segs"], plc["seg_id"], plc["tris"],
+                          plc["facet_id"], plc["nfacets"])
+    classes = []
+    for r in range(3000):
+        g = h.round(1.4)
+        o = om.round(1.4)
+        assert g["cls"] == o["cls"], r
+        if g["cls"] < 0:
+            break
+        classes.append(g["cls"])
+        compare_reports(h.round_report(), om.report(), "recovered round %d" % r)
+        assert g["steiner_inserted"] == o["inserted"]
+        assert_same_mesh(h.export(), om.export(), "recovered round %d" % r)
+    assert set(classes) == {0, 1, 2}
+    h.close()
