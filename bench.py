@@ -345,6 +345,7 @@ def gpu_arm(args, rank, world):
                                      if "recovery_passes" in ex else "GPU Delaunay, untimed"),
                        tuning=tuning or "defaults",
                        steiner_per_step=last["steiner_inserted"], rounds_per_step=last["rounds"],
+                       rounds_by_class=last.get("rounds_by_class"),
                        final_tets=last["n_tets"], bad_left=last["n_bad_left"], wall_s=t_wall),
         "e2e": {"value": e2e_ins / e2e_max, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -746,7 +747,7 @@ def main():
                     help="instances of the batched part of the line (0: leave it out)")
     ap.add_argument("--served", type=int, default=40,
                     help="requests of the served part of the line (0: leave it out)")
-    ap.add_argument("--mixed", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--mixed", type=int, default=2, choices=[0, 1, 2],
                     help="round kind: 0 one class per round, 1 every class, "
                          "2 subsegments and subfaces together")
     ap.add_argument("--profile-run", action="store_true",

@@ -942,12 +942,19 @@ struct Ws {
   int* fbv;   // the edge's 2 vertex ids and the facet id
 };
 
+// Open addressing with linear probing and no deletions. A put gives up after
+// kProbe slots (the caller then treats the table as full and grows the region
+// again in a larger one), so every stored key sits within kProbe slots of its
+// home slot, and a lookup can stop after kProbe slots too: a nearly full table
+// never costs a scan of the whole table.
+constexpr int kProbe = 64;
 __device__ __forceinline__ unsigned hs_slot(int t, int cap) {
   return (unsigned)mix64((unsigned long long)(unsigned)t) & (unsigned)(cap - 1);
 }
 __device__ int hs_find(const int* hs, int cap, int t) {
   unsigned h = hs_slot(t, cap);
-  for (int it = 0; it < cap; ++it) {
+  const int np = min(cap, kProbe);
+  for (int it = 0; it < np; ++it) {
     int e = hs[h];
     if (e == -1) return 0;
     if ((e >> 2) == t) return e & 3;
@@ -958,7 +965,8 @@ __device__ int hs_find(const int* hs, int cap, int t) {
 // returns 1 inserted, 0 present (state overwritten when force), -1 full
 __device__ int hs_put(int* hs, int cap, int t, int state, bool force) {
   unsigned h = hs_slot(t, cap);
-  for (int it = 0; it < cap; ++it) {
+  const int np = min(cap, kProbe);
+  for (int it = 0; it < np; ++it) {
     int old = atomicCAS(&hs[h], -1, (t << 2) | state);
     if (old == -1) return 1;
     if ((old >> 2) == t) {
@@ -1006,7 +1014,8 @@ __device__ bool bt_put(int* t, int cap, const int* bv, int cap3, int e, bool uni
   int a, b;
   bt_key(bv, e, cap3, a, b);
   unsigned h = bt_slot(a, b, cap);
-  for (int it = 0; it < cap; ++it) {
+  const int np = min(cap, kProbe);
+  for (int it = 0; it < np; ++it) {
     int old = atomicCAS(&t[h], -1, e);
     if (old == -1) return true;
     if (unique) {
@@ -1024,7 +1033,8 @@ __device__ int bt_find(const int* t, int cap, const int* bv, int cap3, int a, in
                        int* other) {
   unsigned h = bt_slot(a, b, cap);
   int cnt = 0;
-  for (int it = 0; it < cap; ++it) {
+  const int np = min(cap, kProbe);
+  for (int it = 0; it < np; ++it) {
     const int e = t[h];
     if (e == -1) break;
     if (e != self) {
@@ -1055,9 +1065,13 @@ __device__ __forceinline__ void flush_acc(const DevRound& r, const GrowAcc& a, i
 
 // kOnly >= 0: every candidate of the launch has that class (a one-class
 // round), so the code of the other classes is compiled out. -1: any class.
+// hcap: slots of the workspace's hash set / boundary table in use (a power of
+// two, at most hcap; smaller tables are cleared faster). Returns true if a
+// table filled up: the region was then left as OUT_RETRY and can be grown
+// again with a larger table, with the same result.
 template <class C, int kOnly = -1>
-__device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w, int* slab,
-                         int lane, GrowAcc& acc) {
+__device__ bool grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w, int* slab,
+                         int lane, GrowAcc& acc, int hcap = C::HCAP) {
   using L = SlabLayout<C>;
   // Tier 1's cavity and boundary-face capacities can be lowered at run time
   // (a tuning setting; the arrays keep their compile-time size): a region that
@@ -1073,7 +1087,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
     if (lane == 0) {
       slab[0] = slab[1] = slab[2] = slab[3] = 0;
     }
-    return;
+    return false;
   }
   const int elem = r.cand[i];
   const V4 q4 = r.sp[i];
@@ -1090,11 +1104,12 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   bool retry = false;  // tier-1 capacity exceeded
   bool blast = false;  // the region met a higher-priority start (warp-uniform)
   bool cfail = false;  // a closure failure was met (the growth goes on)
+  bool hf = false;     // a hash set or table filled up (this lane)
 
 #ifdef CDR_PHASES
   long long ph_t = clock64();
 #endif
-  for (int k = lane; k < C::HCAP; k += 32) w.hset[k] = -1;
+  for (int k = lane; k < hcap; k += 32) w.hset[k] = -1;
   __syncwarp();
   PHASE(0);
 
@@ -1102,7 +1117,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   if (cls == CLS_TET || cls == CLS_POINT) {
     if (lane == 0) {
       w.cav[0] = r.loc[i];
-      hs_put(w.hset, C::HCAP, r.loc[i], 1, false);
+      hs_put(w.hset, hcap, r.loc[i], 1, false);
     }
     ncav = 1;
     if (seed_blasts(m, r, r.loc[i], i)) {
@@ -1120,7 +1135,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         if (nc < capc) w.cav[nc] = t;
         ++nc;
         if (seed_blasts(m, r, t, i)) bad |= 2;
-        hs_put(w.hset, C::HCAP, t, 1, false);
+        if (hs_put(w.hset, hcap, t, 1, false) < 0) bad |= 4;
         for (int f = 0; f < 4; ++f) {
           int x = vid(geti(rec.v, f));
           if (x == sa || x == sb) continue;
@@ -1142,6 +1157,11 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
     bad = __shfl_sync(FULLMASK, bad, 0);
     if (bad & 2) {
       blast = true;
+      goto done;
+    }
+    if (bad & 4) {  // the ring did not fit the hash set
+      hf = true;
+      retry = true;
       goto done;
     }
     if (bad) {
@@ -1285,8 +1305,8 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           int c = side == 0 ? c0 : c1;
           bool pred = false, bl = false;
           if (c >= 0) {
-            int res = hs_put(w.hset, C::HCAP, c, 1, false);
-            if (res < 0) retry = true;
+            int res = hs_put(w.hset, hcap, c, 1, false);
+            if (res < 0) retry = hf = true;
             pred = res == 1;
             bl = seed_blasts(m, r, c, i);
           }
@@ -1324,7 +1344,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
             (void)CKI(t, m.nT);
             if (nb >= 0 && !face_sub(rec.v, f)) {
               int nt = nb >> 2;
-              if (hs_find(w.hset, C::HCAP, nt) == 0 && orient_rep(m, rec, f, p) > 0) cand = nt;
+              if (hs_find(w.hset, hcap, nt) == 0 && orient_rep(m, rec, f, p) > 0) cand = nt;
             }
           }
           unsigned grp = __match_any_sync(FULLMASK, cand);
@@ -1333,8 +1353,8 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           if (leader) {
             bool in = tet_in_sphere(m, ld_tet(m, cand), p);
             ++ntested;
-            int res = hs_put(w.hset, C::HCAP, cand, in ? 1 : 2, false);
-            if (res < 0) retry = true;
+            int res = hs_put(w.hset, hcap, cand, in ? 1 : 2, false);
+            if (res < 0) retry = hf = true;
             add = in && res == 1;
             bl = add && seed_blasts(m, r, cand, i);
           }
@@ -1369,7 +1389,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           CKL(nb, m.nT);
           bool sub = face_sub(rec.v, f);
           bool removed = kFacets && sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
-          bool interior = !sub && nb >= 0 && hs_find(w.hset, C::HCAP, nb >> 2) == 1;
+          bool interior = !sub && nb >= 0 && hs_find(w.hset, hcap, nb >> 2) == 1;
           pred = !removed && !interior;
           if (pred && orient_rep(m, rec, f, p) <= 0) {
             if (sub || nb < 0) f_ = true;
@@ -1403,8 +1423,8 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         bool add = false, bl = false;
         if (leader) {
           // (a tet tested out before has its state forced to in)
-          int res = hs_put(w.hset, C::HCAP, cand, 1, true);
-          if (res < 0) retry = true;
+          int res = hs_put(w.hset, hcap, cand, 1, true);
+          if (res < 0) retry = hf = true;
           add = true;
           bl = seed_blasts(m, r, cand, i);
         }
@@ -1443,7 +1463,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           int nb = geti(rec.n, f);
           bool sub = face_sub(rec.v, f);
           bool removed = kFacets && sub && nf > 0 && in_list(w.fcav, nf, ts_ptr(m, t)[f]);
-          bool interior = !sub && nb >= 0 && hs_find(w.hset, C::HCAP, nb >> 2) == 1;
+          bool interior = !sub && nb >= 0 && hs_find(w.hset, hcap, nb >> 2) == 1;
           pred = !removed && !interior;
           bi = (t << 2) | f;
           bo = nb;
@@ -1496,15 +1516,15 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   // ------------------------------------------------ boundary table
   // (the tet set's storage: growth is done)
   {
-    for (int k = lane; k < C::HCAP; k += 32) w.hset[k] = -1;
+    for (int k = lane; k < hcap; k += 32) w.hset[k] = -1;
     __syncwarp();
     bool full = false;
     for (int it = lane; it < 3 * nbnd; it += 32) {
-      full |= !bt_put(w.hset, C::HCAP, w.bv, C::CAP3, it, false);
-      full |= !bt_put(w.hset, C::HCAP, w.bv, C::CAP3, C::CAP3 + it, true);
+      full |= !bt_put(w.hset, hcap, w.bv, C::CAP3, it, false);
+      full |= !bt_put(w.hset, hcap, w.bv, C::CAP3, C::CAP3 + it, true);
     }
-    if (__any_sync(FULLMASK, full)) {  // cannot happen within the caps; be safe
-      retry = true;
+    if (__any_sync(FULLMASK, full)) {  // the table is too small for this region
+      retry = hf = true;
       goto done;
     }
     __syncwarp();
@@ -1519,7 +1539,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       bool miss = false;
       if (it < items) {
         int v = vid(geti(m.T[CKI(w.cav[it >> 2], m.capT)].v, it & 3));
-        miss = !bt_find(w.hset, C::HCAP, w.bv, C::CAP3, v, v, -1, nullptr);
+        miss = !bt_find(w.hset, hcap, w.bv, C::CAP3, v, v, -1, nullptr);
       }
       lost = __any_sync(FULLMASK, miss);
     }
@@ -1529,7 +1549,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       bool miss = false;
       if (it < nfb) {
         int u = w.fbv[3 * it], x = w.fbv[3 * it + 1];
-        miss = !bt_find(w.hset, C::HCAP, w.bv, C::CAP3, min(u, x), max(u, x), -1, nullptr);
+        miss = !bt_find(w.hset, hcap, w.bv, C::CAP3, min(u, x), max(u, x), -1, nullptr);
       }
       lost = __any_sync(FULLMASK, miss);
     }
@@ -1550,7 +1570,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
     for (int it = lane; it < items; it += 32) {
       int a, b, other = -1;
       bt_key(w.bv, it, C::CAP3, a, b);
-      int cnt = bt_find(w.hset, C::HCAP, w.bv, C::CAP3, a, b, it, &other);
+      int cnt = bt_find(w.hset, hcap, w.bv, C::CAP3, a, b, it, &other);
       topo |= cnt > 1;
       slab[L::OFF_PART + it] = cnt == 1 ? other : -1;
     }
@@ -1663,7 +1683,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
           if (!split) {
             bool enc = false;
             if (cls == CLS_TET || cls == CLS_SUBFACE) enc = diametral(vtx(m, u), vtx(m, x), p) < 0;
-            if (!enc) enc = !bt_find(w.hset, C::HCAP, w.bv, C::CAP3, min(u, x), max(u, x), -1, nullptr);
+            if (!enc) enc = !bt_find(w.hset, hcap, w.bv, C::CAP3, min(u, x), max(u, x), -1, nullptr);
             if (enc) {
               int g = hash_lookup(m, ekey(u, x));
               if (g >= 0) {
@@ -1707,6 +1727,7 @@ __device__ void grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   PHASE(8);  // marks
 done:
   __syncwarp();
+  const bool hfull = __any_sync(FULLMASK, hf);
   for (int o = 16; o > 0; o >>= 1) ntested += __shfl_xor_sync(FULLMASK, ntested, o);
   acc.tested += (unsigned long long)ntested;
   if (!retry) {
@@ -1718,14 +1739,14 @@ done:
       set_status(r, i, OUT_BLASTED, RS_NONE);
       slab[0] = slab[1] = slab[2] = slab[3] = 0;
     }
-    return;
+    return false;
   }
   if (retry) {
     if (lane == 0) {
       set_status(r, i, OUT_RETRY, RS_NONE);
       slab[0] = slab[1] = slab[2] = slab[3] = 0;
     }
-    return;
+    return hfull;
   }
   if (lane == 0) {
     set_status(r, i, outcome, reason);
@@ -1752,6 +1773,20 @@ done:
     // the cavity is complete: keep its tets for the round report
     if (w.cav != slab + L::OFF_CAV)
       for (int k = lane; k < min(ncav, capc); k += 32) slab[L::OFF_CAV + k] = w.cav[k];
+  }
+  return false;
+}
+
+// Tier-2 growth of candidate i: the hash set / boundary table starts at 32,768
+// slots (enough for a region at the cavity limit) and is enlarged to
+// Tier2::HCAP only when a region's boundary table fills it, so that most
+// regions clear a quarter of the workspace, and are grown once.
+__device__ void grow_tier2(const DevMesh& m, const DevRound& r, int i, const Ws& w, int* slab,
+                           int lane, GrowAcc& acc) {
+  for (int hcap = 32768;; hcap = min(hcap * 4, Tier2::HCAP)) {
+    const bool full = grow_one<Tier2>(m, r, i, w, slab, lane, acc, hcap);
+    __syncwarp();
+    if (!full || hcap >= Tier2::HCAP) break;
   }
 }
 
@@ -1806,7 +1841,7 @@ __global__ void k_grow2(DevMesh m, DevRound r) {
     int* slab = r.slab2 + (size_t)j * L::STRIDE;
     Ws w{slab + L::OFF_CAV, extra, slab + L::OFF_BIN, slab + L::OFF_BOUT,
          slab + L::OFF_BV, slab + L::OFF_FCAV, slab + L::OFF_FBND, slab + L::OFF_FBV};
-    grow_one<Tier2>(m, r, i, w, slab, lane, acc);
+    grow_tier2(m, r, i, w, slab, lane, acc);
     __syncwarp();
     if (lane == 0 && r.status[i] == OUT_RETRY) set_status(r, i, OUT_UNSPL, RS_OVERFLOW);
   }
@@ -2721,7 +2756,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 1) k_round_fused(DevMesh m, 
     Ws w2{slab + L::OFF_CAV, r.ws2 + (size_t)warp * Tier2::HCAP, slab + L::OFF_BIN,
           slab + L::OFF_BOUT, slab + L::OFF_BV, slab + L::OFF_FCAV, slab + L::OFF_FBND,
           slab + L::OFF_FBV};
-    grow_one<Tier2>(m, r, i, w2, slab, lane, acc);
+    grow_tier2(m, r, i, w2, slab, lane, acc);
     __syncwarp();
     if (lane == 0) {
       if (r.status[i] == OUT_RETRY) set_status(r, i, OUT_UNSPL, RS_OVERFLOW);
@@ -2777,14 +2812,18 @@ void launch_round_fused(const DevMesh& m, const DevRound& r, int* hint, int4* of
     attr = true;
   }
   if (r.n <= 0) return;
+  // as many blocks (a power of two, at most kFusedBlocks) as the round has
+  // warps' worth of candidates: a small round synchronises fewer SMs
+  int blocks = 1;
+  while (blocks < kFusedBlocks && blocks * kFusedWarps < r.n) blocks <<= 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kFusedBlocks, 1, 1);
+  cfg.gridDim = dim3(blocks, 1, 1);
   cfg.blockDim = dim3(32 * kFusedWarps, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kFusedBlocks;
+  at[0].val.clusterDim.x = blocks;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;

@@ -64,10 +64,15 @@ def _workload(cdr, w):
     return ex, plc, lo, hi
 
 
-def _handle(cdr, ex, plc):
+# round kind per workload: the benchmark's (subsegments and subfaces together)
+# on the clustered one, one class per round on the uniform one
+MIXED = {"clustered500k": 2, "uniform100k": 0}
+
+
+def _handle(cdr, ex, plc, mixed=0):
     from paper_1903_03406_gb300 import autotune
     h = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
-                          plc["facet_id"], plc["nfacets"])
+                          plc["facet_id"], plc["nfacets"], mixed_rounds=mixed)
     autotune.apply(h, autotune.load())
     return h
 
@@ -174,7 +179,7 @@ def _check(ex, plc, B, lo, hi, rng):
 def test_full_size_refinement_properties(cdr, name):
     w = CASES[name]
     ex0, plc, lo, hi = _workload(cdr, w)
-    h = _handle(cdr, ex0, plc)
+    h = _handle(cdr, ex0, plc, MIXED[name])
     st = h.refine(w["B"])
     assert st["status"] == 0 and st["steiner_inserted"] > w["n"]
     ex = h.export()

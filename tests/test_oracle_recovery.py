@@ -6,9 +6,9 @@ oracle's own code:
 * every subsegment of a recovered chain is an edge of the final mesh, found by
   brute force over its tetrahedra, and the final mesh is Delaunay (empty
   circumspheres by brute force on a small case);
-* the chains are midpoint subdivisions: every vertex lies on its segment at a
-  dyadic parameter k / 2^d, in increasing order, at the exact rational
-  midpoint of its neighbours at that depth (rounded to FP64);
+* the chains are midpoint subdivisions: every inserted vertex is the exact
+  rational midpoint of the two vertices it split, rounded to FP64, and the
+  vertices come in increasing order along the segment;
 * a segment that is not an edge of the points' Delaunay mesh is split; a
   segment whose closed diametral ball holds no other point (a Gabriel edge,
   hence an edge of every Delaunay mesh of these points) is not;
@@ -54,11 +54,9 @@ def test_recovered_chains_are_midpoint_subdivisions_and_mesh_edges(kind, n, ns, 
         for u, v in zip(ch[:-1], ch[1:]):
             assert (min(u, v), max(u, v)) in E
         split += len(ch) > 2
-        A, Bv = [Fraction(float(x)) for x in xyz[a]], [Fraction(float(x)) for x in xyz[b]]
-        # dyadic depth of each vertex: rebuild the subdivision tree from the
-        # chain and check each midpoint exactly (one FP64 rounding per
-        # coordinate of the exact midpoint of its parents)
-        depth = {0: (0, 1), len(ch) - 1: (1, 1)}  # index -> (k, 2^d)
+        # rebuild the subdivision tree from the chain and check each midpoint
+        # exactly (one FP64 rounding per coordinate of the exact midpoint of
+        # the two vertices it split)
         stack = [(0, len(ch) - 1)]
         while stack:
             i, j = stack.pop()
@@ -108,13 +106,13 @@ def test_recovered_mesh_is_delaunay_by_brute_force():
 
 def test_recovered_recipe_meets_the_contract_and_refines_within_the_band():
     B = 1.4
-    pts, _, _ = inputs.box_points("uniform", 1500, 5)
-    segs = inputs.free_segments(pts, 15, 5)
+    pts, _, _ = inputs.box_points("uniform", 900, 5)
+    segs = inputs.free_segments(pts, 10, 5)
     runs = []
     for mode in ("R", "S"):
         m, xyz, chains, _ = recover_segments(pts, segs)
         e = m.export()
-        plc = inputs.plc_with_chains(xyz, e["tets"], chains, len(pts), 15, 5)
+        plc = inputs.plc_with_chains(xyz, e["tets"], chains, len(pts), 10, 5)
         assert m.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"],
                                  plc["nfacets"]) == 0
         c = m.check(B)
