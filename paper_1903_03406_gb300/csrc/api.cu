@@ -67,6 +67,7 @@ struct cdr_handle {
   int npts = 0;
   // last round, for the report
   int lastN = 0, lastCls = -1, lastN2 = 0;
+  SlabOff lastS1 = slab_off<Tier1>();  // tier-1 slab layout of the last round
   // profiling: events around each kernel group, accumulated per round
   bool prof = false;
   bool profGrowOnly = false;  // time the region-growth groups only
@@ -366,7 +367,7 @@ __global__ void k_report_sizes(DevRound r, int* ncav, int* nbnd, int* nfcav) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += gridDim.x * blockDim.x) {
     int j = r.slab2_of ? r.slab2_of[i] : -1;
     const int* slab = j >= 0 ? r.slab2 + (size_t)j * SlabLayout<Tier2>::STRIDE
-                             : r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
+                             : r.slab1 + (size_t)i * r.s1.STRIDE;
     int st = r.status[i];
     int oc = st & 0xff, rs = (st >> 8) & 0xff;
     bool full = oc == OUT_OK || (oc == OUT_REJECT && rs == RS_ENCROACH) || rs == RS_GUARD ||
@@ -459,7 +460,9 @@ bool ensure_round(cdr_handle* h, int n) {
             ensure(h, h->bSp, (size_t)c * sizeof(V4)) && ensure(h, h->bLoc, (size_t)c * 4) &&
             ensure(h, h->bStatus, (size_t)c * 4) && ensure(h, h->bSurv, (size_t)c * 4) &&
             ensure(h, h->bCounts, (size_t)c * 16) && ensure(h, h->bOffs, (size_t)(c + 1) * 16) &&
-            ensure(h, h->bSlab1, (size_t)c * SlabLayout<Tier1>::STRIDE * 4) &&
+            ensure(h, h->bSlab1,
+                   (size_t)c * std::max(SlabLayout<Tier1>::STRIDE, SlabLayout<Tier1Big>::STRIDE) *
+                       4) &&
             ensure(h, h->bSlab2of, (size_t)c * 4) && ensure(h, h->bList2, (size_t)c * 4) &&
             ensure(h, h->bCkey, (size_t)c * 16) && ensure(h, h->bStats, 32 * 8) &&
             ensure(h, h->bErr, 64) && ensure(h, h->bI32, (size_t)(c + 1) * 4) &&
@@ -474,6 +477,7 @@ DevRound make_round(cdr_handle* h, int cls, int n, double B) {
   r.n = n;
   r.t1cav = h->tier1Cav;
   r.t1bnd = h->tier1Bnd;
+  r.s1 = slab_off<Tier1>();
   r.cand = ptr<int>(h->bCand2);
   r.given = ptr<double>(h->bPts);
   r.loc = ptr<int>(h->bLoc);
@@ -670,6 +674,7 @@ int round_fused(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unso
   h->lastN = n;
   h->lastN2 = fo.n2;
   h->lastCls = cls;
+  h->lastS1 = slab_off<Tier1>();
   if (ro) {
     ro->cls = cls;
     ro->cand = n;
@@ -732,6 +737,8 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsor
     h->prof_ctr[15] += 1;
   }
   r.epoch = next_epoch(h);
+  r.s1 = slab1_layout(grow1_tets_only(r));
+  h->lastS1 = r.s1;
   pmark(h, PG_GROW1, 0);
   launch_grow1(m, r, h->grow1PerSM, s);
   pmark(h, PG_GROW1, 1);
@@ -815,6 +822,7 @@ int round_core(cdr_handle* h, int cls, int n, double B, RoundOut* ro, bool unsor
   r = make_round(h, cls, n, B);  // rebind after any reallocation
   r.epoch = 0;
   r.n2 = h->lastN2;
+  r.s1 = h->lastS1;  // the layout growth wrote its slabs in
   pmark(h, PG_INSERT, 0);
   launch_insert(m, r, ptr<int>(h->bHint), s);
   pmark(h, PG_INSERT, 1);
@@ -1498,6 +1506,7 @@ int cdr_round_report(cdr_handle* h, int32_t* n_cand, int64_t* n_cav_total, int32
   if (n == 0) return CDR_OK;
   DevRound r = make_round(h, h->lastCls, n, 0.0);
   r.n2 = h->lastN2;
+  r.s1 = h->lastS1;
   Buf b;
   if (!ensure(h, b, (size_t)n * 12 + 64)) return CDR_ERR_OOM;
   int* dn = ptr<int>(b);

@@ -924,9 +924,18 @@ static __device__ unsigned long long g_phase[2][16];
       ph_t = t_;                                              \
     }                                                         \
   } while (0)
+// why a tier-1 region moved to tier 2 (diagnostic build): 10 cavity cap, 11
+// boundary-face cap, 12 facet caps, 13 a table filled up
+#define RETRY_NOTE(k)                                       \
+  do {                                                      \
+    if (C::HCAP <= Tier1Big::HCAP && lane == 0) atomicAdd(&g_phase[0][k], 1ULL); \
+  } while (0)
 #else
 #define PHASE(k) \
   do {           \
+  } while (0)
+#define RETRY_NOTE(k) \
+  do {                \
   } while (0)
 #endif
 
@@ -1076,7 +1085,7 @@ __device__ bool grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
   // Tier 1's cavity and boundary-face capacities can be lowered at run time
   // (a tuning setting; the arrays keep their compile-time size): a region that
   // outgrows them is re-run in tier 2, so the result does not change.
-  constexpr bool kTier1 = C::CAPC == Tier1::CAPC && C::HCAP == Tier1::HCAP;
+  constexpr bool kTier1 = C::HCAP <= Tier1Big::HCAP;  // Tier1 or Tier1Big
   const int capc = kTier1 && r.t1cav > 0 ? min(r.t1cav, C::CAPC) : C::CAPC;
   const int capb = kTier1 && r.t1bnd > 0 ? min(r.t1bnd, C::CAPB) : C::CAPB;
   // tetrahedra only: no facet part, no subsegment ring
@@ -1170,6 +1179,7 @@ __device__ bool grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
       goto done;
     }
     if (nc > capc || nfl > C::CAPF) {
+      RETRY_NOTE(nc > capc ? 10 : 12);
       retry = true;
       goto done;
     }
@@ -1209,6 +1219,7 @@ __device__ bool grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         if (nf > C::CAPF) break;
       }
       if (nf > C::CAPF) {
+        RETRY_NOTE(12);
         retry = true;
         goto done;
       }
@@ -1281,6 +1292,7 @@ __device__ bool grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
         nfb += __popc(bal);
       }
       if (nfb > C::CAPFB) {
+        RETRY_NOTE(12);
         retry = true;
         goto done;
       }
@@ -1489,6 +1501,7 @@ __device__ bool grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
     }
     __syncwarp();  // the lists written above are read by other lanes below
     if (nbnd > capb) {
+      RETRY_NOTE(11);
       retry = true;
       goto done;
     }
@@ -1728,6 +1741,8 @@ __device__ bool grow_one(const DevMesh& m, const DevRound& r, int i, const Ws& w
 done:
   __syncwarp();
   const bool hfull = __any_sync(FULLMASK, hf);
+  if (retry && hfull) RETRY_NOTE(13);
+  else if (retry && ncav > capc) RETRY_NOTE(10);
   for (int o = 16; o > 0; o >>= 1) ntested += __shfl_xor_sync(FULLMASK, ntested, o);
   acc.tested += (unsigned long long)ntested;
   if (!retry) {
@@ -1792,16 +1807,19 @@ __device__ void grow_tier2(const DevMesh& m, const DevRound& r, int i, const Ws&
 
 // tier 1: shared-memory workspaces, one per warp
 constexpr int kWarps1 = 8;
-struct Smem1 {
-  int cav[Tier1::CAPC];
-  int hset[Tier1::HCAP];
-  int bin[Tier1::CAPB];
-  int bout[Tier1::CAPB];
-  int bv[3 * Tier1::CAPB];
-  int fcav[Tier1::CAPF];
-  int fbnd[Tier1::CAPFB];
-  int fbv[3 * Tier1::CAPFB];
+template <class C>
+struct SmemT {
+  int cav[C::CAPC];
+  int hset[C::HCAP];
+  int bin[C::CAPB];
+  int bout[C::CAPB];
+  int bv[3 * C::CAPB];
+  int fcav[C::CAPF];
+  int fbnd[C::CAPFB];
+  int fbv[3 * C::CAPFB];
 };
+using Smem1 = SmemT<Tier1>;
+using Smem1Big = SmemT<Tier1Big>;
 
 // blocks per SM the register budget is sized for (build-time, CDR_G1_MINB)
 #ifndef CDR_G1_MINB
@@ -1819,6 +1837,29 @@ __global__ void __launch_bounds__(32 * kWarps1, CDR_G1_MINB) k_grow1(DevMesh m, 
   for (int i = warp; i < r.n; i += nw) {
     int* slab = r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
     grow_one<Tier1, kOnly>(m, r, i, w, slab, lane, acc);
+    __syncwarp();
+    if (lane == 0 && r.rflag) r.rflag[i] = r.status[i] == OUT_RETRY ? 1 : 0;
+  }
+  flush_acc(r, acc, lane);
+}
+
+// tier 1 of rounds with boundary or mixed candidates: larger workspaces, four
+// warps per block
+#ifndef CDR_W1BIG
+#define CDR_W1BIG 4
+#endif
+constexpr int kWarps1Big = CDR_W1BIG;
+__global__ void __launch_bounds__(32 * kWarps1Big, 3) k_grow1big(DevMesh m, DevRound r) {
+  extern __shared__ int smraw[];
+  Smem1Big* sm = reinterpret_cast<Smem1Big*>(smraw) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  Ws w{sm->cav, sm->hset, sm->bin, sm->bout, sm->bv, sm->fcav, sm->fbnd, sm->fbv};
+  int warp = blockIdx.x * kWarps1Big + (threadIdx.x >> 5);
+  int nw = gridDim.x * kWarps1Big;
+  GrowAcc acc;
+  for (int i = warp; i < r.n; i += nw) {
+    int* slab = r.slab1 + (size_t)i * SlabLayout<Tier1Big>::STRIDE;
+    grow_one<Tier1Big>(m, r, i, w, slab, lane, acc);
     __syncwarp();
     if (lane == 0 && r.rflag) r.rflag[i] = r.status[i] == OUT_RETRY ? 1 : 0;
   }
@@ -1853,7 +1894,7 @@ __device__ __forceinline__ const int* slab_of(const DevRound& r, int i, bool& ti
   int j = r.slab2_of ? r.slab2_of[i] : -1;
   tier2 = j >= 0;
   if (tier2) return r.slab2 + (size_t)j * SlabLayout<Tier2>::STRIDE;
-  return r.slab1 + (size_t)i * SlabLayout<Tier1>::STRIDE;
+  return r.slab1 + (size_t)i * r.s1.STRIDE;
 }
 
 // Selection (the "blast" step of Sec. 2): a region is kept if it holds every
@@ -1862,10 +1903,10 @@ __device__ bool holds_marks(const DevMesh& m, const DevRound& r, int i, int lane
   bool t2;
   const int* slab = slab_of(r, i, t2);
   int ncav = slab[0], nbnd = slab[1], nf = slab[2], nfb = slab[3];
-  int offC = t2 ? SlabLayout<Tier2>::OFF_CAV : SlabLayout<Tier1>::OFF_CAV;
-  int offBO = t2 ? SlabLayout<Tier2>::OFF_BOUT : SlabLayout<Tier1>::OFF_BOUT;
-  int offF = t2 ? SlabLayout<Tier2>::OFF_FCAV : SlabLayout<Tier1>::OFF_FCAV;
-  int offFB = t2 ? SlabLayout<Tier2>::OFF_FBND : SlabLayout<Tier1>::OFF_FBND;
+  int offC = t2 ? SlabLayout<Tier2>::OFF_CAV : r.s1.OFF_CAV;
+  int offBO = t2 ? SlabLayout<Tier2>::OFF_BOUT : r.s1.OFF_BOUT;
+  int offF = t2 ? SlabLayout<Tier2>::OFF_FCAV : r.s1.OFF_FCAV;
+  int offFB = t2 ? SlabLayout<Tier2>::OFF_FBND : r.s1.OFF_FBND;
   const unsigned long long mk = (r.epoch << 32) | (unsigned long long)(unsigned)i;
   bool lost = false;
   for (int k = lane; k < ncav; k += 32) lost |= m.Tmark[CKI(slab[offC + k], m.capT)] != mk;
@@ -1958,7 +1999,7 @@ __device__ void insert_one(const DevMesh& m, const DevRound& r, int* hint, int i
   if (!r.survived[i]) return;
   bool t2;
   const int* slab = slab_of(r, i, t2);
-#define SLAB_OFF(name) (t2 ? SlabLayout<Tier2>::name : SlabLayout<Tier1>::name)
+#define SLAB_OFF(name) (t2 ? SlabLayout<Tier2>::name : r.s1.name)
   const int ncav = slab[0], nbnd = slab[1], nf = slab[2], nfb = slab[3];
   const int* cav = slab + SLAB_OFF(OFF_CAV);
   const int* bin = slab + SLAB_OFF(OFF_BIN);
@@ -2423,7 +2464,7 @@ __global__ void k_report_cav(DevMesh m, DevRound r, const int* offs, int4* out) 
     bool t2;
     const int* slab = slab_of(r, i, t2);
     int n = offs[i + 1] - offs[i];
-    const int* cav = slab + (t2 ? SlabLayout<Tier2>::OFF_CAV : SlabLayout<Tier1>::OFF_CAV);
+    const int* cav = slab + (t2 ? SlabLayout<Tier2>::OFF_CAV : r.s1.OFF_CAV);
     for (int k = 0; k < n; ++k) {
       int4 v = m.T[CKI(cav[k], m.capT)].v;
       int s[4] = {vid(v.x), vid(v.y), vid(v.z), vid(v.w)};
@@ -2509,11 +2550,25 @@ void launch_grow1(const DevMesh& m, const DevRound& r, int blocks_per_sm, cudaSt
   }
   long blocks = ((long)r.n + kWarps1 - 1) / kWarps1;
   if (blocks > 152L * blocks_per_sm) blocks = 152L * blocks_per_sm;
-  // a round of bad tetrahedra alone runs the tetrahedron-only growth
-  if (r.cls == CLS_TET && !r.ccls)
+  // a round of bad tetrahedra alone runs the tetrahedron-only growth; other
+  // rounds the larger workspaces (the host set r.s1 to match: slab1_layout)
+  if (grow1_tets_only(r)) {
     k_grow1<CLS_TET><<<(int)blocks, 32 * kWarps1, smem, s>>>(m, r);
-  else
-    k_grow1<-1><<<(int)blocks, 32 * kWarps1, smem, s>>>(m, r);
+    return;
+  }
+  static bool attr_big = false;
+  const size_t smem_big = sizeof(Smem1Big) * kWarps1Big;
+  if (!attr_big) {
+    cudaFuncSetAttribute(k_grow1big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_big);
+    attr_big = true;
+  }
+  long bb = ((long)r.n + kWarps1Big - 1) / kWarps1Big;
+  if (bb > 152L * 2 * blocks_per_sm) bb = 152L * 2 * blocks_per_sm;
+  k_grow1big<<<(int)bb, 32 * kWarps1Big, smem_big, s>>>(m, r);
+}
+bool grow1_tets_only(const DevRound& r) { return r.cls == CLS_TET && !r.ccls; }
+SlabOff slab1_layout(bool tets_only) {
+  return tets_only ? slab_off<Tier1>() : slab_off<Tier1Big>();
 }
 void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s) {
   if (r.n2 <= 0 || r.nws2 <= 0) return;

@@ -48,6 +48,10 @@ void launch_split(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_locate(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s);
 void launch_seed(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_grow1(const DevMesh& m, const DevRound& r, int blocks_per_sm, cudaStream_t s);
+// does the separately launched tier-1 growth of this round use the
+// tetrahedron-only kernel (Tier1 slabs) rather than the larger one (Tier1Big)
+bool grow1_tets_only(const DevRound& r);
+SlabOff slab1_layout(bool tets_only);
 void launch_grow2(const DevMesh& m, const DevRound& r, int nwarps, cudaStream_t s);
 void launch_select(const DevMesh& m, const DevRound& r, cudaStream_t s);
 void launch_insert(const DevMesh& m, const DevRound& r, int* hint, cudaStream_t s);

@@ -138,6 +138,20 @@ struct Caps {
 #define CDR_T1_HCAP 512
 #endif
 using Tier1 = Caps<64, CDR_T1_CAPB, 32, 48, CDR_T1_HCAP>;
+// Tier 1 of rounds with subsegment, subface or mixed candidates: their regions
+// (a subsegment's midpoint, a facet part) are larger than a bad tetrahedron's,
+// so their workspaces hold twice the cavity and three times the boundary, in
+// blocks of fewer warps.
+#ifndef CDR_T1BIG_CAV
+#define CDR_T1BIG_CAV 128
+#endif
+#ifndef CDR_T1BIG_BND
+#define CDR_T1BIG_BND 288
+#endif
+#ifndef CDR_T1BIG_HCAP
+#define CDR_T1BIG_HCAP 2048
+#endif
+using Tier1Big = Caps<CDR_T1BIG_CAV, CDR_T1BIG_BND, 64, 96, CDR_T1BIG_HCAP>;
 using Tier2 = Caps<4096, 16384, 8192, 24576, 131072>;
 constexpr int kCavLimit = 4096;
 
@@ -156,6 +170,18 @@ struct SlabLayout {
                                                            // other face's edge (3 k + q), or -1
   static constexpr int STRIDE = OFF_PART + 3 * C::CAPB;
 };
+
+// Offsets of a tier-1 slab's lists (the layout of the workspace caps the
+// round's growth kernel used), read by selection, insertion and the report.
+struct SlabOff {
+  int OFF_CAV, OFF_BIN, OFF_BOUT, OFF_FCAV, OFF_FBND, OFF_BV, OFF_FBV, OFF_PART, STRIDE;
+};
+template <class C>
+inline SlabOff slab_off() {
+  using L = SlabLayout<C>;
+  return SlabOff{L::OFF_CAV,  L::OFF_BIN, L::OFF_BOUT, L::OFF_FCAV, L::OFF_FBND,
+                 L::OFF_BV,   L::OFF_FBV, L::OFF_PART, L::STRIDE};
+}
 
 struct DevRound {
   int cls;
@@ -190,6 +216,7 @@ struct DevRound {
   int* rflag;                  // per candidate: 1 if its region needs tier 2
   int t1cav, t1bnd;            // tier-1 cavity / boundary-face capacities in use
                                // (0: the compile-time Tier1 sizes)
+  SlabOff s1;                  // layout of the tier-1 slabs (Tier1 or Tier1Big)
 };
 
 // device counters
