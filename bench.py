@@ -226,7 +226,7 @@ def gpu_arm(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cdr.lib()
-    tuning = autotune.load()  # the tuner's stored launch setting, if any
+    tuning = autotune.load(kind="plain")  # the tuner's single-mesh setting, if any
     stream = torch.cuda.current_stream()
     w = WORKLOADS[args.workload]
     B = w["B"]
@@ -662,7 +662,7 @@ def profile_run(args):
     h = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
                           plc["facet_id"], plc["nfacets"], mixed_rounds=args.mixed,
                           allocator=cdr.TorchAllocator(), stream=stream)
-    autotune.apply(h, autotune.load())
+    autotune.apply(h, autotune.load(kind="plain"))
     h.checkpoint()
     cands = []
     while len(cands) < MAX_ROUNDS:

@@ -13,8 +13,12 @@ that the choice is not made inside the run-to-run noise. The chosen setting is
 stored as JSON beside this module (`tuning.json`) and applied with `apply`.
 
     python -m paper_1903_03406_gb300.autotune [--instances 16] [--out PATH]
+    python -m paper_1903_03406_gb300.autotune --plain clustered500k
 
-tunes on a sample of the batched workload (unit-cube PLCs, 1k-50k points).
+The first tunes on a sample of the batched workload (unit-cube PLCs, 1k-50k
+points) and stores the setting of batches and serving ("batched"); the second
+times whole refinements of a single-mesh workload and stores the setting of
+single meshes ("plain"). Each kind keeps its own entry in the file.
 """
 from __future__ import annotations
 
@@ -78,18 +82,40 @@ def search(measure, space=None, start=None, passes=2):
     return best, _stats(best_ts)[0], trials
 
 
-def save(setting, info=None, path=DEFAULT_PATH):
-    with open(path, "w") as f:
-        json.dump({"setting": setting, "info": info or {}}, f, indent=1)
+KINDS = ("batched", "plain")
 
 
-def load(path=DEFAULT_PATH):
-    """The stored setting, or None."""
+def _read(path):
     try:
         with open(path) as f:
-            return json.load(f)["setting"]
-    except (OSError, ValueError, KeyError):
-        return None
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save(setting, info=None, path=DEFAULT_PATH, kind="batched"):
+    """Store the setting of one kind (batched or plain), keeping the other's."""
+    d = _read(path)
+    settings = d.get("settings", {})
+    infos = d.get("info", {})
+    if "setting" in d:  # a file written before settings were kept per kind
+        settings.setdefault("batched", d["setting"])
+        infos = {"batched": infos}
+    settings[kind] = setting
+    infos[kind] = info or {}
+    with open(path, "w") as f:
+        json.dump({"settings": settings, "info": infos}, f, indent=1)
+
+
+def load(path=DEFAULT_PATH, kind="batched"):
+    """The stored setting of a kind (batched: batches and serving; plain: one
+    mesh), or None."""
+    d = _read(path)
+    if "settings" in d:
+        return d["settings"].get(kind)
+    if kind == "batched":
+        return d.get("setting")
+    return None
 
 
 def apply(obj, setting):
@@ -120,14 +146,64 @@ def _batch_measure(cdr, insts, allocator, stream, repeat=REPEAT):
     return measure
 
 
+def _plain_measure(cdr, name, stream, repeat=REPEAT, mixed=2):
+    """Whole refinements of the single-mesh workload `name` (its initial mesh
+    built once, restored before each refinement)."""
+    import torch
+    from paper_1903_03406_gb300 import inputs, recover
+    w = inputs.CONFIGS[name]
+    pts, _, _ = inputs.box_points(w["kind"], w["n"], w["seed"])
+    if w["recipe"] == "recovered":
+        segs = inputs.free_segments(pts, w["n_seg"], w["seed"])
+        xyz, tets, chains, _ = recover.recover_segments(pts, segs, cdr, stream=stream)
+        plc = inputs.plc_with_chains(xyz, tets, chains, len(pts), w["n_tri"], w["seed"])
+    else:
+        dt = cdr.Handle.delaunay_box(pts, stream=stream)
+        ex = dt.export()
+        dt.close()
+        xyz, tets = ex["xyz"], ex["tets"]
+        plc = inputs.plc_from_delaunay(pts, tets, w["n_seg"], w["n_tri"], w["seed"])
+    h = cdr.Handle.create(xyz, tets, plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"],
+                          plc["nfacets"], mixed_rounds=mixed, allocator=cdr.TorchAllocator(),
+                          stream=stream)
+    h.checkpoint()
+
+    def measure(setting):
+        apply(h, dict(DEFAULTS, **(setting or {})))
+        times = []
+        for _ in range(repeat):
+            h.restore()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.refine(w["B"])
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        return times
+    return measure
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--instances", type=int, default=16)
     ap.add_argument("--seed", type=int, default=4242)
     ap.add_argument("--out", default=DEFAULT_PATH)
+    ap.add_argument("--plain", default=None,
+                    help="tune single-mesh refinement on this workload (e.g. clustered500k)")
     args = ap.parse_args()
     import torch
     from paper_1903_03406_gb300 import cdr, workloads
+    if args.plain:
+        cdr.lib()
+        stream = torch.cuda.current_stream()
+        measure = _plain_measure(cdr, args.plain, stream)
+        measure(DEFAULTS)  # warm-up
+        best, t, trials = search(measure)
+        save(best, {"workload": args.plain + " (whole refinements, boundary-mixed rounds)",
+                    "seconds": t, "timings_per_setting": REPEAT,
+                    "trials": [[s_, med, spread] for s_, med, spread in trials]},
+             args.out, kind="plain")
+        print(json.dumps({"kind": "plain", "setting": best, "seconds": t, "trials": len(trials)}))
+        return
     cdr.lib()
     stream = torch.cuda.current_stream()
     spec = dict(workloads.MULTI["batched64"], count=args.instances, seed=args.seed)
@@ -137,7 +213,8 @@ def main():
     best, t, trials = search(measure)
     save(best, {"workload": "batched sample of %d instances (seed %d)" % (args.instances, args.seed),
                 "seconds": t, "timings_per_setting": REPEAT,
-                "trials": [[s, med, spread] for s, med, spread in trials]}, args.out)
+                "trials": [[s, med, spread] for s, med, spread in trials]}, args.out,
+         kind="batched")
     print(json.dumps({"setting": best, "seconds": t, "trials": len(trials)}))
 
 

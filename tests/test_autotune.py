@@ -65,3 +65,21 @@ def test_save_load_apply(tmp_path):
     assert o.kw == s
     autotune.apply(o, None)  # nothing stored: nothing applied
     assert o.kw == s
+
+
+def test_settings_are_kept_per_kind(tmp_path):
+    """Batches and single meshes keep separate settings; a file in the older
+    one-setting form reads as the batched setting."""
+    p = str(tmp_path / "t.json")
+    a = dict(autotune.DEFAULTS, tier1_cavity=32)
+    b = dict(autotune.DEFAULTS, grow1_blocks_per_sm=16)
+    autotune.save(a, {"w": "batched"}, p, kind="batched")
+    autotune.save(b, {"w": "plain"}, p, kind="plain")
+    assert autotune.load(p, kind="batched") == a and autotune.load(p, kind="plain") == b
+    import json
+    with open(p, "w") as f:
+        json.dump({"setting": a, "info": {}}, f)
+    assert autotune.load(p) == a and autotune.load(p, kind="plain") is None
+    autotune.save(b, None, p, kind="plain")
+    assert autotune.load(p) == a and autotune.load(p, kind="plain") == b
+

@@ -73,7 +73,7 @@ def _handle(cdr, ex, plc, mixed=0):
     from paper_1903_03406_gb300 import autotune
     h = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
                           plc["facet_id"], plc["nfacets"], mixed_rounds=mixed)
-    autotune.apply(h, autotune.load())
+    autotune.apply(h, autotune.load(kind="plain"))
     return h
 
 
