@@ -178,11 +178,17 @@ def _incircle2(a, b, c, p):
 
 
 def _check_facet_cavities(snap, rep):
-    """Box facets only (the mesh stays Delaunay and every facet point lies
-    exactly in its facet's plane). Returns (candidates checked, equal)."""
+    """Axis-parallel facets only (every point on such a facet lies exactly in
+    its plane: midpoints and in-facet circumcentres keep the shared
+    coordinate). Returns (candidates checked, equal)."""
     xyz = snap["xyz"]
     sf = [tuple(sorted(int(v) for v in f[:3])) for f in snap["sf"]]
     fid = {k: int(f[3]) for k, f in zip(sf, snap["sf"])}
+    axis_of = {}
+    for k in sf:
+        for ax in range(3):
+            if xyz[k[0]][ax] == xyz[k[1]][ax] == xyz[k[2]][ax]:
+                axis_of.setdefault(fid[k], ax)
     segs = {tuple(sorted(int(v) for v in g[:2])) for g in snap["ss"]}
     edge2sf = {}
     for k in sf:
@@ -202,7 +208,7 @@ def _check_facet_cavities(snap, rep):
             facets = {fid[s] for s in edge2sf.get(key, [])}
         region = set()
         for F in facets:
-            ax = F // 2
+            ax = axis_of[F]
             keep = [k for k in range(3) if k != ax]
             P = {}
 
@@ -271,3 +277,54 @@ def test_facet_cavities_are_bowyer_watson_regions():
             same += b
     assert seen == {0: 6, 1: 6}
     assert n > 40 and same == n
+
+
+def _quad_case():
+    """The unit cube and a quad facet in the plane z = 0.5 given as two
+    triangles, with its diagonal declared a segment (a segment inside a
+    facet, as a PLC allows). Cloud points are kept off the two triangles'
+    equatorial balls so that both triangles are faces of the Delaunay mesh."""
+    corners = np.array([[float((c >> k) & 1) for k in range(3)] for c in range(8)])
+    quad = np.array([[0.2, 0.2, 0.5], [0.8, 0.25, 0.5], [0.75, 0.8, 0.5], [0.25, 0.7, 0.5]])
+    rng = np.random.default_rng(3)
+    cloud = rng.uniform(0.02, 0.98, size=(1500, 3))
+    for tri in ([0, 1, 3], [1, 2, 3]):
+        c, ok = oracle.tri_circumcenter(*quad[tri])
+        r = np.linalg.norm(quad[tri[0]] - c)
+        cloud = cloud[np.linalg.norm(cloud - c, axis=1) > 1.1 * r]
+    pts = np.concatenate([corners, quad, cloud])
+    m = oracle.Mesh.box_delaunay(pts)
+    e = m.export()
+    from paper_1903_03406_gb300 import inputs
+    faces, cnt, _ = inputs._faces_edges(e["tets"])
+    tris, fids, segs, sids = inputs._box_labels(pts, faces, cnt)
+    a, b, c, d = 8, 9, 10, 11
+    tris += [[a, b, d], [b, c, d]]
+    fids += [6, 6]
+    for u, v in ((a, b), (b, c), (c, d), (d, a), (b, d)):  # (b, d) lies inside the facet
+        segs.append((u, v))
+        sids.append(len(sids))
+    assert m.set_constraints(np.array(segs), np.array(sids), np.array(tris), np.array(fids),
+                             7) == 0
+    return m
+
+
+def test_facet_cavities_do_not_cross_a_segment_inside_the_facet():
+    """A facet region is grown across the facet's edges but never across a
+    subsegment, here the diagonal segment inside a quad facet: by brute force,
+    the same facet parts as the oracle's, on the first subface and subsegment
+    rounds of the refinement."""
+    m = _quad_case()
+    n = same = checked = 0
+    for _ in range(400):
+        snap = m.export()
+        cls = m.round(2.0)["cls"]
+        if cls < 0 or checked >= 12:
+            break
+        if cls in (0, 1):
+            a, b = _check_facet_cavities(snap, m.report())
+            n += a
+            same += b
+            checked += 1
+    assert n > 20 and same == n
+
