@@ -612,6 +612,9 @@ def cpu_sample(om, B, seconds):
 def reference_arm(args, rank, world):
     if rank != 0:
         return None
+    if args.workload not in WORKLOADS:
+        return {"impl": "reference", "unavailable": "the reference arm times single-mesh "
+                "workloads only; %s is not one" % args.workload}
     w = WORKLOADS[args.workload]
     om, e, plc = oracle_workload(args.workload)
     import oracle
@@ -698,6 +701,73 @@ def profile_run(args):
     h.close()
 
 
+# ----------------------------------------------------------- Table-1-like sweep
+TABLE1 = os.path.join(ROOT, "tests", "golden", "paper_table1.json")
+
+
+def table1_arm(args, rank, world):
+    """A Table-1-like sweep (paper Table 1: 25K points of a ball distribution
+    plus gamma x 25K polygons, mainly rectangles, for several B): 25,000
+    points uniform in a ball, gamma x 25,000 axis-parallel rectangles as facets
+    (their corners added as points), each (gamma, B) refined once on the GPU.
+    Points, tetrahedra, bad tetrahedra left, time and the dihedral-angle
+    histogram are reported beside the paper's gQM3D figures, as context."""
+    import torch
+    from paper_1903_03406_gb300 import autotune, cdr, inputs, quality
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cdr.lib()
+    stream = torch.cuda.current_stream()
+    with open(TABLE1) as f:
+        paper = {(r["B"], r["gamma"]): r for r in json.load(f)["rows"]}
+    tuning = autotune.load(kind="plain")
+    pts, _, _ = inputs.box_points("ball", 25000, 7 + rank)
+    rows = []
+    for g in args.gammas:
+        rect = inputs.rectangles(pts, int(round(g * 25000)), 7 + rank)
+        xyz = np.ascontiguousarray(np.concatenate([pts, rect.reshape(-1, 3)]))
+        dt = cdr.Handle.delaunay_box(xyz, stream=stream)
+        ex = dt.export()
+        dt.close()
+        plc = inputs.plc_rectangles(ex["xyz"], ex["tets"], len(pts), len(rect))
+        h = cdr.Handle.create(ex["xyz"], ex["tets"], plc["segs"], plc["seg_id"], plc["tris"],
+                              plc["facet_id"], plc["nfacets"], mixed_rounds=args.mixed,
+                              allocator=cdr.TorchAllocator(), stream=stream)
+        autotune.apply(h, tuning)
+        h.checkpoint()
+        for B in args.Bs:
+            h.restore()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = h.refine(B, MAX_ROUNDS)
+            torch.cuda.synchronize()
+            dt_s = time.perf_counter() - t0
+            out = h.export()
+            q = quality.report(out["xyz"], out["tets"], B)
+            p = paper.get((B, g))
+            rows.append({
+                "gamma": g, "B": B, "input_points": int(len(xyz)), "rectangles": int(len(rect)),
+                "points_M": st["n_verts"] / 1e6, "tets_M": st["n_tets"] / 1e6,
+                "bad_tets": st["n_bad_left"], "seconds": dt_s, "rounds": st["rounds"],
+                "steiner_per_s": st["steiner_inserted"] / dt_s,
+                "dihedral_hist": q.get("dihedral_hist"), "dihedral_min_deg": q.get("dihedral_min_deg"),
+                "paper_gQM3D": ({"points_M": p["points_M"]["gQM3D"], "tets_M": p["tets_M"]["gQM3D"],
+                                 "bad_tets": p["bad_tets"]["gQM3D"], "minutes": p["minutes"]["gQM3D"]}
+                                if p else None)})
+            log("table1 gamma %.2f B %.1f: %.2fM points, %.2fM tets, %d bad, %.2fs" %
+                (g, B, st["n_verts"] / 1e6, st["n_tets"] / 1e6, st["n_bad_left"], dt_s))
+        h.close()
+    if rank != 0:
+        return None
+    return {"metric": "Table-1-like sweep (context: the paper's gQM3D figures beside)",
+            "value": sum(r["steiner_per_s"] for r in rows) / len(rows), "unit": "Steiner points/s",
+            "n_gpus": world, "steps": 1, "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "table1", "points": 25000, "distribution": "uniform in a ball",
+                       "polygons": "axis-parallel rectangles, gamma x 25,000",
+                       "tuning": tuning or "defaults"},
+            "rows": rows}
+
+
 def _cpu_baseline_job(name, seconds):
     """The plain workload's CPU baseline, in a spawned process: the oracle's
     sequential refinement of the same input for about `seconds`; its initial
@@ -739,7 +809,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     from paper_1903_03406_gb300 import workloads
     ap.add_argument("--workload", default="clustered500k",
-                    choices=sorted(WORKLOADS) + sorted(workloads.MULTI))
+                    choices=sorted(WORKLOADS) + sorted(workloads.MULTI) + ["table1"])
+    ap.add_argument("--gammas", type=float, nargs="+", default=[0.05, 0.10, 0.15, 0.20, 0.25],
+                    help="table1: polygons per input point")
+    ap.add_argument("--Bs", type=float, nargs="+", default=[1.4, 1.6, 1.8, 2.0],
+                    help="table1: radius-edge bounds")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -768,6 +842,11 @@ def main():
             print(json.dumps(line), flush=True)
         return
     plain = args.workload not in workloads.MULTI
+    if args.workload == "table1":
+        line = table1_arm(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -81,6 +81,12 @@ def box_points(kind: str, n: int, seed: int) -> tuple[np.ndarray, float, float]:
             ok = np.all((x > lo) & (x < hi), axis=1)
             out = np.concatenate([out, x[ok]])
         inner = out[:n]
+    elif kind == "ball":
+        # uniform in the ball of radius 450 about the box centre
+        lo, hi = 0.0, 1000.0
+        d = rng.normal(size=(n, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        inner = 500.0 + 450.0 * d * rng.uniform(0.0, 1.0, size=(n, 1)) ** (1.0 / 3.0)
     else:
         raise ValueError(kind)
     corners = np.array([[hi if (c >> k) & 1 else lo for k in range(3)] for c in range(8)],
@@ -361,3 +367,110 @@ def plc_with_chains(xyz: np.ndarray, tets: np.ndarray, chains, n_in: int, n_tri:
     if got < n_tri:
         raise ValueError("not enough well-shaped faces")
     return _labels(tris, fids, segs, sids, nf)
+
+
+def rectangles(pts: np.ndarray, count: int, seed: int, tries: int = 50) -> np.ndarray:
+    """count rectangles for a Table-1-like PLC (the paper's polygons are
+    "mainly rectangles"): near random input points, parallel to a random pair
+    of axes, with sides of 0.3 to 0.6 times the distance from the point to its
+    nearest neighbour. A rectangle is kept when no point (input or corner of an
+    earlier rectangle) lies within 1.05 times its circumradius of its centre,
+    and none of its corners lies that close to an earlier rectangle's centre,
+    so that its four corners, which lie on one circle, span faces of the
+    Delaunay mesh. Returns the corners, (count, 4, 3), in order around the
+    rectangle."""
+    from scipy.spatial import cKDTree
+    pts = np.asarray(pts, dtype=np.float64)
+    rng = np.random.default_rng(seed + 65537)
+    tree = cKDTree(pts)
+    dnn, _ = tree.query(pts, k=2)
+    out, centres, radii = [], [], []
+    old_corners = old_centres = None  # trees of the rectangles before `recent`
+    recent = 0  # rectangles accepted since the trees were built
+    rmax = 0.0
+    attempts = 0
+    while len(out) < count:
+        attempts += 1
+        if attempts > tries * count + 1000:
+            raise ValueError("not enough room for %d rectangles" % count)
+        i = int(rng.integers(8, len(pts)))
+        s0 = dnn[i, 1]
+        a_, b_ = rng.uniform(0.3, 0.6, size=2) * s0
+        c = pts[i] + 0.5 * s0 * rng.normal(size=3) / np.sqrt(3.0)
+        # axis-parallel, so that the corners share coordinates exactly: they are
+        # exactly coplanar and exactly on one circle
+        k = int(rng.integers(0, 3))
+        k1, k2 = (k + 1) % 3, (k + 2) % 3
+        q = np.empty((4, 3))
+        q[:, k] = c[k]
+        q[:, k1] = [c[k1] - a_ / 2, c[k1] + a_ / 2, c[k1] + a_ / 2, c[k1] - a_ / 2]
+        q[:, k2] = [c[k2] - b_ / 2, c[k2] - b_ / 2, c[k2] + b_ / 2, c[k2] + b_ / 2]
+        if np.any(q <= 0.0) or np.any(q >= 1000.0):
+            continue
+        c = q.mean(axis=0)
+        R = 0.5 * np.linalg.norm(q[2] - q[0])
+        if tree.query_ball_point(c, 1.05 * R):
+            continue
+        n_old = len(out) - recent
+        if old_corners is not None and old_corners.query_ball_point(c, 1.05 * R):
+            continue
+        if recent and np.any(np.linalg.norm(np.concatenate(out[n_old:]) - c, axis=1) < 1.05 * R):
+            continue
+        # no corner inside an earlier rectangle's sphere
+        bad = False
+        if old_centres is not None:
+            for j in set(sum(old_centres.query_ball_point(q, 1.05 * rmax), [])):
+                if np.any(np.linalg.norm(q - centres[j], axis=1) < 1.05 * radii[j]):
+                    bad = True
+                    break
+        for j in range(n_old, len(out)):
+            if bad:
+                break
+            bad = np.any(np.linalg.norm(q - centres[j], axis=1) < 1.05 * radii[j])
+        if bad:
+            continue
+        out.append(q)
+        centres.append(c)
+        radii.append(R)
+        rmax = max(rmax, R)
+        recent += 1
+        if recent == 256:
+            old_corners = cKDTree(np.concatenate(out))
+            old_centres = cKDTree(np.asarray(centres))
+            recent = 0
+    return np.asarray(out)
+
+
+def plc_rectangles(xyz: np.ndarray, tets: np.ndarray, n_in: int, n_rect: int) -> dict:
+    """Labels for the box PLC plus rectangles whose corners are xyz[n_in:]
+    (four per rectangle, in order): each rectangle is a facet made of the two
+    faces of ``tets`` on its corners (whichever diagonal the Delaunay mesh of
+    the cocircular corners has; the diagonal is not a segment), and its four
+    sides are segments."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    faces, cnt, edges = _faces_edges(tets)
+    tris, fids, segs, sids = _box_labels(xyz, faces, cnt)
+    inner = faces[cnt == 2]
+    key = (inner[:, 0] << 42) | (inner[:, 1] << 21) | inner[:, 2]
+    srt = np.sort(key)
+    nf = 6
+    for r in range(n_rect):
+        c = [n_in + 4 * r + k for k in range(4)]
+        found = []
+        for tri in ((c[0], c[1], c[2]), (c[0], c[2], c[3]), (c[0], c[1], c[3]), (c[1], c[2], c[3])):
+            t = sorted(tri)
+            k = (t[0] << 42) | (t[1] << 21) | t[2]
+            j = np.searchsorted(srt, k)
+            if j < len(srt) and srt[j] == k:
+                found.append(t)
+        if len(found) != 2:
+            raise ValueError("rectangle %d is not two faces of the mesh" % r)
+        for t in found:
+            tris.append(t)
+            fids.append(nf)
+        for k in range(4):
+            segs.append((c[k], c[(k + 1) % 4]))
+            sids.append(len(sids))
+        nf += 1
+    return _labels(tris, fids, segs, sids, nf)
+

@@ -4,7 +4,8 @@ The GPU recovery (Delaunay meshes built by the library's point-insertion
 rounds, midpoints by its midpoint formula) must give the oracle's recovery bit
 for bit on small inputs: the same points in the same order, the same chains
 and the same tetrahedra. A PLC built on the recovered mesh is then refined in
-lockstep with the oracle's mode R, round by round, to the end.
+lockstep with the oracle's mode R, round by round, to the end; so is a PLC of
+the Table-1-like recipe (a ball of points with rectangles).
 """
 import numpy as np
 import pytest
@@ -62,5 +63,45 @@ def test_rounds_lockstep_on_recovered_segments(cdr):
         compare_reports(h.round_report(), om.report(), "recovered round %d" % r)
         assert g["steiner_inserted"] == o["inserted"]
         assert_same_mesh(h.export(), om.export(), "recovered round %d" % r)
+    assert set(classes) == {0, 1, 2}
+    h.close()
+
+
+def test_rounds_lockstep_ball_with_rectangles(cdr):
+    """The Table-1-like recipe (points in a ball, axis-parallel rectangles whose
+    corners lie on one circle): the initial Delaunay mesh built on the GPU is a
+    valid Delaunay mesh of the same points (four cocircular, coplanar corners
+    have two Delaunay triangulations, so it need not be the oracle's), and from
+    the oracle's mesh every round equals mode R's, to the end."""
+    import oracle
+    from paper_1903_03406_gb300 import inputs
+    pts, _, _ = inputs.box_points("ball", 1500, 6)
+    rect = inputs.rectangles(pts, 50, 6)
+    xyz = np.concatenate([pts, rect.reshape(-1, 3)])
+    om = oracle.Mesh.box_delaunay(xyz)
+    e = om.export()
+    dt = cdr.Handle.delaunay_box(xyz)
+    ge = dt.export()
+    dt.close()
+    assert dt.skipped == 0 and np.array_equal(ge["xyz"], xyz)
+    c = oracle.Mesh.create(ge["xyz"], ge["tets"]).check(1.6)
+    assert c["bad_orient"] == 0 and c["nonlocal_delaunay"] == 0 and c["euler"] == 1
+    assert abs(c["vol_rel_err"]) < 1e-12
+    plc = inputs.plc_rectangles(e["xyz"], e["tets"], len(pts), len(rect))
+    assert om.set_constraints(plc["segs"], plc["seg_id"], plc["tris"], plc["facet_id"],
+                              plc["nfacets"]) == 0
+    h = cdr.Handle.create(e["xyz"], e["tets"], plc["segs"], plc["seg_id"], plc["tris"],
+                          plc["facet_id"], plc["nfacets"])
+    classes = []
+    for r in range(3000):
+        g = h.round(1.6)
+        o = om.round(1.6)
+        assert g["cls"] == o["cls"], r
+        if g["cls"] < 0:
+            break
+        classes.append(g["cls"])
+        compare_reports(h.round_report(), om.report(), "rectangles round %d" % r)
+        assert g["steiner_inserted"] == o["inserted"]
+        assert_same_mesh(h.export(), om.export(), "rectangles round %d" % r)
     assert set(classes) == {0, 1, 2}
     h.close()
