@@ -6,10 +6,13 @@ on the device and restored at the start of the step) to the end.
 
 Workload (default, the largest single-GPU configuration): 500,000 points drawn
 from a mixture of 3 isotropic Gaussians (sigma 50) in [0,1000]^3 plus the 8 box
-corners, 5,000 segments and 5,000 triangles inside the box (constraints chosen
-among the Delaunay edges and faces; seed 2), B = 1.4. The initial Delaunay mesh
-is built on the GPU by the library's point-insertion rounds (untimed set-up).
-`--workload uniform100k` runs the 100,000-point uniform configuration instead.
+corners, 5,000 segments between nearby points and 5,000 triangles inside the
+box (seed 2), B = 1.4, subsegments and subfaces split in the same rounds. The
+segments that are not Delaunay edges are recovered by midpoints and the
+triangles drawn among the recovered mesh's faces; the initial Delaunay meshes
+are built on the GPU by the library's point-insertion rounds (untimed set-up).
+`--workload uniform100k` runs the 100,000-point uniform configuration instead,
+`--workload table1` a sweep shaped like the paper's Table 1.
 
 The line also carries:
 * quality_band: the final Steiner count and fraction of bad tetrahedra against
