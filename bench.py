@@ -12,7 +12,9 @@ segments that are not Delaunay edges are recovered by midpoints and the
 triangles drawn among the recovered mesh's faces; the initial Delaunay meshes
 are built on the GPU by the library's point-insertion rounds (untimed set-up).
 `--workload uniform100k` runs the 100,000-point uniform configuration instead,
-`--workload table1` a sweep shaped like the paper's Table 1.
+`--workload table1` a sweep shaped like the paper's Table 1, and
+`--workload handoff` the gQM3D+ hand-off (a CPU stage for the first k
+insertions, then the GPU rounds) against the GPU rounds from the start.
 
 The line also carries:
 * quality_band: the final Steiner count and fraction of bad tetrahedra against
@@ -771,6 +773,176 @@ def table1_arm(args, rank, world):
             "rows": rows}
 
 
+# ------------------------------------------------- gQM3D+ hand-off (Sec. 3)
+def handoff_labels(e):
+    """cdr_create arguments from an exported oracle mesh: its subsegments and
+    subfaces become the constraint labels, its per-facet reference points the
+    facet references (so the GPU continues with the same in-facet predicate)."""
+    ss, sf = np.asarray(e["ss"]), np.asarray(e["sf"])
+    return dict(xyz=np.ascontiguousarray(e["xyz"]), tets=np.ascontiguousarray(e["tets"]),
+                segs=np.ascontiguousarray(ss[:, :2]), seg_id=np.ascontiguousarray(ss[:, 2]),
+                tris=np.ascontiguousarray(sf[:, :3]), facet_id=np.ascontiguousarray(sf[:, 3]),
+                nfacets=int(len(e["facetq"])), facet_ref=np.ascontiguousarray(e["facetq"]))
+
+
+def _handoff_cpu_job(name, ks, seconds):
+    """The CPU stage of the hand-off, in a spawned process: the oracle's
+    sequential refinement of the workload, snapshotted (exported) after k
+    insertions for every k in ks it reaches within `seconds` of refinement.
+    Returns [(k, cumulative refinement seconds, labels)], k = 0 first."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    om, _, _ = oracle_workload(name)
+    B = WORKLOADS[name]["B"]
+    out = [(0, 0.0, handoff_labels(om.export()))]
+    done, t, ended = 0, 0.0, False
+    for k in sorted(ks):
+        if ended or t >= seconds:
+            break
+        while done < k:  # a step may refuse its point instead of inserting it
+            t0 = time.perf_counter()
+            st = om.refine_S(B, k - done)
+            t += time.perf_counter() - t0
+            done += st["inserted"]
+            if st["steps"] < k - done + st["inserted"]:
+                ended = True  # the refinement finished first
+                break
+        if not ended:
+            out.append((done, t, handoff_labels(om.export())))
+    return out
+
+
+def handoff_arm(args, rank, world):
+    """gQM3D+ (Sec. 3) replaces the initial part of the computation with a CPU
+    program. Measured here: a sequential CPU refiner (the oracle's sequential
+    refinement stands in for it) makes the first k insertions, the mesh is
+    handed to the library through cdr_create, and the GPU rounds finish it;
+    against the GPU rounds from the start. Also the GPU's own time for its
+    first k insertions (round by round), beside the CPU's."""
+    if rank != 0:
+        return None
+    import multiprocessing as mp
+    import torch
+    from paper_1903_03406_gb300 import autotune, cdr
+    name = args.handoff_of
+    w = WORKLOADS[name]
+    B = w["B"]
+    log("hand-off: the CPU stage (sequential refinement of %s, up to %.0f s)" %
+        (name, args.cpu_seconds))
+    with mp.get_context("spawn").Pool(1) as pool:
+        snaps = pool.apply(_handoff_cpu_job, (name, args.handoff_k, args.cpu_seconds))
+    torch.cuda.set_device(0)
+    cdr.lib()
+    stream = torch.cuda.current_stream()
+    tuning = autotune.load(kind="plain")
+    al = cdr.TorchAllocator()
+
+    def create(lab):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = cdr.Handle.create(lab["xyz"], lab["tets"], lab["segs"], lab["seg_id"], lab["tris"],
+                              lab["facet_id"], lab["nfacets"], facet_ref=lab["facet_ref"],
+                              mixed_rounds=args.mixed, allocator=al, stream=stream)
+        autotune.apply(h, tuning)
+        torch.cuda.synchronize()
+        return h, time.perf_counter() - t0
+
+    # the GPU from the start: whole refinements, then one round by round
+    h, t_create0 = create(snaps[0][2])
+    h.checkpoint()
+    for _ in range(args.warmup):
+        h.restore()
+        h.refine(B, MAX_ROUNDS)
+    times = []
+    for _ in range(args.steps):
+        h.restore()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st0 = h.refine(B, MAX_ROUNDS)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t_gpu_all = statistics.median(times)
+    h.restore()
+    torch.cuda.synchronize()
+    timeline = []  # (cumulative insertions, cumulative seconds) after each round
+    ins, t = 0, 0.0
+    by = {}  # (class, candidate bucket) -> [rounds, seconds, insertions]
+    while len(timeline) < MAX_ROUNDS:
+        t0 = time.perf_counter()
+        r = h.round(B)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        t += dt
+        if r["cls"] < 0:
+            break
+        ins += r["steiner_inserted"]
+        timeline.append((ins, t))
+        c = r["candidates"]
+        bucket = next(b for b in (128, 1000, 10000, 100000, 1 << 62) if c <= b)
+        acc = by.setdefault((r["cls"], bucket), [0, 0.0, 0])
+        acc[0] += 1
+        acc[1] += dt
+        acc[2] += r["steiner_inserted"]
+    h.close()
+    cls_name = {0: "subsegments", 1: "subfaces", 2: "tetrahedra", 3: "mixed"}
+    round_profile = [{"class": cls_name.get(c, str(c)), "candidates_up_to": b, "rounds": v[0],
+                      "seconds": v[1], "inserted": v[2]} for (c, b), v in sorted(by.items())]
+
+    def gpu_first(k):
+        for n, s in timeline:
+            if n >= k:
+                return s
+        return None
+
+    rows = []
+    for k, t_cpu, lab in snaps:
+        if k == 0:
+            rows.append({"k": 0, "cpu_s": 0.0, "handoff_s": t_create0, "gpu_rest_s": t_gpu_all,
+                         "total_s": t_create0 + t_gpu_all, "steiner": st0["steiner_inserted"],
+                         "bad_left": st0["n_bad_left"], "tets": st0["n_tets"]})
+            continue
+        hk, t_create = create(lab)
+        hk.checkpoint()
+        rest = []
+        for j in range(max(1, min(args.steps, 3))):
+            hk.restore()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = hk.refine(B, MAX_ROUNDS)
+            torch.cuda.synchronize()
+            rest.append(time.perf_counter() - t0)
+        hk.close()
+        g = gpu_first(k)
+        rows.append({"k": k, "cpu_s": t_cpu, "cpu_rate": k / t_cpu if t_cpu > 0 else None,
+                     "gpu_first_k_s": g, "gpu_first_k_rate": k / g if g else None,
+                     "handoff_s": t_create, "gpu_rest_s": statistics.median(rest),
+                     "total_s": t_cpu + t_create + statistics.median(rest),
+                     "steiner": k + st["steiner_inserted"], "bad_left": st["n_bad_left"],
+                     "tets": st["n_tets"]})
+        log("hand-off k=%d: CPU %.2f s, create %.3f s, GPU rest %.3f s (GPU alone: first k "
+            "in %s s)" % (k, t_cpu, t_create, statistics.median(rest),
+                          "%.3f" % g if g else "-"))
+    base = rows[0]["total_s"]
+    better = [r["k"] for r in rows[1:] if r["total_s"] < base]
+    return {"metric": "gQM3D+ hand-off: CPU refinement of the first k insertions, then the GPU "
+                      "rounds (Sec. 3)",
+            "value": base, "unit": "s (GPU rounds from the start, create included)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(argparse.Namespace(workload=name, mixed=args.mixed),
+                                           1),
+                           cpu_stage="the oracle's sequential refinement, one host core",
+                           initial_mesh="the oracle's Delaunay mesh and segment recovery",
+                           tuning=tuning or "defaults"),
+            "rows": rows, "gpu_rounds": len(timeline),
+            "gpu_round_profile": {"timing": "host clock around each cdr_round (one "
+                                            "synchronisation per round)",
+                                  "seconds": t, "by_class_and_size": round_profile},
+            "crossover_k": min(better) if better else None,
+            "crossover": ("the hand-off is faster from k = %d" % min(better)) if better else
+                         "none: at every k measured the GPU rounds from the start finish first"}
+
+
 def _cpu_baseline_job(name, seconds):
     """The plain workload's CPU baseline, in a spawned process: the oracle's
     sequential refinement of the same input for about `seconds`; its initial
@@ -812,12 +984,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     from paper_1903_03406_gb300 import workloads
     ap.add_argument("--workload", default="clustered500k",
-                    choices=sorted(WORKLOADS) + sorted(workloads.MULTI) + ["table1"])
+                    choices=sorted(WORKLOADS) + sorted(workloads.MULTI) + ["table1", "handoff"])
     ap.add_argument("--gammas", type=float, nargs="+", default=[0.05, 0.10, 0.15, 0.20, 0.25],
                     help="table1: polygons per input point")
     ap.add_argument("--Bs", type=float, nargs="+", default=[1.4, 1.6, 1.8, 2.0],
                     help="table1: radius-edge bounds")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--handoff-of", default="clustered500k", choices=sorted(WORKLOADS),
+                    help="handoff: the single-mesh workload refined")
+    ap.add_argument("--handoff-k", type=int, nargs="+", default=[500, 2000, 8000],
+                    help="handoff: insertions made by the CPU stage before the hand-off")
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=128,
@@ -845,8 +1021,8 @@ def main():
             print(json.dumps(line), flush=True)
         return
     plain = args.workload not in workloads.MULTI
-    if args.workload == "table1":
-        line = table1_arm(args, rank, world)
+    if args.workload in ("table1", "handoff"):
+        line = (table1_arm if args.workload == "table1" else handoff_arm)(args, rank, world)
         if line is not None:
             print(json.dumps(line), flush=True)
         return

@@ -95,3 +95,29 @@ def test_cpu_baseline_states_its_coverage():
     line = bench.cpu_baseline_line("clustered500k", 50000, 15.0)
     assert line["value"] == 50000 / 15.0 and line["cores"] == 1 and line["kind"] == "oracle"
     assert "of the %d insertions" % o["steiner"] in line["sample"]
+
+
+def test_handoff_cpu_stage_snapshots_are_valid_cdts():
+    """The hand-off's CPU stage stops after exactly k insertions and exports a
+    mesh whose labels, loaded the way cdr_create takes them, form a CDT of the
+    PLC that refines on to the end."""
+    import oracle
+    snaps = bench._handoff_cpu_job("cube2k", [40, 150], 60.0)
+    assert [k for k, _, _ in snaps] == [0, 40, 150]
+    assert snaps[0][1] == 0.0 and 0.0 < snaps[1][1] <= snaps[2][1]
+    B = bench.WORKLOADS["cube2k"]["B"]
+    n0 = len(snaps[0][2]["xyz"])
+    for k, _, lab in snaps:
+        assert len(lab["xyz"]) == n0 + k
+        assert lab["segs"].shape[1] == 2 and len(lab["seg_id"]) == len(lab["segs"])
+        assert lab["tris"].shape[1] == 3 and len(lab["facet_id"]) == len(lab["tris"])
+        assert lab["facet_ref"].shape == (lab["nfacets"], 3)
+        om = oracle.Mesh.create(lab["xyz"], lab["tets"])
+        assert om.set_constraints(lab["segs"], lab["seg_id"], lab["tris"], lab["facet_id"],
+                                  lab["nfacets"], facetq=lab["facet_ref"]) == 0
+        c = om.check(B)
+        assert c["bad_orient"] == 0 and c["nonlocal_delaunay"] == 0
+        assert c["sf_not_face"] == 0 and c["ss_not_edge"] == 0 and c["seg_chain_bad"] == 0
+        om.refine_S(B)
+        c = om.check(B)
+        assert c["nonlocal_delaunay"] == 0 and c["enc_subsegs"] == 0 and c["enc_subfaces"] == 0
