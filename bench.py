@@ -883,6 +883,23 @@ def handoff_arm(args, rank, world):
         acc[0] += 1
         acc[1] += dt
         acc[2] += r["steiner_inserted"]
+    # a second pass with CUDA events around every kernel group (untimed):
+    # device time per group, summed over the rounds of each class
+    h.restore()
+    h.profile(enable=1, reset=True)
+    groups = {}
+    prev = h.profile()["ms"]
+    while True:
+        r = h.round(B)
+        if r["cls"] < 0:
+            break
+        cur = h.profile()["ms"]
+        acc = groups.setdefault(r["cls"], {})
+        for g, v in cur.items():
+            if v > prev[g]:
+                acc[g] = acc.get(g, 0.0) + v - prev[g]
+        prev = cur
+    h.profile(enable=0)
     h.close()
     cls_name = {0: "subsegments", 1: "subfaces", 2: "tetrahedra", 3: "mixed"}
     round_profile = [{"class": cls_name.get(c, str(c)), "candidates_up_to": b, "rounds": v[0],
@@ -937,7 +954,9 @@ def handoff_arm(args, rank, world):
             "rows": rows, "gpu_rounds": len(timeline),
             "gpu_round_profile": {"timing": "host clock around each cdr_round (one "
                                             "synchronisation per round)",
-                                  "seconds": t, "by_class_and_size": round_profile},
+                                  "seconds": t, "by_class_and_size": round_profile,
+                                  "group_ms_by_class": {cls_name.get(c, str(c)): v for c, v in
+                                                        sorted(groups.items())}},
             "crossover_k": min(better) if better else None,
             "crossover": ("the hand-off is faster from k = %d" % min(better)) if better else
                          "none: at every k measured the GPU rounds from the start finish first"}

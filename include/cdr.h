@@ -290,8 +290,9 @@ int cdr_profile(cdr_handle* h, int32_t enable, int32_t reset, double* ms, int64_
 
 /* Launch tuning of a handle (one mesh or a batch). Results do not depend on
  * it, only speed; zero fields select the defaults.
- *   fused_max            rounds with at most this many candidates (1..128) run
- *                        as one kernel; -1: never; 0: 128
+ *   fused_max            rounds with at most this many candidates (1..512) run
+ *                        as one kernel (above 128, a warp takes several
+ *                        candidates in turn); -1: never; 0: 128
  *   grow1_blocks_per_sm  at most this many blocks per SM in the region-growth
  *                        grid (1..32); 0: 8
  *   tier2_warps          warps (each with a global workspace) for regions that

@@ -33,7 +33,7 @@ DEFAULT_PATH = os.path.join(HERE, "tuning.json")
 DEFAULTS = {"fused_max": 128, "grow1_blocks_per_sm": 8, "tier2_warps": 608,
             "tier1_cavity": 64, "tier1_boundary": 96}
 SPACE = {
-    "fused_max": [-1, 16, 32, 64, 128],
+    "fused_max": [-1, 16, 32, 64, 128, 256, 512],
     "grow1_blocks_per_sm": [2, 4, 8, 16],
     "tier2_warps": [152, 304, 608, 1216],
     "tier1_cavity": [16, 32, 64],

@@ -74,7 +74,7 @@ struct cdr_handle {
   cudaEvent_t ev[2 * 32] = {};
   bool fused = true;  // small rounds as one kernel
   // launch tuning (cdr_set_tuning)
-  int fusedMax = kFusedMax;   // rounds with at most this many candidates run fused
+  int fusedMax = kFusedDefault;  // rounds with at most this many candidates run fused
   int grow1PerSM = 8;         // growth grid: at most this many blocks per SM
   int tier2Warps = 152 * 4;   // warps (workspaces) for tier-2 growth
   int tier1Cav = 0;           // tier-1 cavity capacity (0: Tier1::CAPC)
@@ -2162,7 +2162,7 @@ int cdr_set_tuning(cdr_handle* h, const cdr_tuning* t) {
   h->compactMin = t->compact_min_tets > 0 ? t->compact_min_tets : (1 << 19);
   h->compactPct = t->compact_dead_pct > 0 ? t->compact_dead_pct : 50;
   h->fused = t->fused_max != -1;
-  h->fusedMax = t->fused_max > 0 ? t->fused_max : kFusedMax;
+  h->fusedMax = t->fused_max > 0 ? t->fused_max : kFusedDefault;
   h->grow1PerSM = t->grow1_blocks_per_sm > 0 ? t->grow1_blocks_per_sm : 8;
   int w = t->tier2_warps > 0 ? t->tier2_warps : 152 * 4;
   h->tier2Warps = w + (w & 1);  // tier-2 launches run two warps per block

@@ -1792,12 +1792,23 @@ done:
   return false;
 }
 
-// Tier-2 growth of candidate i: the hash set / boundary table starts at 32,768
-// slots (enough for a region at the cavity limit) and is enlarged to
-// Tier2::HCAP only when a region's boundary table fills it, so that most
-// regions clear a quarter of the workspace, and are grown once.
+// Tier-2 growth of candidate i. With shs set, the hash set / boundary table
+// first lives in shared memory (shcap slots), where its probes cost a fraction
+// of a global atomic's latency; a region whose table fills it is grown again
+// in the global workspace w.hset. There the table starts at 32,768 slots
+// (enough for a region at the cavity limit) and is enlarged to Tier2::HCAP
+// only when a region's boundary table fills it. A region is grown the same
+// way whatever its table's size, so the result does not depend on where the
+// table lives.
 __device__ void grow_tier2(const DevMesh& m, const DevRound& r, int i, const Ws& w, int* slab,
-                           int lane, GrowAcc& acc) {
+                           int lane, GrowAcc& acc, int* shs = nullptr, int shcap = 0) {
+  if (shs) {
+    Ws ws = w;
+    ws.hset = shs;
+    const bool full = grow_one<Tier2>(m, r, i, ws, slab, lane, acc, shcap);
+    __syncwarp();
+    if (!full) return;
+  }
   for (int hcap = 32768;; hcap = min(hcap * 4, Tier2::HCAP)) {
     const bool full = grow_one<Tier2>(m, r, i, w, slab, lane, acc, hcap);
     __syncwarp();
@@ -1866,8 +1877,17 @@ __global__ void __launch_bounds__(32 * kWarps1Big, 3) k_grow1big(DevMesh m, DevR
   flush_acc(r, acc, lane);
 }
 
-// tier 2: global-memory workspaces; the slab doubles as the list storage
+// tier 2: global-memory workspaces; the slab doubles as the list storage.
+// (Hash sets in shared memory here cost residency and ran 9% slower on the
+// 500k clustered workload: this launch is bound by the number of regions in
+// flight, not by the latency of one.)
 constexpr int kWs2Extra = Tier2::HCAP;
+// In a fused round, tier-2 hash sets of kT2FusedSlots slots are cut from the
+// block's tier-1 workspaces, which are free by then: there the slowest region
+// holds up the whole cluster, so its latency is what counts.
+constexpr int kT2FusedSlots = 8192;
+constexpr int kFusedT2Chunks = (int)(sizeof(Smem1) * kFusedWarps / (kT2FusedSlots * sizeof(int)));
+static_assert(kFusedT2Chunks >= 1, "a fused block holds at least one tier-2 hash set");
 __global__ void k_grow2(DevMesh m, DevRound r) {
   int lane = threadIdx.x & 31;
   int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -2682,8 +2702,9 @@ void launch_stall(const DevMesh& m, const DevRound& r, cudaStream_t s) {
 }
 
 // ============================================================ small rounds
-// A round with at most kFusedMax candidates runs in one thread-block cluster
-// (kFusedBlocks blocks on as many SMs, one warp per candidate): split, locate
+// A round with few candidates (kFusedDefault by default, at most kFusedMax)
+// runs in one thread-block cluster (kFusedBlocks blocks on as many SMs, one
+// warp per candidate, or several in turn): split, locate
 // (with the start claims), growth in tier 1 (shared-memory workspaces) and,
 // for regions that do not fit, tier 2 (global workspaces; candidate i uses
 // tier-2 slab i), selection, the stall rule, the allocation scan and
@@ -2779,9 +2800,11 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 1) k_round_fused(DevMesh m, 
                                                                       int* cand_w, uint8_t* ccls_w,
                                                                       int* cinst_w) {
   extern __shared__ int smraw[];
+  __shared__ int t2chunks;  // shared-memory hash sets handed out in the tier-2 phase
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
   const int warp = blockIdx.x * kFusedWarps + wib, nwarps = gridDim.x * kFusedWarps;
+  if (threadIdx.x == 0) t2chunks = 0;
   if (src) {  // order the candidates first (instead of separate key, sort and tie launches)
     if (blockIdx.x == 0) fused_order(m, r.cls, src, r.n, cand_w, ccls_w, cinst_w);
     cluster_barrier();
@@ -2802,6 +2825,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 1) k_round_fused(DevMesh m, 
     }
   }
   cluster_barrier();
+  int t2c = -2;  // this warp's shared-memory tier-2 hash set: -2 none yet, -1 global
   for (int i = warp; i < r.n; i += nwarps) {
     if (r.status[i] != OUT_RETRY) continue;  // the same value in every lane
     using L = SlabLayout<Tier2>;
@@ -2811,7 +2835,16 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 1) k_round_fused(DevMesh m, 
     Ws w2{slab + L::OFF_CAV, r.ws2 + (size_t)warp * Tier2::HCAP, slab + L::OFF_BIN,
           slab + L::OFF_BOUT, slab + L::OFF_BV, slab + L::OFF_FCAV, slab + L::OFF_FBND,
           slab + L::OFF_FBV};
-    grow_tier2(m, r, i, w2, slab, lane, acc);
+    // the tier-1 workspaces are free now: the first kFusedT2Chunks warps of
+    // the block to meet a tier-2 region keep their hash sets there
+    if (t2c < -1) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&t2chunks, 1);
+      t2c = __shfl_sync(FULLMASK, c, 0);
+      if (t2c >= kFusedT2Chunks) t2c = -1;
+    }
+    int* shs = t2c >= 0 ? smraw + (size_t)t2c * kT2FusedSlots : nullptr;
+    grow_tier2(m, r, i, w2, slab, lane, acc, shs, kT2FusedSlots);
     __syncwarp();
     if (lane == 0) {
       if (r.status[i] == OUT_RETRY) set_status(r, i, OUT_UNSPL, RS_OVERFLOW);

@@ -60,7 +60,8 @@ void launch_stall(const DevMesh& m, const DevRound& r, cudaStream_t s);
 // rounds with few candidates: the whole round in one block
 constexpr int kFusedBlocks = 8;  // one cluster (the portable maximum)
 constexpr int kFusedWarps = 16;  // per block
-constexpr int kFusedMax = kFusedBlocks * kFusedWarps;  // one warp per candidate
+constexpr int kFusedDefault = kFusedBlocks * kFusedWarps;  // one warp per candidate
+constexpr int kFusedMax = 4 * kFusedDefault;  // the largest setting: four per warp
 struct FusedOut {
   int4 tot;  // new vertices, tetrahedra, subfaces, subsegments
   int n2;    // regions grown in tier 2

@@ -194,20 +194,22 @@ def test_rounds_lockstep_boundary_mixed(cdr):
     assert h.round(1.4)["cls"] == -1
 
 
-@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("fused", [-1, 0, 512])
 def test_rounds_lockstep_tier2_growth(cdr, fused):
     """Tier-1 workspaces shrunk to 8 cavity tetrahedra and 24 boundary faces, so
     that most regions are re-grown in tier 2 (the separate k_grow2 launch, or
-    the fused round's own tier 2): lockstep with mode R to the end."""
+    the fused round's own tier 2, where at fused_max 512 a warp takes several
+    candidates and several tier-2 regions in turn): lockstep with mode R to
+    the end."""
     om, e, plc = oracle_case("uniform", 700, 7, 7, 5)
     h = gpu_handle(cdr, e, plc)
-    h.tune(fused_max=0 if fused else -1, tier1_cavity=8, tier1_boundary=24)
+    h.tune(fused_max=fused, tier1_cavity=8, tier1_boundary=24)
     h.profile(enable=1, reset=True)
     classes = _lockstep(cdr, om, h, 1.4, 3000, "tier2-700")
     assert set(classes) == {0, 1, 2}
     prof = h.profile(enable=0)
     assert prof["counters"]["retried"] > 100
-    if fused:
+    if fused >= 0:
         assert prof["calls"]["fused"] > 0
     else:
         assert prof["calls"]["grow2"] > 0 and prof["calls"]["fused"] == 0
@@ -228,8 +230,8 @@ def test_results_do_not_depend_on_tuning(cdr):
     mesh is the same."""
     om, e, plc = oracle_case("uniform", 1500, 12, 12, 9)
     ref = None
-    for t in [dict(), dict(fused_max=-1), dict(fused_max=16), dict(grow1_blocks_per_sm=2),
-              dict(tier2_warps=2, fused_max=-1)]:
+    for t in [dict(), dict(fused_max=-1), dict(fused_max=16), dict(fused_max=512),
+              dict(grow1_blocks_per_sm=2), dict(tier2_warps=2, fused_max=-1)]:
         h = gpu_handle(cdr, e, plc)
         h.tune(**t)
         st = h.refine(1.4)
