@@ -44,6 +44,14 @@ are input points touching no other constraint (every angle >= 45 degrees);
 after each triangle, with probability 1/4, a second triangle sharing one of
 its edges is added as a facet of its own when the two meet at a dihedral
 angle of at least 70 degrees, so some interior facets share a segment.
+
+Facet-recovered recipe (``free_segments`` + ``free_triangles``, for the
+recovery of r18 and its tests): triangles between input points, a seed point
+and two of its nearest neighbours, kept when their grown bounding balls meet
+no other constraint's; each triangle edge becomes a segment, and some
+triangles get an edge-sharing partner. Neither segments nor triangles need be
+in the points' Delaunay mesh; the recovery makes them so. ``plc_recovered``
+labels the result.
 """
 from __future__ import annotations
 
@@ -366,6 +374,137 @@ def plc_with_chains(xyz: np.ndarray, tets: np.ndarray, chains, n_in: int, n_tri:
             break
     if got < n_tri:
         raise ValueError("not enough well-shaped faces")
+    return _labels(tris, fids, segs, sids, nf)
+
+
+def free_triangles(pts: np.ndarray, segs: np.ndarray, n_tri: int, seed: int, knn: int = 8,
+                   min_angle: float = 30.0, gap: float = 0.25, pair_prob: float = 0.25,
+                   min_dihedral: float = 70.0) -> dict:
+    """n_tri triangles between input points for the facet-recovered recipe:
+    a seed point uniform among the unused non-corner points and two of its knn
+    nearest neighbours, every angle >= min_angle. A triangle is kept when its
+    ball (centred at its centroid, through its farthest corner), grown by the
+    factor 1 + gap, meets no grown ball of an earlier constraint (the given
+    segments, centred at their midpoints, and earlier triangles), so that no
+    two constraints meet. With probability pair_prob, a kept triangle gets a
+    partner on one of its edges (a facet of its own, sharing that segment):
+    the apex among the knn nearest unused points of the edge's midpoint, with
+    every angle >= min_angle, a dihedral angle of at least min_dihedral with
+    the first, and a ball that meets no other constraint's.
+    Returns dict(segs=(m, 2) the given segments followed by every triangle
+    edge once, tris=(t, 3), tri_segs=(t, 3) the segment of each triangle's
+    edges (a, b), (b, c), (c, a))."""
+    from scipy.spatial import cKDTree
+    pts = np.asarray(pts, dtype=np.float64)
+    segs = np.asarray(segs, dtype=np.int64).reshape(-1, 2)
+    rng = np.random.default_rng(seed + 15485863)
+    tree = cKDTree(pts)
+    used = np.zeros(len(pts), dtype=bool)
+    used[:8] = True
+    used[segs.ravel()] = True
+    centres = [0.5 * (pts[a] + pts[b]) for a, b in segs]
+    radii = [0.5 * float(np.linalg.norm(pts[b] - pts[a])) for a, b in segs]
+    cosmax = np.cos(np.radians(min_angle))
+    out_segs = [tuple(int(v) for v in e) for e in segs]
+    tris, tri_segs = [], []
+
+    def ball(P):
+        c = P.mean(axis=0)
+        return c, float(np.max(np.linalg.norm(P - c, axis=1)))
+
+    def clear(c, r, skip=()):
+        for k, (c2, r2) in enumerate(zip(centres, radii)):
+            if k in skip:
+                continue
+            if np.linalg.norm(c - c2) <= (1.0 + gap) * (r + r2):
+                return False
+        return True
+
+    def add(t, edge_ids):
+        tris.append(tuple(int(v) for v in t))
+        tri_segs.append(tuple(edge_ids))
+        c, r = ball(pts[list(t)])
+        centres.append(c)
+        radii.append(r)
+        used[list(t)] = True
+
+    tries = 0
+    while len(tris) < n_tri:
+        tries += 1
+        if tries > 200 * n_tri + 1000:
+            raise ValueError("not enough room for %d triangles" % n_tri)
+        a = int(rng.integers(8, len(pts)))
+        if used[a]:
+            continue
+        _, nb = tree.query(pts[a], k=knn + 1)
+        pick = rng.choice(knn, size=2, replace=False) + 1
+        b, c = int(nb[pick[0]]), int(nb[pick[1]])
+        if used[b] or used[c] or b < 8 or c < 8:
+            continue
+        P = pts[[a, b, c]]
+        if not _angles_ok(P, cosmax):
+            continue
+        cb, rb = ball(P)
+        if not clear(cb, rb):
+            continue
+        e0 = len(out_segs)
+        out_segs += [(a, b), (b, c), (c, a)]
+        add((a, b, c), (e0, e0 + 1, e0 + 2))
+        me = len(centres) - 1
+        if len(tris) >= n_tri or rng.random() >= pair_prob:
+            continue
+        j0 = int(rng.integers(0, 3))
+        f = (a, b, c)
+        for dj in range(3):
+            j = (j0 + dj) % 3
+            u, v, opp = f[j], f[(j + 1) % 3], f[(j + 2) % 3]
+            _, nb2 = tree.query(0.5 * (pts[u] + pts[v]), k=knn)
+            g = None
+            for x in (int(y) for y in nb2):
+                if used[x] or x < 8:
+                    continue
+                Q = pts[[u, v, x]]
+                if not _angles_ok(Q, cosmax):
+                    continue
+                if _dihedral_deg(pts[opp], pts[x], pts[u], pts[v]) < min_dihedral:
+                    continue
+                cq, rq = ball(Q)
+                if not clear(cq, rq, skip=(me,)):
+                    continue
+                g = x
+                break
+            if g is None:
+                continue
+            e1 = len(out_segs)
+            out_segs += [(v, g), (g, u)]
+            add((u, v, g), (e0 + j, e1, e1 + 1))
+            break
+    return dict(segs=np.asarray(out_segs, dtype=np.int32).reshape(-1, 2),
+                tris=np.asarray(tris, dtype=np.int32).reshape(-1, 3),
+                tri_segs=np.asarray(tri_segs, dtype=np.int32).reshape(-1, 3))
+
+
+def plc_recovered(xyz: np.ndarray, tets: np.ndarray, chains, subfaces) -> dict:
+    """Labels of a mesh whose segments and triangle facets were recovered:
+    box facets and edges, then one segment per chain (its subsegments) and one
+    facet per recovered triangle (its subfaces, facet ids from 6 on)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    if len(xyz) >= (1 << 21):
+        raise ValueError("too many points for the face packing")
+    faces, cnt, _ = _faces_edges(tets)
+    tris, fids, segs, sids = _box_labels(xyz, faces, cnt)
+    nseg = 12
+    for ch in chains:
+        for k in range(len(ch) - 1):
+            segs.append((int(ch[k]), int(ch[k + 1])))
+            sids.append(nseg)
+        nseg += 1
+    nf = 6
+    for T in subfaces:
+        for t in T:
+            tris.append(tuple(int(v) for v in t))
+            fids.append(nf)
+        nf += 1
     return _labels(tris, fids, segs, sids, nf)
 
 

@@ -105,3 +105,67 @@ def test_rounds_lockstep_ball_with_rectangles(cdr):
         assert_same_mesh(h.export(), om.export(), "rectangles round %d" % r)
     assert set(classes) == {0, 1, 2}
     h.close()
+
+
+def _free_plc_case(n, ns, nt, seed, knn):
+    from paper_1903_03406_gb300 import inputs
+    pts, _, _ = inputs.box_points("uniform", n, seed)
+    segs = inputs.free_segments(pts, ns, seed)
+    return pts, inputs.free_triangles(pts, segs, nt, seed, knn=knn)
+
+
+def test_gpu_facet_recovery_equals_oracle(cdr):
+    """Triangles that are not unions of Delaunay faces: the GPU recovery (device
+    predicates in batches, device Delaunay meshes) makes the oracle's points,
+    chains, facet points and subfaces, bit for bit, and the same mesh."""
+    from oracle.recover import recover_plc as oracle_recover
+    from paper_1903_03406_gb300 import recover
+    pts, plc = _free_plc_case(2000, 6, 6, 5, 150)
+    g = recover.recover_plc(pts, plc["segs"], plc["tris"], plc["tri_segs"], cdr)
+    o = oracle_recover(pts, plc["segs"], plc["tris"], plc["tri_segs"])
+    assert g["passes"] == o["passes"] and sum(map(len, o["facet_points"])) > 0
+    assert np.array_equal(g["xyz"], o["xyz"])
+    assert g["chains"] == o["chains"] and g["facet_points"] == o["facet_points"]
+    assert [list(map(tuple, s)) for s in g["subfaces"]] == o["subfaces"]
+    assert np.array_equal(g["facetq"], o["facetq"])
+    assert np.array_equal(_canon_tets(g["tets"]), _canon_tets(o["mesh"].export()["tets"]))
+
+
+def test_rounds_lockstep_on_recovered_facets(cdr):
+    """A PLC with recovered segments and facets, each side labelled from its
+    own recovery: every GPU round equals mode R's, to the end."""
+    from oracle.recover import facet_reference, recover_plc as oracle_recover, reference_shift
+    from paper_1903_03406_gb300 import inputs, recover
+    pts, plc = _free_plc_case(900, 4, 5, 11, 80)
+    o = oracle_recover(pts, plc["segs"], plc["tris"], plc["tri_segs"])
+    om = o["mesh"]
+    e = om.export()
+    olab = inputs.plc_recovered(o["xyz"], e["tets"], o["chains"], o["subfaces"])
+    first = {}
+    for t, f in zip(olab["tris"], olab["facet_id"]):
+        first.setdefault(int(f), t)
+    oq = np.zeros((olab["nfacets"], 3))
+    s = reference_shift(o["xyz"])
+    for f in range(6):
+        oq[f] = facet_reference(o["xyz"], int(first[f][0]), int(first[f][1]), int(first[f][2]), s)
+    oq[6:] = o["facetq"]
+    assert om.set_constraints(olab["segs"], olab["seg_id"], olab["tris"], olab["facet_id"],
+                              olab["nfacets"], facetq=oq) == 0
+    g = recover.recover_plc(pts, plc["segs"], plc["tris"], plc["tri_segs"], cdr)
+    glab = inputs.plc_recovered(g["xyz"], g["tets"], g["chains"], g["subfaces"])
+    gq = np.concatenate([recover.box_facet_refs(g["xyz"], glab), g["facetq"]])
+    h = cdr.Handle.create(g["xyz"], g["tets"], glab["segs"], glab["seg_id"], glab["tris"],
+                          glab["facet_id"], glab["nfacets"], facet_ref=gq)
+    classes = []
+    for r in range(3000):
+        gr = h.round(1.5)
+        orr = om.round(1.5)
+        assert gr["cls"] == orr["cls"], r
+        if gr["cls"] < 0:
+            break
+        classes.append(gr["cls"])
+        compare_reports(h.round_report(), om.report(), "facets round %d" % r)
+        assert gr["steiner_inserted"] == orr["inserted"]
+        assert_same_mesh(h.export(), om.export(), "facets round %d" % r)
+    assert 2 in classes
+    h.close()
