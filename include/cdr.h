@@ -74,6 +74,14 @@ typedef struct {
  *                              first vertex moved along the dominant axis of that
  *                              triangle's normal by the smallest power of two that
  *                              is >= 4x the largest bounding-box extent.
+ *   tet_flag[n_tets]          optional (NULL = none) element flags, coded as
+ *   subface_flag[n_tris]      cdr_mesh_out's (tetrahedra: bit1 unsplittable;
+ *   subseg_flag[n_segs]       subfaces and subsegments: bit0 must split, bit1
+ *                              unsplittable). With them, a mesh exported
+ *                              between rounds and created again (by cdr_create
+ *                              or cdr_batch_add) refines on exactly as the
+ *                              uninterrupted refinement would: a checkpoint on
+ *                              the host. Other bits: CDR_ERR_INVALID_INPUT.
  * Every hull face must be a subface (the domain is closed by facets). */
 typedef struct {
   const double* xyz;
@@ -88,6 +96,9 @@ typedef struct {
   int32_t n_tris;
   int32_t n_facets;
   const double* facet_ref;
+  const uint8_t* tet_flag;
+  const uint8_t* subface_flag;
+  const uint8_t* subseg_flag;
 } cdr_mesh_in;
 
 /* Options. Zero-initialised fields select the defaults given. */

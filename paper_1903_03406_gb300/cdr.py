@@ -36,7 +36,10 @@ class MeshIn(ctypes.Structure):
                 ("segs", ctypes.POINTER(ctypes.c_int32)), ("seg_id", ctypes.POINTER(ctypes.c_int32)),
                 ("n_segs", ctypes.c_int32), ("tris", ctypes.POINTER(ctypes.c_int32)),
                 ("facet_id", ctypes.POINTER(ctypes.c_int32)), ("n_tris", ctypes.c_int32),
-                ("n_facets", ctypes.c_int32), ("facet_ref", ctypes.POINTER(ctypes.c_double))]
+                ("n_facets", ctypes.c_int32), ("facet_ref", ctypes.POINTER(ctypes.c_double)),
+                ("tet_flag", ctypes.POINTER(ctypes.c_uint8)),
+                ("subface_flag", ctypes.POINTER(ctypes.c_uint8)),
+                ("subseg_flag", ctypes.POINTER(ctypes.c_uint8))]
 
 
 class Options(ctypes.Structure):
@@ -200,8 +203,9 @@ def set_tuning(ptr, fused_max=0, grow1_blocks_per_sm=0, tier2_warps=0, tier1_cav
     _check(lib().cdr_set_tuning(ptr, ctypes.byref(t)), "cdr_set_tuning")
 
 
-def _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref=None):
-    """A cdr_mesh_in over contiguous copies (returned too, to keep them alive)."""
+def _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref=None, flags=None):
+    """A cdr_mesh_in over contiguous copies (returned too, to keep them alive).
+    flags: optional (tet_flag, subface_flag, subseg_flag), any entry None."""
     xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
     tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
     segs = np.ascontiguousarray(segs, dtype=np.int32).reshape(-1, 2)
@@ -211,11 +215,16 @@ def _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref=None):
     fr = None
     if facet_ref is not None:
         fr = np.ascontiguousarray(facet_ref, dtype=np.float64).reshape(-1, 3)
+    fl = [None if f is None else np.ascontiguousarray(f, dtype=np.uint8).reshape(-1)
+          for f in (flags or (None, None, None))]
+    for f, n in zip(fl, (len(tets), len(tris), len(segs))):
+        if f is not None and len(f) != n:
+            raise ValueError("a flag array does not match its elements")
     mi = MeshIn(_p(xyz, ctypes.c_double), len(xyz), _p(tets, ctypes.c_int32), len(tets),
                 _p(segs, ctypes.c_int32), _p(seg_id, ctypes.c_int32), len(segs),
                 _p(tris, ctypes.c_int32), _p(facet_id, ctypes.c_int32), len(tris),
-                int(n_facets), _p(fr, ctypes.c_double))
-    return mi, (xyz, tets, segs, seg_id, tris, facet_id, fr)
+                int(n_facets), _p(fr, ctypes.c_double), *[_p(f, ctypes.c_uint8) for f in fl])
+    return mi, (xyz, tets, segs, seg_id, tris, facet_id, fr) + tuple(fl)
 
 
 def _export(s, call, what):
@@ -256,8 +265,9 @@ class Handle:
     @classmethod
     def create(cls, xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref=None,
                guard2=0.0, walk_limit=0, reserve_factor=0, mixed_rounds=False, allocator=None,
-               stream=None):
-        mi, _arrays = _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref)
+               stream=None, flags=None):
+        mi, _arrays = _mesh_in(xyz, tets, segs, seg_id, tris, facet_id, n_facets, facet_ref,
+                               flags)
         opt = Options(float(guard2), int(walk_limit), int(reserve_factor), int(mixed_rounds))
         out = ctypes.c_void_p()
         al = ctypes.byref(allocator.struct) if allocator is not None else None
@@ -265,6 +275,17 @@ class Handle:
                               ctypes.byref(out))
         _check(st, "cdr_create")
         return cls(out, keep=(allocator,))
+
+    @classmethod
+    def from_export(cls, ex, **kw):
+        """A handle from a mesh exported between rounds (export()'s dict): its
+        labels, facet reference points and element flags, so that the
+        refinement goes on as if it had not been interrupted (a host-side
+        checkpoint). Keyword arguments as for create."""
+        sf, ss = ex["sf"], ex["ss"]
+        return cls.create(ex["xyz"], ex["tets"], ss[:, :2], ss[:, 2], sf[:, :3], sf[:, 3],
+                          len(ex["facetq"]), facet_ref=ex["facetq"],
+                          flags=(ex["tflag"], ex["sfflag"], ex["ssflag"]), **kw)
 
     @classmethod
     def delaunay_box(cls, xyz, walk_limit=0, allocator=None, stream=None):

@@ -1200,6 +1200,15 @@ extern "C" int cdr_create(const cdr_mesh_in* in, const cdr_options* opt, const c
     if (in->facet_id[i] < 0 || in->facet_id[i] >= in->n_facets) return CDR_ERR_INVALID_INPUT;
   for (long i = 0; i < 3L * in->n_verts; ++i)
     if (!std::isfinite(in->xyz[i])) return CDR_ERR_INVALID_INPUT;
+  if (in->tet_flag)
+    for (int i = 0; i < in->n_tets; ++i)
+      if (in->tet_flag[i] & ~2) return CDR_ERR_INVALID_INPUT;
+  if (in->subface_flag)
+    for (int i = 0; i < in->n_tris; ++i)
+      if (in->subface_flag[i] & ~3) return CDR_ERR_INVALID_INPUT;
+  if (in->subseg_flag)
+    for (int i = 0; i < in->n_segs; ++i)
+      if (in->subseg_flag[i] & ~3) return CDR_ERR_INVALID_INPUT;
 
   cdr_handle* h = new (std::nothrow) cdr_handle();
   if (!h) return CDR_ERR_OOM;
@@ -1317,6 +1326,26 @@ extern "C" int cdr_create(const cdr_mesh_in* in, const cdr_options* opt, const c
       dfree(h, slo);
       dfree(h, sperm);
     }
+  }
+  // element flags of a mesh exported between rounds
+  if ((in->tet_flag && in->n_tets) || (in->subface_flag && in->n_tris) ||
+      (in->subseg_flag && in->n_segs)) {
+    Buf fl;
+    const size_t nt = in->n_tets, ns = in->n_tris, ng = in->n_segs;
+    if (!ensure(h, fl, nt + ns + ng + 64)) {
+      cdr_destroy(h);
+      return CDR_ERR_OOM;
+    }
+    uint8_t* d = ptr<uint8_t>(fl);
+    if (in->tet_flag && nt) cudaMemcpyAsync(d, in->tet_flag, nt, cudaMemcpyHostToDevice, h->stream);
+    if (in->subface_flag && ns)
+      cudaMemcpyAsync(d + nt, in->subface_flag, ns, cudaMemcpyHostToDevice, h->stream);
+    if (in->subseg_flag && ng)
+      cudaMemcpyAsync(d + nt + ns, in->subseg_flag, ng, cudaMemcpyHostToDevice, h->stream);
+    launch_apply_flags(m, in->tet_flag ? d : nullptr, in->subface_flag ? d + nt : nullptr,
+                       in->subseg_flag ? d + nt + ns : nullptr, h->stream);
+    cudaStreamSynchronize(h->stream);
+    dfree(h, fl);
   }
   launch_mark_edges(m, h->stream);
   launch_check_create(m, ptr<int>(h->bErr), h->stream);

@@ -104,6 +104,30 @@ def test_create_refuses_malformed_mesh_on_the_host(cdr, name, mesh):
     assert e.value.status == INVALID, name
 
 
+@pytest.mark.parametrize("name,flags", [
+    ("tetrahedron flag with the must-split bit", (np.array([0, 0, 1, 0, 0, 0], np.uint8), None,
+                                                   None)),
+    ("tetrahedron flag past bit1", (np.array([0, 4, 0, 0, 0, 0], np.uint8), None, None)),
+    ("subface flag past bit1", (None, np.eye(1, 12, 5, dtype=np.uint8).ravel() * 8, None)),
+    ("subsegment flag past bit1", (None, None, np.full(12, 0x80, np.uint8))),
+])
+def test_create_refuses_unknown_element_flags_on_the_host(cdr, name, flags):
+    """Element flags (a mesh exported between rounds) carry only the export's
+    bits: tetrahedra bit1, subfaces and subsegments bits 0 and 1."""
+    m = _cube()
+    with pytest.raises(cdr.CdrError) as e:
+        cdr.Handle.create(m["xyz"], m["tets"], m["segs"], m["seg_id"], m["tris"],
+                          m["facet_id"], m["n_facets"], flags=flags)
+    assert e.value.status == INVALID, name
+
+
+def test_flag_arrays_must_match_their_elements(cdr):
+    m = _cube()
+    with pytest.raises(ValueError):
+        cdr.Handle.create(m["xyz"], m["tets"], m["segs"], m["seg_id"], m["tris"],
+                          m["facet_id"], m["n_facets"], flags=(np.zeros(5, np.uint8), None, None))
+
+
 def _box_points(extra):
     corners = np.array([[i & 1, (i >> 1) & 1, (i >> 2) & 1] for i in range(8)], dtype=np.float64)
     return np.vstack([corners, np.asarray(extra, dtype=np.float64).reshape(-1, 3)])

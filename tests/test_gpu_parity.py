@@ -320,3 +320,31 @@ def test_torch_allocator_and_stream(cdr):
     h2 = gpu_handle(cdr, e, plc)
     h2.refine(2.0)
     assert_same_mesh(h1.export(), h2.export(), "torch allocator")
+
+
+def test_resume_from_exported_mesh_equals_uninterrupted(cdr):
+    """A mesh exported between rounds, element flags included, and created
+    again (Handle.from_export, cdr_mesh_in's flag arrays) refines to the mesh
+    of the uninterrupted run. The stops are chosen where the mode-R run holds
+    a must-split subsegment (50 rounds), must-split subfaces and an
+    unsplittable tetrahedron (150, 200)."""
+    B = 1.5
+    om, e, plc = oracle_case("uniform", 150, 3, 3, 41)
+    h = gpu_handle(cdr, e, plc)
+    h.refine(B)
+    final = h.export()
+    h.close()
+    om.refine_R(B)
+    assert_same_mesh(final, om.export(), "uninterrupted")
+    seen = np.zeros(3, dtype=bool)
+    for k in (50, 150, 200):
+        hp = gpu_handle(cdr, e, plc)
+        assert hp.refine(B, max_rounds=k)["rounds"] == k
+        ex = hp.export()
+        hp.close()
+        seen |= [bool(ex["tflag"].any()), bool(ex["sfflag"].any()), bool(ex["ssflag"].any())]
+        hr = cdr.Handle.from_export(ex)
+        hr.refine(B)
+        assert_same_mesh(hr.export(), final, "resumed after %d rounds" % k)
+        hr.close()
+    assert seen.all()
