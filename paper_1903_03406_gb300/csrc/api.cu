@@ -294,6 +294,29 @@ __global__ void k_init_subsegs(int4* GV, uint8_t* Gf, uint8_t* Gm, const int* se
     Gm[i] = 0;
   }
 }
+// Element flags given with the input (a mesh exported between rounds), from
+// the export's coding (tetrahedra bit1 unsplittable; subfaces and subsegments
+// bit0 must split, bit1 unsplittable) into the device flags. Element i of
+// each kind is input element i.
+__global__ void k_apply_flags(DevMesh m, const uint8_t* tf, const uint8_t* sf, const uint8_t* gf) {
+  const long n = (long)m.nT + m.nS + m.nG;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    if (i < m.nT) {
+      if (tf && (tf[i] & 2)) m.Tflag[i] |= F_UNSPL;
+    } else if (i < (long)m.nT + m.nS) {
+      const long k = i - m.nT;
+      if (!sf) continue;
+      if (sf[k] & 2) m.Sflag[k] |= F_UNSPL;
+      m.Smust[k] = (sf[k] & 1) ? 1 : 0;
+    } else {
+      const long k = i - m.nT - m.nS;
+      if (!gf) continue;
+      if (gf[k] & 2) m.Gflag[k] |= F_UNSPL;
+      m.Gmust[k] = (gf[k] & 1) ? 1 : 0;
+    }
+  }
+}
 __global__ void k_scatter_slab2(const int* list2, int n2, int* slab2_of) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n2; j += gridDim.x * blockDim.x)
     slab2_of[list2[j]] = j;
@@ -1342,8 +1365,9 @@ extern "C" int cdr_create(const cdr_mesh_in* in, const cdr_options* opt, const c
       cudaMemcpyAsync(d + nt, in->subface_flag, ns, cudaMemcpyHostToDevice, h->stream);
     if (in->subseg_flag && ng)
       cudaMemcpyAsync(d + nt + ns, in->subseg_flag, ng, cudaMemcpyHostToDevice, h->stream);
-    launch_apply_flags(m, in->tet_flag ? d : nullptr, in->subface_flag ? d + nt : nullptr,
-                       in->subseg_flag ? d + nt + ns : nullptr, h->stream);
+    k_apply_flags<<<gridn((long)nt + ns + ng), 256, 0, h->stream>>>(
+        m, in->tet_flag ? d : nullptr, in->subface_flag ? d + nt : nullptr,
+        in->subseg_flag ? d + nt + ns : nullptr);
     cudaStreamSynchronize(h->stream);
     dfree(h, fl);
   }

@@ -242,35 +242,6 @@ __device__ int face_lower_bound(const unsigned long long* hi, const unsigned int
   return a;
 }
 
-// Element flags given with the input (a mesh exported between rounds): the
-// export's coding (tetrahedra bit1 unsplittable; subfaces and subsegments bit0
-// must split, bit1 unsplittable) into the device flags.
-__global__ void k_apply_flags(DevMesh m, const uint8_t* tf, const uint8_t* sf, const uint8_t* gf) {
-  const long n = (long)m.nT + m.nS + m.nG;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
-    if (i < m.nT) {
-      const int t = (int)i;
-      if (tf && (tf[t] & 2)) m.Tflag[CKI(t, m.capT)] |= F_UNSPL;
-    } else if (i < (long)m.nT + m.nS) {
-      const int k = (int)(i - m.nT);
-      if (!sf) continue;
-      if (sf[k] & 2) m.Sflag[CKI(k, m.capS)] |= F_UNSPL;
-      m.Smust[CKI(k, m.capS)] = (sf[k] & 1) ? 1 : 0;
-    } else {
-      const int k = (int)(i - m.nT - m.nS);
-      if (!gf) continue;
-      if (gf[k] & 2) m.Gflag[CKI(k, m.capG)] |= F_UNSPL;
-      m.Gmust[CKI(k, m.capG)] = (gf[k] & 1) ? 1 : 0;
-    }
-  }
-}
-void launch_apply_flags(const DevMesh& m, const uint8_t* tf, const uint8_t* sf, const uint8_t* gf,
-                        cudaStream_t s) {
-  const long n = (long)m.nT + m.nS + m.nG;
-  if (n > 0) k_apply_flags<<<grid_for(n, 256), 256, 0, s>>>(m, tf, sf, gf);
-}
-
 __global__ void k_label_subfaces(DevMesh m, const int4* tris, int n, const unsigned long long* hi,
                                  const unsigned int* lo, const int* val, int nfaces, int* err) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {

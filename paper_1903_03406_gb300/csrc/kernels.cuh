@@ -23,8 +23,6 @@ void launch_pair_subface_edges(const DevMesh& m, const unsigned long long* hi,
 void launch_hash_clear(const DevMesh& m, cudaStream_t s);
 void launch_hash_insert_subsegs(const DevMesh& m, int g0, int g1, cudaStream_t s);
 void launch_mark_edges(const DevMesh& m, cudaStream_t s);
-void launch_apply_flags(const DevMesh& m, const uint8_t* tf, const uint8_t* sf, const uint8_t* gf,
-                        cudaStream_t s);
 void launch_check_create(const DevMesh& m, int* err, cudaStream_t s);
 void launch_recompute_bad(const DevMesh& m, double B, cudaStream_t s);
 
