@@ -126,43 +126,65 @@ def _items(*pts):
     return it
 
 
+_TRIPLES = {}
+
+
+def _triples(k):
+    """Index triples (a < b < c) of range(k), lexicographic, cached per k."""
+    t = _TRIPLES.get(k)
+    if t is None:
+        t = np.asarray(list(itertools.combinations(range(k), 3)), dtype=np.int64).reshape(-1, 3)
+        _TRIPLES[k] = t
+    return t
+
+
 def _facet_triangles(xyz, verts, chain_sets, q, ev):
     """Per facet: its Delaunay triangles (sorted id triples, sorted), from the
-    device's orient3d and insphere signs."""
-    cand, owner = [], []
+    device's orient3d and insphere signs, each kind in one batch."""
+    cand, owner, vsets = [], [], []
     for f, V in enumerate(verts):
-        V = sorted(V)
-        for t in itertools.combinations(V, 3):
-            if any(t[0] in c and t[1] in c and t[2] in c for c in chain_sets[f]):
-                continue
-            cand.append(t)
-            owner.append(f)
+        V = np.asarray(sorted(V), dtype=np.int64)
+        vsets.append(V)
+        if len(V) < 3:
+            continue
+        tr = _triples(len(V))
+        on = np.stack([np.isin(V, np.fromiter(c, dtype=np.int64)) for c in chain_sets[f]],
+                      axis=1)  # (k, chains): vertex on chain
+        one = (on[tr[:, 0]] & on[tr[:, 1]] & on[tr[:, 2]]).any(axis=1)
+        cand.append(V[tr[~one]])
+        owner.append(np.full(int((~one).sum()), f, dtype=np.int64))
     out = [[] for _ in verts]
     if not cand:
         return out
-    T = np.asarray(cand, dtype=np.int64)
-    own = np.asarray(owner)
+    T = np.concatenate(cand)
+    own = np.concatenate(owner)
+    if not len(T):
+        return out
     o, _ = ev("orient", _items(xyz[T[:, 0]], xyz[T[:, 1]], xyz[T[:, 2]], q[own]))
     keep = np.nonzero(o != 0)[0]
     P = T[keep].copy()
     neg = o[keep] < 0
     P[neg, 1], P[neg, 2] = T[keep][neg, 2], T[keep][neg, 1]  # positively oriented
+    # every other point of the facet against each kept triangle
     rows, pts_ = [], []
-    for r, i in enumerate(keep):
-        for p in sorted(verts[owner[i]]):
-            if p not in cand[i]:
-                rows.append(r)
-                pts_.append(p)
-    rows = np.asarray(rows, dtype=np.int64)
+    ko = own[keep]
+    for f in np.unique(ko):
+        r = np.nonzero(ko == f)[0]
+        V = vsets[f]
+        other = ~((V[None, :] == T[keep][r][:, :1]) | (V[None, :] == T[keep][r][:, 1:2]) |
+                  (V[None, :] == T[keep][r][:, 2:3]))
+        rr, cc = np.nonzero(other)
+        rows.append(r[rr])
+        pts_.append(V[cc])
+    rows = np.concatenate(rows)
     inside = np.zeros(len(keep), dtype=bool)
     if len(rows):
-        pp = np.asarray(pts_, dtype=np.int64)
+        pp = np.concatenate(pts_)
         s, _ = ev("insphere", _items(xyz[P[rows, 0]], xyz[P[rows, 1]], xyz[P[rows, 2]],
                                      q[own[keep][rows]], xyz[pp]))
         np.logical_or.at(inside, rows, s > 0)
-    for r, i in enumerate(keep):
-        if not inside[r]:
-            out[owner[i]].append(cand[i])
+    for r in np.nonzero(~inside)[0]:
+        out[int(ko[r])].append(tuple(int(v) for v in T[keep[r]]))
     return [sorted(x) for x in out]
 
 
