@@ -121,6 +121,25 @@ def test_create_refuses_unknown_element_flags_on_the_host(cdr, name, flags):
     assert e.value.status == INVALID, name
 
 
+def test_from_export_passes_labels_references_and_flags(cdr):
+    """Handle.from_export reads an export()-shaped dict: subsegments (a, b, id),
+    subfaces (a, b, c, facet), facet references and the three flag arrays; a
+    flag bit the export never writes is refused on the host, so the flags do
+    reach cdr_create."""
+    m = _cube()
+    ex = dict(xyz=m["xyz"], tets=m["tets"], tflag=np.zeros(6, np.uint8),
+              sf=np.concatenate([m["tris"], m["facet_id"][:, None]], axis=1),
+              sfflag=np.zeros(12, np.uint8),
+              ss=np.concatenate([m["segs"], m["seg_id"][:, None]], axis=1),
+              ssflag=np.zeros(12, np.uint8), facetq=np.zeros((6, 3)))
+    for key, n in (("tflag", 6), ("sfflag", 12), ("ssflag", 12)):
+        bad = dict(ex)
+        bad[key] = np.full(n, 0x10, np.uint8)
+        with pytest.raises(cdr.CdrError) as e:
+            cdr.Handle.from_export(bad)
+        assert e.value.status == INVALID, key
+
+
 def test_flag_arrays_must_match_their_elements(cdr):
     m = _cube()
     with pytest.raises(ValueError):
