@@ -1,11 +1,13 @@
-"""Segment recovery on the GPU against the oracle's recovery (needs a GPU).
+"""Segment and facet recovery on the GPU against the oracle's (needs a GPU).
 
 The GPU recovery (Delaunay meshes built by the library's point-insertion
-rounds, midpoints by its midpoint formula) must give the oracle's recovery bit
-for bit on small inputs: the same points in the same order, the same chains
-and the same tetrahedra. A PLC built on the recovered mesh is then refined in
-lockstep with the oracle's mode R, round by round, to the end; so is a PLC of
-the Table-1-like recipe (a ball of points with rectangles).
+rounds, midpoints, circumcentres and predicate signs from its device
+formulas) must give the oracle's recovery bit for bit on small inputs: the
+same points in the same order, the same chains, facet points and subfaces,
+and the same tetrahedra. PLCs built on recovered meshes (segments only, and
+segments with triangle facets) are then refined in lockstep with the oracle's
+mode R, round by round, to the end; so is a PLC of the Table-1-like recipe (a
+ball of points with rectangles).
 """
 import numpy as np
 import pytest
